@@ -1,0 +1,258 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+* residual and energy vs brute-force second quantisation (e^{-T} H e^{T} on determinants)
+* Jacobian: connected term list vs the polynomial-exact stencil of Omega, and
+  entry by entry vs finite differences of the brute-force residual at o=2, v=4
+* transpose product: bilinear identity and the explicit transpose
+* xi vs brute force; eta0 vs finite differences of E
+* alpha vs the exact sum over states at o=2 (CCSD = FCI for two electrons)
+* static alpha vs the finite-field second derivative of the CCSD energy at o=3
+* left (Y) route = right (X-only) route; Hermiticity of alpha
+* Cholesky: pivoted decomposition reconstructs (pr|qs) within the threshold
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccsd, jacobian as J, response as R, secondq
+from oracle.integrals import as_t, eri_anti, eri_phys, pivoted_cholesky
+from paper_2604_12914_gb300.inputs import make_system, random_amplitudes, make_config
+
+from oracle_helpers import oracle_problem, hermitian
+
+C = torch.complex128
+
+
+def _system(o, v, naux, seed, scale, t1_scale=0.0):
+    return make_system(o, v, naux, seed=seed, scale=scale, t1_scale=t1_scale)
+
+
+@pytest.mark.parametrize("o,v,naux", [(2, 4, 6), (3, 5, 8)])
+def test_residual_energy_vs_brute_force(o, v, naux, rng):
+    s = _system(o, v, naux, seed=3, scale=0.5, t1_scale=0.3)
+    L = as_t(s.L)
+    g = eri_anti(L)
+    f = torch.diag(as_t(s.eps).to(C)) + as_t(hermitian(rng, o + v, 0.1))   # non-canonical
+    a1, a2 = random_amplitudes(o, v, seed=9, s1=0.3, s2=0.3)
+    t1, t2 = as_t(a1), as_t(a2)
+    bf = secondq.BruteForce(f.numpy(), g.numpy(), o)
+    r1b, r2b, eb = bf.residual(t1.numpy(), t2.numpy())
+    r1, r2 = ccsd.residual(f, g, t1, t2)
+    e = ccsd.energy(f, g, t1, t2)
+    assert abs(e.item() - eb) < 1e-12
+    assert np.abs(r1.numpy() - r1b).max() < 1e-12
+    assert np.abs(r2.numpy() - r2b).max() < 1e-12 * max(1.0, np.abs(r2b).max())
+
+
+def test_integrals_bruteforce_sum():
+    s = make_config("C1")
+    L = as_t(s.L)
+    g = eri_phys(L)
+    rng = np.random.default_rng(0)
+    for _ in range(20):
+        p, q, r, t = rng.integers(0, s.n, 4)
+        ref = sum(s.L[P, p, r] * s.L[P, q, t] for P in range(s.naux))
+        assert abs(g[p, q, r, t].item() - ref) < 1e-10
+    # Hermiticity <pq|rs>* = <rs|pq> and particle symmetry <pq|rs> = <qp|sr>
+    sub = g[:12, :12, :12, :12]
+    assert torch.allclose(sub.conj(), sub.permute(2, 3, 0, 1), atol=1e-12)
+    assert torch.allclose(sub, sub.permute(1, 0, 3, 2), atol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["T0", "T2", "T1", "T1T2"])
+def test_sigma_terms_vs_stencil(case):
+    o, v, naux = 3, 6, 10
+    s = _system(o, v, naux, seed=3, scale=0.5)
+    L = as_t(s.L)
+    g = eri_anti(L)
+    f = torch.diag(as_t(s.eps).to(C))
+    a1, a2 = random_amplitudes(o, v, seed=9, s1=0.3, s2=0.3)
+    t1 = as_t(a1) if "T1" in case else torch.zeros(o, v, dtype=C)
+    t2 = as_t(a2) if "T2" in case else torch.zeros(o, o, v, v, dtype=C)
+    x1, x2 = map(as_t, random_amplitudes(o, v, seed=11))
+    s1, s2 = J.sigma_stencil(f, g, t1, t2, x1, x2)
+    q1, q2 = J.sigma_terms(J.Dressed(f, L, t1, t2), x1, x2)
+    scale = float(s2.abs().max())
+    assert float((s1 - q1).abs().max()) < 1e-12 * scale
+    assert float((s2 - q2).abs().max()) < 1e-12 * scale
+
+
+def test_jacobian_entrywise_vs_bruteforce_fd():
+    """A_mu,nu at o=2, v=4 from central differences of the brute-force residual."""
+    o, v = 2, 4
+    s = _system(o, v, 6, seed=5, scale=0.4, t1_scale=0.2)
+    P = oracle_problem(s)
+    a1, a2 = random_amplitudes(o, v, seed=4, s1=0.2, s2=0.2)
+    P.t1, P.t2 = as_t(a1), as_t(a2)
+    A = P.jacobian_matrix()
+    bf = secondq.BruteForce(P.f.numpy(), P.g.numpy(), o)
+    N = P.nvec
+    h = 1e-4
+    Afd = np.zeros((N, N), complex)
+    for k in range(N):
+        e = torch.zeros(N, dtype=C)
+        e[k] = 1.0
+        d1, d2 = P.unpack(e)
+        cols = []
+        for sgn in (+1, -1):
+            r1, r2, _ = bf.residual((P.t1 + sgn * h * d1).numpy(), (P.t2 + sgn * h * d2).numpy())
+            cols.append(P.pack(torch.from_numpy(r1), torch.from_numpy(r2)).numpy())
+        Afd[:, k] = (cols[0] - cols[1]) / (2 * h)
+    assert np.abs(A.numpy() - Afd).max() < 1e-6 * np.abs(Afd).max()
+
+
+def test_sigma_linear_and_antisymmetric():
+    o, v = 3, 7
+    s = _system(o, v, 9, seed=6, scale=0.5, t1_scale=0.1)
+    P = oracle_problem(s)
+    x1, x2 = map(as_t, random_amplitudes(o, v, seed=1))
+    y1, y2 = map(as_t, random_amplitudes(o, v, seed=2))
+    a, b = 0.7 - 0.2j, -1.3 + 0.4j
+    s_x = P.sigma(x1, x2)
+    s_y = P.sigma(y1, y2)
+    s_c = P.sigma(a * x1 + b * y1, a * x2 + b * y2)
+    ref = (a * s_x[0] + b * s_y[0], a * s_x[1] + b * s_y[1])
+    sc = float(s_c[1].abs().max())
+    assert float((s_c[0] - ref[0]).abs().max()) < 1e-13 * sc
+    assert float((s_c[1] - ref[1]).abs().max()) < 1e-13 * sc
+    s2 = s_x[1]
+    assert float((s2 + s2.transpose(0, 1)).abs().max()) < 1e-13 * sc
+    assert float((s2 + s2.transpose(2, 3)).abs().max()) < 1e-13 * sc
+
+
+def test_sigma_T_bilinear_and_explicit_transpose():
+    o, v = 2, 4
+    s = _system(o, v, 6, seed=7, scale=0.5, t1_scale=0.2)
+    P = oracle_problem(s)
+    x1, x2 = map(as_t, random_amplitudes(o, v, seed=1))
+    y1, y2 = map(as_t, random_amplitudes(o, v, seed=2))
+    sx = P.sigma(x1, x2)
+    sty = J.sigma_T(P.f, P.g, P.t1, P.t2, y1, y2)
+    lhs = ccsd.dot(y1, y2, *sx)
+    rhs = ccsd.dot(*sty, x1, x2)
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    A = P.jacobian_matrix()
+    z = A.transpose(0, 1) @ P.pack(y1, y2)
+    assert float((P.pack(*sty) - z).abs().max()) < 1e-12 * float(z.abs().max())
+
+
+def test_xi_vs_bruteforce():
+    o, v = 3, 5
+    s = _system(o, v, 8, seed=8, scale=0.5, t1_scale=0.2)
+    P = oracle_problem(s)
+    a1, a2 = random_amplitudes(o, v, seed=3, s1=0.3, s2=0.3)
+    P.t1, P.t2 = as_t(a1), as_t(a2)
+    B = as_t(s.mu[2])
+    bf = secondq.BruteForce(P.f.numpy(), P.g.numpy(), o)
+    r1b, r2b = bf.xi(B.numpy(), P.t1.numpy(), P.t2.numpy())
+    r1, r2 = P.xi(B)
+    assert np.abs(r1.numpy() - r1b).max() < 1e-12
+    assert np.abs(r2.numpy() - r2b).max() < 1e-12
+
+
+def test_eta0_vs_energy_fd():
+    o, v = 3, 5
+    s = _system(o, v, 8, seed=9, scale=0.5, t1_scale=0.2)
+    P = oracle_problem(s)
+    a1, a2 = random_amplitudes(o, v, seed=5, s1=0.3, s2=0.3)
+    P.t1, P.t2 = as_t(a1), as_t(a2)
+    e0 = P.eta0()
+    d1, d2 = map(as_t, random_amplitudes(o, v, seed=6))
+    h = 1e-3
+    fd = sum(c * P.energy(P.t1 + k * h * d1, P.t2 + k * h * d2) for c, k in R.STENCIL) / (12 * h)
+    assert abs(fd - e0 @ P.pack(d1, d2)) < 1e-10 * abs(fd)
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.0428])
+def test_alpha_vs_sum_over_states(omega):
+    """Two electrons: CCSD is exact, so CC linear response equals Eq. sos."""
+    o, v = 2, 4
+    s = _system(o, v, 6, seed=2, scale=0.3)
+    P = oracle_problem(s, converge=True)
+    bf = secondq.BruteForce(P.f.numpy(), P.g.numpy(), o)
+    w, U = bf.fci()
+    st, ov = secondq.cc_state_overlap(U, P.t1.numpy(), P.t2.numpy(), bf)
+    assert ov > 1 - 1e-10
+    mu = [as_t(m) for m in s.mu]
+    ops = [bf.one_body_op(m.numpy()) for m in mu]
+    al = R.alpha(P, mu, omega).numpy()
+    sos = np.array([[-secondq.sos_response(w, U, ops[a], ops[b], omega, st) for b in range(3)]
+                    for a in range(3)])
+    assert np.abs(al - sos).max() < 1e-10 * np.abs(sos).max()
+    # Hermitian tensor, real diagonal
+    assert np.abs(al - al.conj().T).max() < 1e-12 * np.abs(al).max()
+    # excitation energies: eig(A) = FCI excitation energies from the CC state
+    eigA = np.sort(np.linalg.eigvals(P.jacobian_matrix().numpy()).real)
+    exc = np.sort(np.delete(w - w[st], st))
+    assert np.abs(eigA - exc).max() < 1e-10
+
+
+def test_left_route_equals_right_route():
+    o, v = 2, 5
+    s = _system(o, v, 6, seed=12, scale=0.3)
+    P = oracle_problem(s, converge=True)
+    mu = [as_t(m) for m in s.mu]
+    omega = 0.05
+    A = P.jacobian_matrix()
+    lam = torch.linalg.solve(A.transpose(0, 1), -P.eta0())
+    gl = R.g_left(P, mu[0], mu[2], omega, lam=lam, A=A)
+    xi = [P.pack(*P.xi(m)) for m in mu]
+    Xb = P.unpack(R.solve_x(A, xi[2], omega))
+    Xa = P.unpack(R.solve_x(A, xi[0], -omega))
+    gr = P.eta_dot(mu[0], lam, *Xb) + P.eta_dot(mu[2], lam, *Xa) + P.fxx(lam, Xa, Xb)
+    assert abs(gl - gr) < 1e-10 * abs(gr)
+
+
+@pytest.mark.slow
+def test_static_alpha_vs_finite_field():
+    """o=3: unconjugated g(A,B;0) = d^2 E / dF_A dF_B (unrelaxed orbitals, V = +F mu)."""
+    o, v = 3, 5
+    s = _system(o, v, 8, seed=14, scale=0.3)
+    P = oracle_problem(s, converge=True)
+    mu = [as_t(m) for m in s.mu]
+    A = P.jacobian_matrix()
+    lam = torch.linalg.solve(A.transpose(0, 1), -P.eta0())
+
+    def e_field(FA, FB, a, b):
+        f = P.f + FA * mu[a] + FB * mu[b]
+        t1, t2, _ = R.solve_ccsd(f, P.g, o, t1=P.t1, t2=P.t2, tol=1e-13, L=P.L)
+        return ccsd.energy(f, P.g, t1, t2).item()
+
+    h = 2e-3
+    for a, b in [(2, 2), (0, 2)]:
+        d2 = (e_field(h, h, a, b) - e_field(h, -h, a, b) - e_field(-h, h, a, b) + e_field(-h, -h, a, b)) / (4 * h * h)
+        xi = [P.pack(*P.xi(m)) for m in mu]
+        Xa = P.unpack(R.solve_x(A, xi[a], 0.0))
+        Xb = P.unpack(R.solve_x(A, xi[b], 0.0))
+        g = P.eta_dot(mu[a], lam, *Xb) + P.eta_dot(mu[b], lam, *Xa) + P.fxx(lam, Xa, Xb)
+        assert abs(g - d2) < 2e-5 * abs(d2), (a, b, g, d2)
+
+
+def test_cholesky_reconstruction():
+    """(pr|qs) supermatrix from the C1-sized L: pivoted CD to tau reproduces it within tau."""
+    s = make_system(6, 14, 40, seed=1)
+    n = s.n
+    Lm = s.L.reshape(s.naux, n * n)                       # row P, column (p,r)
+    # G_(pr),(sq) = (pr|qs) = sum_P L^P_pr L^P_qs, with L^P_qs = conj(L^P_sq)
+    G = Lm.T @ np.conj(Lm)
+    assert np.abs(G - G.conj().T).max() < 1e-10
+    for tau in (1e-2, 1e-5):
+        K, dmax = pivoted_cholesky(G, tau)
+        assert K.shape[1] <= s.naux
+        assert dmax < tau
+        assert np.abs(G - K @ K.conj().T).max() <= tau + 1e-10
+
+
+def test_first_order_amplitudes_cancel_first_order_residual():
+    o, v = 3, 6
+    s = _system(o, v, 8, seed=15, scale=1.0)
+    L = as_t(s.L)
+    f = torch.diag(as_t(s.eps).to(C))
+    res = []
+    for lam_ in (1e-3, 2e-3):
+        g = eri_anti(L * np.sqrt(lam_))
+        t2 = ccsd.first_order_t2(as_t(s.eps), g, o)
+        r1, r2 = ccsd.residual(f, g, torch.zeros(o, v, dtype=C), t2)
+        res.append(float(r2.abs().max()))
+    # remaining residual is second order in the interaction
+    assert 3.5 < res[1] / res[0] < 4.5
