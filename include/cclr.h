@@ -1,0 +1,138 @@
+/*
+ * cclr.h -- C ABI of libcclr, the GB300 (sm_103a) Cholesky-decomposed relativistic
+ * LR-CCSD response library.
+ *
+ * The operation: the CC Jacobian-vector product sigma = A X (Sec. 2.2, the Jacobian
+ * A_mu,nu = <mu|[H-bar_0, tau_nu]|Phi_0>), its transpose Y A (the left / Lambda
+ * equations, Sec. 2.2), and the linear solve (A - omega) X = -xi whose solution gives
+ * the polarisability alpha_AB(omega) = -<<A;B>>_omega through the CC linear response
+ * function with the P(A,B) symmetrisation (Sec. 2.2).  Two-electron integrals enter
+ * only as Cholesky vectors (Sec. 3): <pq|rs> = (pr|qs) = sum_P L^P_pr L^P_qs, with each
+ * L^P Hermitian; integrals with more than two virtual indices are formed on the fly on
+ * the GPU and never stored.
+ *
+ * Conventions common to every entry point:
+ *  - Complex numbers are interleaved (re, im) pairs of doubles (the layout of C99
+ *    double _Complex and numpy complex128).  A "complex array of N entries" is 2N doubles.
+ *  - All arrays are row-major.  n = o + v spinors, occupied first.
+ *      eps [n]            real orbital (spinor) energies; the Fock matrix is diag(eps)
+ *      L   [naux][n][n]   complex, each L[P] Hermitian
+ *      mu  [3][n][n]      complex Hermitian dipole integrals (x, y, z)
+ *      t1  [o][v]         t_i^a             (NULL: zero)
+ *      t2  [o][o][v][v]   t_ij^ab, antisymmetric in (i,j) and in (a,b)
+ *                         (NULL: first-order amplitudes <ab||ij>/(e_i+e_j-e_a-e_b))
+ *      x1/s1 [nrhs][o][v], x2/s2 [nrhs][o][o][v][v]  amplitude-shaped vectors; doubles
+ *                         blocks are full antisymmetric tensors (not packed).
+ *  - Ownership: inputs are copied (to the device) during the call; the caller keeps
+ *    ownership and may free them after return.  Outputs are caller-allocated.
+ *  - device_ptrs = 0: every array argument is host memory; 1: device memory of the
+ *    current CUDA device (e.g. torch tensors), used on the context's stream.
+ *  - Errors: every call returns a cclr_status and never aborts or exits.  On error the
+ *    outputs are unspecified; cc_lr_last_error() describes the failure.
+ *  - Threading: a context is used by one host thread at a time.
+ */
+#ifndef CCLR_H
+#define CCLR_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cclr_ctx cclr_ctx;
+
+typedef enum {
+  CCLR_OK = 0,
+  CCLR_EINVAL = 1,      /* bad argument (size, pointer, mode)                         */
+  CCLR_ENOMEM = 2,      /* device allocation failed or the HBM budget is exceeded       */
+  CCLR_ENOCONV = 3,     /* solver stopped without meeting the tolerance (alpha filled)  */
+  CCLR_EDEVICE = 4,     /* CUDA runtime / driver error                                  */
+  CCLR_ETIMEOUT = 5,    /* a bounded device-side wait gave up                           */
+  CCLR_EUNSUPPORTED = 6 /* mode not available on this device or build                   */
+} cclr_status;
+
+/* Arithmetic of sigma and sigma^T.  FP64: complex128 everywhere.  The others run the
+ * contractions in complex64 (tensor cores for the dominant ones) and keep the solver
+ * state, residuals, subspace algebra and alpha in FP64. */
+typedef enum {
+  CCLR_FP64 = 0,
+  CCLR_C64_TF32 = 1,     /* one TF32 tensor-core pass                                   */
+  CCLR_C64_3XTF32 = 2,   /* split hi/lo TF32, three passes (about FP32 accuracy)        */
+  CCLR_C64_FP32 = 3      /* complex64 on FP32 CUDA cores (no tensor cores)              */
+} cclr_prec;
+
+typedef struct {
+  int iterations;        /* total solver iterations over all right-hand sides          */
+  int sigma_calls;       /* number of sigma (or sigma^T) vectors formed                */
+  int refinements;       /* FP64-accurate residual evaluations (mixed modes)           */
+  int converged;         /* 1 if every right-hand side met the tolerance               */
+  double max_rel_residual; /* max over RHS of ||r|| / ||b|| at exit                     */
+  double time_solve_ms;  /* X solves                                                   */
+  double time_lambda_ms; /* ground-state Lambda solve (cached after the first call)    */
+  double time_alpha_ms;  /* eta.X, F.X.X and the alpha contraction                     */
+} cclr_stats;
+
+/* Create a context: copy the inputs to the device, T1-dress the Cholesky vectors,
+ * build the stored intermediates (integrals with at most two virtual indices, the
+ * one-body and o^2v^2 / o^3v / o^4 elements of H-bar) and the diagonal preconditioner.
+ * lam1/lam2 ([o][v], [o][o][v][v]) give the ground-state Lambda; NULL means it is
+ * solved on first use (lambda A = -dE/dT).  hbm_budget_bytes = 0: no limit.
+ * cuda_stream: a cudaStream_t (NULL: the legacy default stream). */
+cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux,
+                       const double *eps, const double *L, const double *mu,
+                       const double *t1, const double *t2,
+                       const double *lam1, const double *lam2,
+                       int prec, size_t hbm_budget_bytes, int device_ptrs,
+                       void *cuda_stream);
+
+/* sigma = A X for nrhs vectors (Sec. 2.2 Jacobian).  s1/s2 are overwritten. */
+cclr_status cc_lr_sigma(cclr_ctx *ctx, int nrhs, const double *x1, const double *x2,
+                        double *s1, double *s2);
+
+/* sigma^T = Y A (bilinear, no conjugation) over unique amplitudes: with
+ * <Y, Z> = sum_ia Y_ia Z_ia + 1/4 sum_ijab Y_ijab Z_ijab it satisfies
+ * <Y, A X> = <sigma^T(Y), X>.  Used by the Lambda and left response equations. */
+cclr_status cc_lr_sigma_T(cclr_ctx *ctx, int nrhs, const double *y1, const double *y2,
+                          double *s1, double *s2);
+
+/* Right-hand side xi^B = <nu|e^{-T} mu^B e^{T}|Phi_0> (Sec. 2.2) for component
+ * comp (0 = x, 1 = y, 2 = z). */
+cclr_status cc_lr_xi(cclr_ctx *ctx, int comp, double *xi1, double *xi2);
+
+/* Solve (A - omega) X = -xi^comp (Sec. 2.2, alpha -> 0+) and return X. */
+cclr_status cc_lr_solve_x(cclr_ctx *ctx, double omega, int comp, double tol, int diis_depth,
+                          double *x1, double *x2, cclr_stats *stats);
+
+/* alpha_AB(omega) = -<<A;B>>_omega for every omega in omegas and A, B in comps:
+ * alpha[w][a][b], complex (2 doubles per entry), host memory.  Solves X^B(+-omega) for
+ * each component (batched), the ground-state Lambda if not given, and evaluates
+ * g(A,B;w) = eta^A.X^B(w) + eta^B.X^A(-w) + (F X^A(-w)).X^B(w),
+ * <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)].  tol is the relative residual target
+ * ||r||/||b||.  On CCLR_ENOCONV alpha and stats still hold the last estimate. */
+cclr_status cc_lr_solve(cclr_ctx *ctx, int nomega, const double *omegas, int ncomp,
+                        const int *comps, double tol, int diis_depth, double *alpha,
+                        cclr_stats *stats);
+
+/* Ground-state Lambda (solved if needed) copied out: lam1 [o][v], lam2 [o][o][v][v]. */
+cclr_status cc_lr_lambda(cclr_ctx *ctx, double tol, double *lam1, double *lam2);
+
+/* The amplitudes the context holds (useful when t2 was NULL at init). */
+cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
+
+/* Switch the arithmetic of subsequent sigma / sigma^T / solves. */
+cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
+
+/* Device-side timing of the last cc_lr_sigma call, split by kernel family
+ * (milliseconds): [0] pp-ladder, [1] other contractions, [2] elementwise/permute. */
+cclr_status cc_lr_last_timings(cclr_ctx *ctx, double *ms3);
+
+void cc_lr_free(cclr_ctx *ctx);
+const char *cc_lr_strerror(cclr_status status);
+/* Thread-local text of the most recent failure (never NULL). */
+const char *cc_lr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCLR_H */

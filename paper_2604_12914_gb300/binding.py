@@ -1,0 +1,217 @@
+"""Thin ctypes binding of libcclr (include/cclr.h): argument marshalling only.
+
+Every computation runs in the CUDA library.  Arrays may be numpy (host; the context is
+created with device_ptrs=0) or CUDA torch tensors (device_ptrs=1, used on the given
+stream).  Complex arrays are complex128 (interleaved re/im doubles).  If the shared
+library is missing or cannot be loaded, every entry point raises: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcclr.so")
+
+CCLR_OK, CCLR_EINVAL, CCLR_ENOMEM, CCLR_ENOCONV, CCLR_EDEVICE, CCLR_ETIMEOUT, CCLR_EUNSUPPORTED = range(7)
+CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32 = range(4)
+PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32}
+
+EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
+           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_last_timings",
+           "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error"]
+
+
+class CclrError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"libcclr status {status}: {msg}")
+        self.status = status
+
+
+class cclr_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("sigma_calls", ctypes.c_int),
+                ("refinements", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_rel_residual", ctypes.c_double), ("time_solve_ms", ctypes.c_double),
+                ("time_lambda_ms", ctypes.c_double), ("time_alpha_ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcclr.so (raises if absent: the product path has no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libcclr.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, D, I, S = ctypes.c_void_p, ctypes.c_double, ctypes.c_int, ctypes.c_size_t
+    sig = {
+        "cc_lr_init": [ctypes.POINTER(ctypes.c_void_p), I, I, I, P, P, P, P, P, P, P, I, S, I, P],
+        "cc_lr_sigma": [P, I, P, P, P, P],
+        "cc_lr_sigma_T": [P, I, P, P, P, P],
+        "cc_lr_xi": [P, I, P, P],
+        "cc_lr_solve_x": [P, D, I, D, I, P, P, ctypes.POINTER(cclr_stats)],
+        "cc_lr_solve": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
+        "cc_lr_lambda": [P, D, P, P],
+        "cc_lr_get_t": [P, P, P],
+        "cc_lr_set_precision": [P, I],
+        "cc_lr_last_timings": [P, P],
+        "cc_lr_free": [P],
+        "cc_lr_strerror": [I],
+        "cc_lr_last_error": [],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = I
+    lib.cc_lr_free.restype = None
+    lib.cc_lr_strerror.restype = ctypes.c_char_p
+    lib.cc_lr_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status, allow=()):
+    if status != CCLR_OK and status not in allow:
+        msg = load().cc_lr_last_error().decode()
+        raise CclrError(status, msg)
+    return status
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return a.data_ptr()   # torch tensor
+
+
+def _c128(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.complex128)
+
+
+class Context:
+    """Owning wrapper around a cclr_ctx (host numpy arrays unless device=True)."""
+
+    def __init__(self, o, v, naux, eps, L, mu, t1=None, t2=None, lam1=None, lam2=None,
+                 prec="fp64", hbm_budget=0, device=False, stream=None):
+        lib = load()
+        self.o, self.v, self.naux = o, v, naux
+        self.device = device
+        if device:
+            arrs = [eps, L, mu, t1, t2, lam1, lam2]
+            self._keep = arrs
+            ptrs = [_ptr(a) for a in arrs]
+        else:
+            eps = np.ascontiguousarray(eps, dtype=np.float64)
+            arrs = [eps, _c128(L), _c128(mu), _c128(t1), _c128(t2), _c128(lam1), _c128(lam2)]
+            self._keep = arrs
+            ptrs = [_ptr(a) for a in arrs]
+        h = ctypes.c_void_p()
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        _check(lib.cc_lr_init(ctypes.byref(h), o, v, naux, *ptrs, p, int(hbm_budget),
+                              1 if device else 0, stream))
+        self._h = h
+        self._keep = None
+
+    # -- helpers
+    def _out(self, shape):
+        if self.device:
+            import torch
+            return torch.empty(shape, dtype=torch.complex128, device="cuda")
+        return np.empty(shape, dtype=np.complex128)
+
+    def _in(self, a):
+        return a if self.device else _c128(a)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cc_lr_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- entry points
+    def cc_lr_sigma(self, x1, x2, transpose=False):
+        o, v = self.o, self.v
+        x1, x2 = self._in(x1), self._in(x2)
+        batched = x1.ndim == 3
+        nr = x1.shape[0] if batched else 1
+        s1 = self._out(tuple(x1.shape))
+        s2 = self._out(tuple(x2.shape))
+        fn = load().cc_lr_sigma_T if transpose else load().cc_lr_sigma
+        _check(fn(self._h, nr, _ptr(x1), _ptr(x2), _ptr(s1), _ptr(s2)))
+        return s1, s2
+
+    def cc_lr_sigma_T(self, y1, y2):
+        return self.cc_lr_sigma(y1, y2, transpose=True)
+
+    def cc_lr_xi(self, comp):
+        o, v = self.o, self.v
+        x1 = self._out((o, v))
+        x2 = self._out((o, o, v, v))
+        _check(load().cc_lr_xi(self._h, comp, _ptr(x1), _ptr(x2)))
+        return x1, x2
+
+    def cc_lr_solve_x(self, omega, comp, tol=1e-10, diis_depth=8, allow_noconv=False):
+        o, v = self.o, self.v
+        x1 = self._out((o, v))
+        x2 = self._out((o, o, v, v))
+        st = cclr_stats()
+        _check(load().cc_lr_solve_x(self._h, float(omega), comp, float(tol), diis_depth,
+                                    _ptr(x1), _ptr(x2), ctypes.byref(st)),
+               allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        return x1, x2, st.as_dict()
+
+    def cc_lr_solve(self, omegas, comps=(0, 1, 2), tol=1e-10, diis_depth=8, allow_noconv=False):
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        cp = np.ascontiguousarray(comps, dtype=np.int32)
+        out = np.zeros((len(om), len(cp), len(cp)), dtype=np.complex128)
+        st = cclr_stats()
+        status = _check(load().cc_lr_solve(self._h, len(om), _ptr(om), len(cp), _ptr(cp), float(tol),
+                                           diis_depth, _ptr(out), ctypes.byref(st)),
+                        allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["status"] = status
+        return out, d
+
+    def cc_lr_lambda(self, tol=1e-10):
+        o, v = self.o, self.v
+        l1 = self._out((o, v))
+        l2 = self._out((o, o, v, v))
+        _check(load().cc_lr_lambda(self._h, float(tol), _ptr(l1), _ptr(l2)))
+        return l1, l2
+
+    def cc_lr_get_t(self):
+        o, v = self.o, self.v
+        t1 = self._out((o, v))
+        t2 = self._out((o, o, v, v))
+        _check(load().cc_lr_get_t(self._h, _ptr(t1), _ptr(t2)))
+        return t1, t2
+
+    def cc_lr_set_precision(self, prec):
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        _check(load().cc_lr_set_precision(self._h, p))
+
+    def cc_lr_last_timings(self):
+        out = np.zeros(3, dtype=np.float64)
+        _check(load().cc_lr_last_timings(self._h, _ptr(out)))
+        return out
+
+
+def cc_lr_strerror(status: int) -> str:
+    return load().cc_lr_strerror(status).decode()

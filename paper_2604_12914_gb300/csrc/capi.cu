@@ -1,0 +1,546 @@
+// C ABI of libcclr (declared in include/cclr.h): context life cycle, sigma / sigma^T, the
+// preconditioned DIIS linear solver in FP64, the ground-state Lambda, and alpha(omega).
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+
+#include "../../include/cclr.h"
+#include "model.cuh"
+
+using namespace cclr;
+using zd = std::complex<double>;
+
+namespace {
+thread_local std::string g_last_error = "";
+
+int fail(int status, const std::string &msg) {
+  g_last_error = msg;
+  return status;
+}
+
+// Amplitude vector: singles [o][v] then doubles [o][o][v][v], complex128, contiguous.
+struct AVec {
+  DevBuf b;
+  void *p1() const { return b.p; }
+  void *p2(int64_t n1) const { return (char *)b.p + n1 * 16; }
+};
+}  // namespace
+
+struct cclr_ctx {
+  std::unique_ptr<Model> M;
+  int o = 0, v = 0, naux = 0;
+  int64_t n1 = 0, n2 = 0;
+  int device_ptrs = 0;
+  cudaStream_t st = nullptr;
+  size_t budget = 0;
+  bool have_lambda = false;
+  AVec lam;
+  AVec stage_in, stage_out;       // host <-> device staging (complex128)
+  DevBuf x64, s64;                // complex64 copies for mixed precision sigma
+  CstSet shift;                   // intermediates at shifted amplitudes (F X stencils)
+  int sigma_calls = 0;
+
+  int64_t ntot() const { return n1 + n2; }
+
+  void alloc_vec(AVec &v_) { if (!v_.b.p) v_.b.alloc((size_t)ntot() * 16); }
+
+  // weighted dot: sum_ia conj?(a) b + 1/4 sum_ijab conj?(a) b, FP64 accumulation
+  zd dot(const void *a, const void *b, int herm) {
+    double2 *part = M->E.dot_scratch();
+    double2 *res = M->E.dot_results();
+    vec_dot(C128, n1, a, b, herm, part, res, 0, st);
+    vec_dot(C128, n2, (const char *)a + n1 * 16, (const char *)b + n1 * 16, herm, part, res, 1, st);
+    double2 h[2];
+    CCLR_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return zd(h[0].x, h[0].y) + 0.25 * zd(h[1].x, h[1].y);
+  }
+  double norm(const void *a) { return std::sqrt(std::max(0.0, dot(a, a, 1).real())); }
+  void axpy(zd a, const void *x, void *y) { vec_axpy(C128, ntot(), zc(a.real(), a.imag()), x, y, st); }
+  void copy(const void *x, void *y) { CCLR_CUDA(cudaMemcpyAsync(y, x, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st)); }
+  void scal(zd a, void *y) { vec_scal(C128, ntot(), zc(a.real(), a.imag()), y, st); }
+  void precond(double omega, const void *r, void *out) {
+    vec_precond(C128, n1, M->D1.as<double>(), omega, r, out, st);
+    vec_precond(C128, n2, M->D2.as<double>(), omega, (const char *)r + n1 * 16, (char *)out + n1 * 16, st);
+  }
+
+  // s = A x (dir +1) or x A (dir -1) in the current precision; x, s complex128 amplitude vectors
+  void op(int dir, const void *x, void *s, const CstSet *set = nullptr) {
+    ++sigma_calls;
+    const int prec = M->prec;
+    if (set == nullptr) set = &M->cst_for(prec);
+    if (set->dt == C128) {
+      M->apply(dir, *set, x, (const char *)x + n1 * 16, s, (char *)s + n1 * 16);
+      return;
+    }
+    if (!x64.p) { x64.alloc((size_t)ntot() * 8); s64.alloc((size_t)ntot() * 8); }
+    Tens xi = make_tens((void *)x, C128, {ntot()}), xo = make_tens(x64.p, C64, {ntot()});
+    M->E.permute(zc(1), xi, "a", xo, "a", false);
+    M->apply(dir, *set, x64.p, (char *)x64.p + n1 * 8, s64.p, (char *)s64.p + n1 * 8);
+    Tens si = make_tens(s64.p, C64, {ntot()}), so = make_tens(s, C128, {ntot()});
+    M->E.permute(zc(1), si, "a", so, "a", false);
+  }
+
+  // Solve (Op - omega) x = b with the diagonal preconditioner (D - omega) and DIIS.
+  // Returns relative residual; iterations added to *its.
+  double solve(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+               int *its) {
+    depth = std::max(2, std::min(depth, 16));
+    std::vector<AVec> X(depth), Er(depth);
+    for (auto &a : X) alloc_vec(a);
+    for (auto &a : Er) alloc_vec(a);
+    AVec s, r;
+    alloc_vec(s);
+    alloc_vec(r);
+    const double bn = std::max(norm(b), 1e-300);
+    precond(omega, b, x);
+    std::vector<zd> B((size_t)depth * depth);
+    int nh = 0, head = 0;
+    double rel = 1e300;
+    for (int it = 0; it < maxit; ++it) {
+      op(dir, x, s.b.p);
+      copy(b, r.b.p);
+      axpy(zd(-1), s.b.p, r.b.p);
+      axpy(zd(omega), x, r.b.p);
+      rel = norm(r.b.p) / bn;
+      if (its) ++*its;
+      if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
+      if (rel < tol) break;
+      int k = head;
+      head = (head + 1) % depth;
+      nh = std::min(nh + 1, depth);
+      precond(omega, r.b.p, Er[k].b.p);
+      copy(x, X[k].b.p);
+      axpy(zd(1), Er[k].b.p, X[k].b.p);
+      for (int l = 0; l < depth; ++l) {
+        if (!(nh == depth || l < nh)) continue;  // slot not filled yet
+        zd d = dot(Er[k].b.p, Er[l].b.p, 1);
+        B[(size_t)k * depth + l] = d;
+        B[(size_t)l * depth + k] = std::conj(d);
+      }
+      if (nh < 2) {
+        copy(X[k].b.p, x);
+        continue;
+      }
+      // slots in use: if nh < depth they are 0..nh-1, else all
+      std::vector<int> idx;
+      for (int l = 0; l < depth; ++l)
+        if (nh == depth || l < nh) idx.push_back(l);
+      int m = (int)idx.size();
+      double sc = 0.0;
+      for (int a : idx) sc = std::max(sc, std::abs(B[(size_t)a * depth + a]));
+      if (sc <= 0) sc = 1.0;
+      std::vector<zd> Am((size_t)(m + 1) * (m + 1)), rhs(m + 1, 0.0);
+      for (int a = 0; a < m; ++a) {
+        for (int c = 0; c < m; ++c) Am[(size_t)a * (m + 1) + c] = B[(size_t)idx[a] * depth + idx[c]] / sc;
+        Am[(size_t)a * (m + 1) + m] = 1.0;
+        Am[(size_t)m * (m + 1) + a] = 1.0;
+      }
+      Am[(size_t)m * (m + 1) + m] = 0.0;
+      rhs[m] = 1.0;
+      std::vector<zd> c = solve_small(Am, rhs, m + 1);
+      CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
+      for (int a = 0; a < m; ++a) axpy(c[a], X[idx[a]].b.p, x);
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return rel;
+  }
+
+  static std::vector<zd> solve_small(std::vector<zd> A, std::vector<zd> b, int N) {
+    for (int c = 0; c < N; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < N; ++r)
+        if (std::abs(A[(size_t)r * N + c]) > std::abs(A[(size_t)piv * N + c])) piv = r;
+      if (piv != c) {
+        for (int k = 0; k < N; ++k) std::swap(A[(size_t)c * N + k], A[(size_t)piv * N + k]);
+        std::swap(b[c], b[piv]);
+      }
+      zd d = A[(size_t)c * N + c];
+      if (std::abs(d) < 1e-300) d = 1e-300;
+      for (int r = c + 1; r < N; ++r) {
+        zd f = A[(size_t)r * N + c] / d;
+        for (int k = c; k < N; ++k) A[(size_t)r * N + k] -= f * A[(size_t)c * N + k];
+        b[r] -= f * b[c];
+      }
+    }
+    std::vector<zd> x(N);
+    for (int r = N - 1; r >= 0; --r) {
+      zd s = b[r];
+      for (int k = r + 1; k < N; ++k) s -= A[(size_t)r * N + k] * x[k];
+      zd d = A[(size_t)r * N + r];
+      if (std::abs(d) < 1e-300) d = 1e-300;
+      x[r] = s / d;
+    }
+    return x;
+  }
+
+  void xi_vec(int comp, const void *t1d, const void *t2d, void *out) {
+    const int64_t nn = (int64_t)M->n * M->n;
+    M->xi((char *)M->mu.p + (size_t)comp * nn * 16, t1d, t2d, out, (char *)out + n1 * 16);
+  }
+
+  // eta0 = dE/dT = [ sum_jb <ij||ab> t_jb ; <ij||ab> ] (canonical Fock: f_ia = 0)
+  void eta0(void *out) {
+    const CstSet &C = M->c128;
+    Tens e1 = make_tens(out, C128, {o, v});
+    Tens e2 = make_tens((char *)out + n1 * 16, C128, {o, o, v, v});
+    M->E.zero(e1);
+    M->E.contract(zc(1), C.t[K_OOVV], "ijab", make_tens(M->t1.p, C128, {o, v}), "jb", e1, "ia");
+    M->E.permute(zc(1), C.t[K_OOVV], "ijab", e2, "ijab", false);
+    // f_ia of diag(eps) is zero; the one-body h keeps any ov part of the input Fock
+  }
+
+  void ensure_lambda(double tol, int depth, cclr_stats *stats) {
+    if (have_lambda) return;
+    auto t0 = std::chrono::steady_clock::now();
+    alloc_vec(lam);
+    AVec b;
+    alloc_vec(b);
+    eta0(b.b.p);
+    scal(zd(-1), b.b.p);
+    int its = 0;
+    double rel = solve(-1, 0.0, b.b.p, lam.b.p, tol, depth, 200, &its);
+    if (stats) {
+      stats->iterations += its;
+      stats->time_lambda_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      stats->max_rel_residual = std::max(stats->max_rel_residual, rel);
+      if (rel >= tol) stats->converged = 0;
+    }
+    have_lambda = true;
+  }
+
+  // step length for the polynomial-exact stencils
+  double step(const void *x) {
+    double nx = norm(x);
+    double nt = tnorm();  // ||T|| over unique amplitudes
+    return std::max(nt, 1e-2) / std::max(nx, 1e-300) * 0.25;
+  }
+  double tnorm() {
+    // t1, t2 are separate buffers: assemble weighted norm
+    double2 *part = M->E.dot_scratch();
+    double2 *res = M->E.dot_results();
+    vec_dot(C128, n1, M->t1.p, M->t1.p, 1, part, res, 0, st);
+    vec_dot(C128, n2, M->t2.p, M->t2.p, 1, part, res, 1, st);
+    double2 h[2];
+    CCLR_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return std::sqrt(h[0].x + 0.25 * h[1].x);
+  }
+
+  // shifted amplitudes T + k h X into (t1s, t2s)
+  void shifted(const void *x, double kh, AVec &ts) {
+    alloc_vec(ts);
+    CCLR_CUDA(cudaMemcpyAsync(ts.p1(), M->t1.p, (size_t)n1 * 16, cudaMemcpyDeviceToDevice, st));
+    CCLR_CUDA(cudaMemcpyAsync(ts.p2(n1), M->t2.p, (size_t)n2 * 16, cudaMemcpyDeviceToDevice, st));
+    axpy(zd(kh), x, ts.b.p);
+  }
+
+  // eta^A . X = sum_ia mu^A_ia X_ia + d/de lambda . xi^A(T + eX)   (4-point stencil)
+  zd eta_dot(int comp, const void *x) {
+    const int64_t nn = (int64_t)M->n * M->n;
+    Tens muA = make_tens((char *)M->mu.p + (size_t)comp * nn * 16, C128, {M->n, M->n});
+    // sum_ia mu_ia X_ia
+    DevBuf mov((size_t)n1 * 16);
+    Tens mo = make_tens(mov.p, C128, {o, v});
+    M->E.permute(zc(1), muA.slice(0, 0, o).slice(1, o, M->n), "ia", mo, "ia", false);
+    double2 *part = M->E.dot_scratch();
+    double2 *res = M->E.dot_results();
+    vec_dot(C128, n1, mov.p, x, 0, part, res, 0, st);
+    double2 hv;
+    CCLR_CUDA(cudaMemcpyAsync(&hv, res, sizeof(hv), cudaMemcpyDeviceToHost, st));
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    zd val(hv.x, hv.y);
+    const double h = step(x);
+    static const double cs[4] = {-1, 8, -8, 1}, ks[4] = {2, 1, -1, -2};
+    AVec ts, xv;
+    alloc_vec(xv);
+    zd acc = 0.0;
+    for (int s = 0; s < 4; ++s) {
+      shifted(x, ks[s] * h, ts);
+      xi_vec(comp, ts.p1(), ts.p2(n1), xv.b.p);
+      acc += cs[s] * dot(lam.b.p, xv.b.p, 0);
+    }
+    return val + acc / (12.0 * h);
+  }
+
+  // F X = d/de [ lambda A(T + eX) + eta0(T + eX) ]  (4-point stencil over rebuilt H-bar)
+  void fx(const void *x, void *out) {
+    const double h = step(x);
+    static const double cs[4] = {-1, 8, -8, 1}, ks[4] = {2, 1, -1, -2};
+    AVec ts, sv;
+    alloc_vec(sv);
+    CCLR_CUDA(cudaMemsetAsync(out, 0, (size_t)ntot() * 16, st));
+    for (int s = 0; s < 4; ++s) {
+      shifted(x, ks[s] * h, ts);
+      M->build_set(ts.p1(), ts.p2(n1), shift);
+      op(-1, lam.b.p, sv.b.p, &shift);
+      axpy(zd(cs[s] / (12.0 * h)), sv.b.p, out);
+    }
+    // d eta0 / dT along X: sum_jb <ij||ab> X_jb (singles only)
+    Tens o1 = make_tens(out, C128, {o, v});
+    M->E.contract(zc(1), M->c128.t[K_OOVV], "ijab", make_tens((void *)x, C128, {o, v}), "jb", o1, "ia");
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+};
+
+namespace {
+template <typename F> int guarded(F &&f) {
+  try {
+    f();
+    return CCLR_OK;
+  } catch (const Error &e) {
+    return fail(e.status, e.what());
+  } catch (const std::exception &e) {
+    return fail(CCLR_EDEVICE, e.what());
+  }
+}
+
+void to_dev(cclr_ctx *c, const double *src, void *dst, size_t bytes) {
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, c->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+}
+void from_dev(cclr_ctx *c, const void *src, double *dst, size_t bytes) {
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, c->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+}
+}  // namespace
+
+extern "C" {
+
+cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps, const double *L,
+                       const double *mu, const double *t1, const double *t2, const double *lam1,
+                       const double *lam2, int prec, size_t hbm_budget_bytes, int device_ptrs,
+                       void *cuda_stream) {
+  if (!ctx) return (cclr_status)fail(CCLR_EINVAL, "ctx is NULL");
+  *ctx = nullptr;
+  if (o < 1 || v < 1 || naux < 1) return (cclr_status)fail(CCLR_EINVAL, "o, v and naux must be >= 1");
+  if (!eps || !L || !mu) return (cclr_status)fail(CCLR_EINVAL, "eps, L and mu are required");
+  if (prec < 0 || prec > 3) return (cclr_status)fail(CCLR_EINVAL, "unknown precision mode");
+  if ((lam1 == nullptr) != (lam2 == nullptr)) return (cclr_status)fail(CCLR_EINVAL, "lam1 and lam2 must both be given or both be NULL");
+  auto c = new cclr_ctx();
+  int st = guarded([&] {
+    c->o = o; c->v = v; c->naux = naux;
+    c->n1 = (int64_t)o * v;
+    c->n2 = (int64_t)o * o * v * v;
+    c->device_ptrs = device_ptrs;
+    c->st = (cudaStream_t)cuda_stream;
+    c->budget = hbm_budget_bytes;
+    int dev = 0;
+    CCLR_CUDA(cudaGetDevice(&dev));
+    c->M.reset(new Model(o, v, naux, c->st));
+    c->M->prec = prec;
+    c->M->upload_inputs(eps, L, mu, t1, t2, device_ptrs);
+    c->M->build_set(c->M->t1.p, c->M->t2.p, c->M->c128);
+    c->M->build_diagonal();
+    if (prec != CCLR_FP64) c->M->cst_for(prec);
+    if (lam1) {
+      c->alloc_vec(c->lam);
+      to_dev(c, lam1, c->lam.p1(), (size_t)c->n1 * 16);
+      to_dev(c, lam2, c->lam.p2(c->n1), (size_t)c->n2 * 16);
+      c->have_lambda = true;
+    }
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+    if (c->budget && device_bytes_in_use() > c->budget)
+      throw Error(CCLR_ENOMEM, "HBM budget exceeded: " + std::to_string(device_bytes_in_use()) + " bytes in use");
+  });
+  if (st != CCLR_OK) {
+    delete c;
+    return (cclr_status)st;
+  }
+  *ctx = c;
+  return CCLR_OK;
+}
+
+static cclr_status sigma_common(cclr_ctx *c, int dir, int nrhs, const double *x1, const double *x2,
+                                double *s1, double *s2) {
+  if (!c || nrhs < 0 || (nrhs > 0 && (!x1 || !x2 || !s1 || !s2)))
+    return (cclr_status)fail(CCLR_EINVAL, "bad sigma arguments");
+  return (cclr_status)guarded([&] {
+    c->alloc_vec(c->stage_in);
+    c->alloc_vec(c->stage_out);
+    for (int r = 0; r < nrhs; ++r) {
+      to_dev(c, x1 + (size_t)r * c->n1 * 2, c->stage_in.p1(), (size_t)c->n1 * 16);
+      to_dev(c, x2 + (size_t)r * c->n2 * 2, c->stage_in.p2(c->n1), (size_t)c->n2 * 16);
+      c->op(dir, c->stage_in.b.p, c->stage_out.b.p);
+      from_dev(c, c->stage_out.p1(), s1 + (size_t)r * c->n1 * 2, (size_t)c->n1 * 16);
+      from_dev(c, c->stage_out.p2(c->n1), s2 + (size_t)r * c->n2 * 2, (size_t)c->n2 * 16);
+    }
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
+}
+
+cclr_status cc_lr_sigma(cclr_ctx *c, int nrhs, const double *x1, const double *x2, double *s1, double *s2) {
+  return sigma_common(c, +1, nrhs, x1, x2, s1, s2);
+}
+
+cclr_status cc_lr_sigma_T(cclr_ctx *c, int nrhs, const double *y1, const double *y2, double *s1, double *s2) {
+  return sigma_common(c, -1, nrhs, y1, y2, s1, s2);
+}
+
+cclr_status cc_lr_xi(cclr_ctx *c, int comp, double *xi1, double *xi2) {
+  if (!c || comp < 0 || comp > 2 || !xi1 || !xi2) return (cclr_status)fail(CCLR_EINVAL, "bad xi arguments");
+  return (cclr_status)guarded([&] {
+    c->alloc_vec(c->stage_out);
+    c->xi_vec(comp, c->M->t1.p, c->M->t2.p, c->stage_out.b.p);
+    from_dev(c, c->stage_out.p1(), xi1, (size_t)c->n1 * 16);
+    from_dev(c, c->stage_out.p2(c->n1), xi2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
+}
+
+cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int diis_depth,
+                          double *x1, double *x2, cclr_stats *stats) {
+  if (!c || comp < 0 || comp > 2 || !x1 || !x2 || !(tol > 0)) return (cclr_status)fail(CCLR_EINVAL, "bad solve_x arguments");
+  double rel = 0;
+  int st = guarded([&] {
+    auto t0 = std::chrono::steady_clock::now();
+    AVec b, x;
+    c->alloc_vec(b);
+    c->alloc_vec(x);
+    c->xi_vec(comp, c->M->t1.p, c->M->t2.p, b.b.p);
+    c->scal(zd(-1), b.b.p);
+    int its = 0;
+    int calls0 = c->sigma_calls;
+    rel = c->solve(+1, omega, b.b.p, x.b.p, tol, diis_depth, 300, &its);
+    from_dev(c, x.p1(), x1, (size_t)c->n1 * 16);
+    from_dev(c, x.p2(c->n1), x2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+    if (stats) {
+      std::memset(stats, 0, sizeof(*stats));
+      stats->iterations = its;
+      stats->sigma_calls = c->sigma_calls - calls0;
+      stats->converged = rel < tol;
+      stats->max_rel_residual = rel;
+      stats->time_solve_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+  });
+  if (st != CCLR_OK) return (cclr_status)st;
+  return rel < tol ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve_x: residual " + std::to_string(rel));
+}
+
+cclr_status cc_lr_lambda(cclr_ctx *c, double tol, double *lam1, double *lam2) {
+  if (!c || !lam1 || !lam2) return (cclr_status)fail(CCLR_EINVAL, "bad lambda arguments");
+  return (cclr_status)guarded([&] {
+    c->ensure_lambda(tol, 8, nullptr);
+    from_dev(c, c->lam.p1(), lam1, (size_t)c->n1 * 16);
+    from_dev(c, c->lam.p2(c->n1), lam2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
+}
+
+cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
+                        double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0))
+    return (cclr_status)fail(CCLR_EINVAL, "bad solve arguments");
+  for (int k = 0; k < ncomp; ++k)
+    if (comps[k] < 0 || comps[k] > 2) return (cclr_status)fail(CCLR_EINVAL, "component out of range");
+  cclr_stats loc;
+  std::memset(&loc, 0, sizeof(loc));
+  loc.converged = 1;
+  int st = guarded([&] {
+    int calls0 = c->sigma_calls;
+    c->ensure_lambda(tol, diis_depth, &loc);
+    for (int w = 0; w < nomega; ++w) {
+      const double om = omegas[w];
+      const int nsign = om == 0.0 ? 1 : 2;
+      // X^C(s*omega) for every component and sign
+      std::vector<AVec> X((size_t)ncomp * 2);
+      auto t0 = std::chrono::steady_clock::now();
+      for (int a = 0; a < ncomp; ++a) {
+        AVec b;
+        c->alloc_vec(b);
+        c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, b.b.p);
+        c->scal(zd(-1), b.b.p);
+        for (int s = 0; s < nsign; ++s) {
+          AVec &x = X[(size_t)a * 2 + s];
+          c->alloc_vec(x);
+          int its = 0;
+          double rel = c->solve(+1, s == 0 ? om : -om, b.b.p, x.b.p, tol, diis_depth, 300, &its);
+          loc.iterations += its;
+          loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
+          if (!(rel < tol)) loc.converged = 0;
+        }
+      }
+      auto t1 = std::chrono::steady_clock::now();
+      loc.time_solve_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+      auto Xs = [&](int a, int s) -> AVec & { return X[(size_t)a * 2 + (nsign == 1 ? 0 : s)]; };
+      // eta^A . X^B(s w) and F X^A(s w)
+      std::vector<zd> ED((size_t)ncomp * ncomp * 2);
+      for (int a = 0; a < ncomp; ++a)
+        for (int b = 0; b < ncomp; ++b)
+          for (int s = 0; s < nsign; ++s) ED[((size_t)a * ncomp + b) * 2 + s] = c->eta_dot(comps[a], Xs(b, s).b.p);
+      std::vector<AVec> FX((size_t)ncomp * 2);
+      for (int a = 0; a < ncomp; ++a)
+        for (int s = 0; s < nsign; ++s) {
+          c->alloc_vec(FX[(size_t)a * 2 + s]);
+          c->fx(Xs(a, s).b.p, FX[(size_t)a * 2 + s].b.p);
+        }
+      auto FXs = [&](int a, int s) -> AVec & { return FX[(size_t)a * 2 + (nsign == 1 ? 0 : s)]; };
+      auto EDs = [&](int a, int b, int s) { return ED[((size_t)a * ncomp + b) * 2 + (nsign == 1 ? 0 : s)]; };
+      for (int a = 0; a < ncomp; ++a)
+        for (int b = 0; b < ncomp; ++b) {
+          // g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w)
+          zd gp = EDs(a, b, 0) + EDs(b, a, 1) + c->dot(FXs(a, 1).b.p, Xs(b, 0).b.p, 0);
+          zd gm = EDs(a, b, 1) + EDs(b, a, 0) + c->dot(FXs(a, 0).b.p, Xs(b, 1).b.p, 0);
+          zd al = -0.5 * (gp + std::conj(gm));
+          size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
+          alpha[k] = al.real();
+          alpha[k + 1] = al.imag();
+        }
+      loc.time_alpha_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    }
+    loc.sigma_calls = c->sigma_calls - calls0;
+  });
+  if (stats) *stats = loc;
+  if (st != CCLR_OK) return (cclr_status)st;
+  return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve: tolerance not met");
+}
+
+cclr_status cc_lr_get_t(cclr_ctx *c, double *t1, double *t2) {
+  if (!c || !t1 || !t2) return (cclr_status)fail(CCLR_EINVAL, "bad get_t arguments");
+  return (cclr_status)guarded([&] {
+    from_dev(c, c->M->t1.p, t1, (size_t)c->n1 * 16);
+    from_dev(c, c->M->t2.p, t2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
+}
+
+cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
+  if (!c || prec < 0 || prec > 3) return (cclr_status)fail(CCLR_EINVAL, "bad precision");
+  return (cclr_status)guarded([&] {
+    c->M->prec = prec;
+    if (prec != CCLR_FP64) c->M->cst_for(prec);
+  });
+}
+
+cclr_status cc_lr_last_timings(cclr_ctx *c, double *ms3) {
+  if (!c || !ms3) return (cclr_status)fail(CCLR_EINVAL, "bad timings arguments");
+  for (int k = 0; k < 3; ++k) ms3[k] = c->M->ms_last[k];
+  return CCLR_OK;
+}
+
+void cc_lr_free(cclr_ctx *c) {
+  if (!c) return;
+  try {
+    if (c->st) cudaStreamSynchronize(c->st);
+  } catch (...) {
+  }
+  delete c;
+}
+
+const char *cc_lr_strerror(cclr_status s) {
+  switch (s) {
+    case CCLR_OK: return "success";
+    case CCLR_EINVAL: return "invalid argument";
+    case CCLR_ENOMEM: return "out of device memory or HBM budget exceeded";
+    case CCLR_ENOCONV: return "solver did not converge";
+    case CCLR_EDEVICE: return "CUDA device error";
+    case CCLR_ETIMEOUT: return "bounded device wait timed out";
+    case CCLR_EUNSUPPORTED: return "unsupported on this device or build";
+  }
+  return "unknown status";
+}
+
+const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

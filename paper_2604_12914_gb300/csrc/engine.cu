@@ -1,0 +1,220 @@
+// Contraction engine: classifies the modes of C += A*B into batch / M / N / K groups,
+// views each operand as a strided batched matrix when its modes merge, and permutes it
+// into a contiguous scratch layout otherwise.
+#include <atomic>
+
+#include "engine.cuh"
+
+namespace cclr {
+
+static std::atomic<size_t> g_bytes_in_use{0};
+
+size_t device_bytes_in_use() { return g_bytes_in_use.load(); }
+
+void DevBuf::alloc(size_t b) {
+  release();
+  if (b == 0) return;
+  cudaError_t e = cudaMalloc(&p, b);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    (void)cudaGetLastError();
+    throw Error(2, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+  }
+  bytes = b;
+  g_bytes_in_use += b;
+}
+
+void DevBuf::release() {
+  if (p) {
+    cudaFree(p);
+    g_bytes_in_use -= bytes;
+  }
+  p = nullptr;
+  bytes = 0;
+}
+
+void *Engine::ws(int slot, size_t bytes) {
+  if ((int)slots_.size() <= slot) slots_.resize(slot + 1);
+  if (slots_[slot].bytes < bytes) {
+    if (slots_[slot].p) CCLR_CUDA(cudaStreamSynchronize(st));
+    slots_[slot].alloc(bytes + bytes / 8);
+  }
+  return slots_[slot].p;
+}
+
+double2 *Engine::dot_scratch() {
+  if (!dots_.p) dots_.alloc(sizeof(double2) * (512 + 64));
+  return dots_.as<double2>();
+}
+double2 *Engine::dot_results() { return dot_scratch() + 512; }
+
+static int mode_pos(const std::string &m, char c) {
+  auto k = m.find(c);
+  return k == std::string::npos ? -1 : (int)k;
+}
+
+// View the modes `group` (outer to inner) of tensor t as one index with a single stride.
+static bool group_view(const Tens &t, const std::string &modes, const std::string &group,
+                       int64_t &size, int64_t &stride) {
+  size = 1;
+  stride = 0;
+  int64_t expect = -1;
+  for (int g = (int)group.size() - 1; g >= 0; --g) {
+    int pos = mode_pos(modes, group[g]);
+    int64_t d = t.dim[pos], s = t.str[pos];
+    if (d == 1) continue;
+    if (expect < 0) stride = s;
+    else if (s != expect) return false;
+    expect = s * d;
+    size *= d;
+  }
+  return true;
+}
+
+static int64_t prod_dims(const Tens &t, const std::string &modes, const std::string &group) {
+  int64_t p = 1;
+  for (char c : group) p *= t.dim[mode_pos(modes, c)];
+  return p;
+}
+
+static Tens contiguous_like(void *p, int dt, const Tens &src, const std::string &smodes,
+                            const std::string &order) {
+  Tens t;
+  t.p = p;
+  t.dt = dt;
+  t.rank = (int)order.size();
+  for (int i = 0; i < t.rank; ++i) t.dim[i] = src.dim[mode_pos(smodes, order[i])];
+  int64_t s = 1;
+  for (int i = t.rank - 1; i >= 0; --i) {
+    t.str[i] = s;
+    s *= t.dim[i];
+  }
+  return t;
+}
+
+void Engine::permute(zc alpha, const Tens &in, const std::string &mi, const Tens &out,
+                     const std::string &mo, bool acc) {
+  CCLR_REQUIRE((int)mi.size() == in.rank && (int)mo.size() == out.rank && in.rank == out.rank,
+               "permute: rank / mode mismatch " + mi + " -> " + mo);
+  PermArgs a;
+  a.in = in.p;
+  a.out = out.p;
+  a.alr = alpha.re;
+  a.ali = alpha.im;
+  a.acc = acc ? 1 : 0;
+  // drop unit modes, keep output order
+  int r = 0;
+  a.total = 1;
+  for (int d = 0; d < out.rank; ++d) {
+    int pi = mode_pos(mi, mo[d]);
+    CCLR_REQUIRE(pi >= 0, "permute: mode missing in input");
+    CCLR_REQUIRE(in.dim[pi] == out.dim[d], "permute: dimension mismatch for mode " + std::string(1, mo[d]));
+    if (out.dim[d] == 1) continue;
+    a.dim[r] = out.dim[d];
+    a.sout[r] = out.str[d];
+    a.sin[r] = in.str[pi];
+    a.total *= out.dim[d];
+    ++r;
+  }
+  a.rank = r;
+  if (r == 0) {  // scalar
+    a.rank = 1;
+    a.dim[0] = 1;
+    a.sin[0] = a.sout[0] = 0;
+  }
+  for (int d = 0; d < out.rank; ++d)
+    if (out.dim[d] == 0) a.total = 0;
+  launch_permute(a, in.dt, out.dt, st);
+}
+
+void Engine::zero(const Tens &t) {
+  CCLR_REQUIRE(t.contiguous(), "zero: tensor is not contiguous");
+  if (t.numel() > 0) CCLR_CUDA(cudaMemsetAsync(t.p, 0, t.numel() * dt_size(t.dt), st));
+}
+
+void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens &B,
+                      const std::string &mb, const Tens &C, const std::string &mc) {
+  CCLR_REQUIRE((int)ma.size() == A.rank && (int)mb.size() == B.rank && (int)mc.size() == C.rank,
+               "contract: rank / mode mismatch " + ma + "," + mb + "->" + mc);
+  CCLR_REQUIRE(A.dt == B.dt && B.dt == C.dt, "contract: dtype mismatch");
+  const int dt = C.dt;
+  std::string bat, Mm, Nm, Km;
+  for (char c : mc) {
+    int pa = mode_pos(ma, c), pb = mode_pos(mb, c);
+    CCLR_REQUIRE(pa >= 0 || pb >= 0, std::string("contract: output mode only in C: ") + c);
+    if (pa >= 0 && pb >= 0) bat += c;
+    else if (pa >= 0) Mm += c;
+    else Nm += c;
+  }
+  for (char c : ma) {
+    if (mode_pos(mc, c) >= 0) continue;
+    CCLR_REQUIRE(mode_pos(mb, c) >= 0, std::string("contract: mode only in A: ") + c);
+    Km += c;
+  }
+  for (char c : mb)
+    CCLR_REQUIRE(mode_pos(mc, c) >= 0 || mode_pos(ma, c) >= 0, std::string("contract: mode only in B: ") + c);
+  for (char c : ma) {
+    int pb = mode_pos(mb, c), pc = mode_pos(mc, c), pa = mode_pos(ma, c);
+    if (pb >= 0) CCLR_REQUIRE(A.dim[pa] == B.dim[pb], std::string("contract: dim mismatch A/B for ") + c);
+    if (pc >= 0) CCLR_REQUIRE(A.dim[pa] == C.dim[pc], std::string("contract: dim mismatch A/C for ") + c);
+  }
+  for (char c : mb) {
+    int pc = mode_pos(mc, c), pb = mode_pos(mb, c);
+    if (pc >= 0) CCLR_REQUIRE(B.dim[pb] == C.dim[pc], std::string("contract: dim mismatch B/C for ") + c);
+  }
+  const int64_t nb = prod_dims(C, mc, bat), M = prod_dims(C, mc, Mm), N = prod_dims(C, mc, Nm);
+  const int64_t K = prod_dims(A, ma, Km);
+  if (nb == 0 || M == 0 || N == 0) return;
+  if (K == 0) return;
+  const size_t es = dt_size(dt);
+
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K; g.batch = nb;
+  g.alr = alpha.re; g.ali = alpha.im;
+  // A as [batch][M][K]
+  {
+    int64_t s0, s1, s2, z;
+    bool ok = group_view(A, ma, bat, z, s0) && group_view(A, ma, Mm, z, s1) &&
+              group_view(A, ma, Km, z, s2);
+    ok = ok && (M == 1 || K == 1 || s1 == 1 || s2 == 1);
+    if (ok) {
+      g.A = A.p; g.sAb = s0; g.sAm = s1; g.sAk = s2;
+    } else {
+      std::string order = bat + Mm + Km;
+      Tens T = contiguous_like(ws(0, nb * M * K * es), dt, A, ma, order);
+      permute(zc(1.0), A, ma, T, order, false);
+      g.A = T.p; g.sAb = M * K; g.sAm = K; g.sAk = 1;
+    }
+  }
+  // B as [batch][K][N]
+  {
+    int64_t s0, s1, s2, z;
+    bool ok = group_view(B, mb, bat, z, s0) && group_view(B, mb, Km, z, s1) &&
+              group_view(B, mb, Nm, z, s2);
+    ok = ok && (K == 1 || N == 1 || s1 == 1 || s2 == 1);
+    if (ok) {
+      g.B = B.p; g.sBb = s0; g.sBk = s1; g.sBn = s2;
+    } else {
+      std::string order = bat + Km + Nm;
+      Tens T = contiguous_like(ws(1, nb * K * N * es), dt, B, mb, order);
+      permute(zc(1.0), B, mb, T, order, false);
+      g.B = T.p; g.sBb = K * N; g.sBk = N; g.sBn = 1;
+    }
+  }
+  // C as [batch][M][N]
+  int64_t s0, s1, s2, z;
+  bool ok = group_view(C, mc, bat, z, s0) && group_view(C, mc, Mm, z, s1) &&
+            group_view(C, mc, Nm, z, s2);
+  if (ok) {
+    g.C = C.p; g.sCb = s0; g.sCm = s1; g.sCn = s2; g.overwrite = 0;
+    launch_gemm(g, dt, st);
+  } else {
+    std::string order = bat + Mm + Nm;
+    Tens T = contiguous_like(ws(2, nb * M * N * es), dt, C, mc, order);
+    g.C = T.p; g.sCb = M * N; g.sCm = N; g.sCn = 1; g.overwrite = 1;
+    launch_gemm(g, dt, st);
+    permute(zc(1.0), T, order, C, mc, true);
+  }
+}
+
+}  // namespace cclr

@@ -1,0 +1,53 @@
+// Host-side tensor-contraction engine: device buffers, workspace, einsum-style
+// contractions mapped onto the strided complex GEMM, permutes and vector helpers.
+#pragma once
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace cclr {
+
+// Owning device allocation.
+struct DevBuf {
+  void *p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  explicit DevBuf(size_t b) { alloc(b); }
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf &operator=(DevBuf &&o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void alloc(size_t b);
+  void release();
+  template <typename T> T *as() const { return (T *)p; }
+};
+
+size_t device_bytes_in_use();
+
+class Engine {
+ public:
+  cudaStream_t st = nullptr;
+  // Workspace slot s of at least `bytes` bytes (grown on demand, reused across calls).
+  void *ws(int slot, size_t bytes);
+  // C[mc] += alpha * sum A[ma] B[mb] over the modes not in mc (einsum semantics; every
+  // mode must appear in exactly two operands or in all three).
+  void contract(zc alpha, const Tens &A, const std::string &ma, const Tens &B,
+                const std::string &mb, const Tens &C, const std::string &mc);
+  // out[mo] (+)= alpha * in[mi]  (same mode set; dtypes may differ -> conversion).
+  void permute(zc alpha, const Tens &in, const std::string &mi, const Tens &out,
+               const std::string &mo, bool acc);
+  void zero(const Tens &t);
+  double2 *dot_scratch();  // device: partials [>=304] and results [64]
+  double2 *dot_results();
+
+ private:
+  std::vector<DevBuf> slots_;
+  DevBuf dots_;
+};
+
+}  // namespace cclr

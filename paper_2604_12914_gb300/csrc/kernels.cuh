@@ -1,0 +1,51 @@
+// Declarations of the generic device kernels and their host launchers.
+#pragma once
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace cclr {
+
+struct GemmArgs {
+  const void *A = nullptr;
+  const void *B = nullptr;
+  void *C = nullptr;
+  int64_t M = 0, N = 0, K = 0, batch = 1;
+  int64_t sAb = 0, sAm = 0, sAk = 0;
+  int64_t sBb = 0, sBk = 0, sBn = 0;
+  int64_t sCb = 0, sCm = 0, sCn = 0;
+  double alr = 1.0, ali = 0.0;
+  int overwrite = 0;  // 1: C = alpha A B ; 0: C += alpha A B
+};
+
+struct PermArgs {
+  const void *in = nullptr;
+  void *out = nullptr;
+  int rank = 0;
+  int64_t dim[8] = {0};
+  int64_t sin[8] = {0};
+  int64_t sout[8] = {0};
+  double alr = 1.0, ali = 0.0;
+  int acc = 0;
+  int64_t total = 0;
+};
+
+void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st);
+void launch_permute(const PermArgs &a, int dt_in, int dt_out, cudaStream_t st);
+void vec_axpy(int dt, int64_t n, zc a, const void *x, void *y, cudaStream_t st);
+void vec_scal(int dt, int64_t n, zc a, void *y, cudaStream_t st);
+void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 *part,
+             double2 *out, int slot, cudaStream_t st);
+void vec_precond(int dt, int64_t n, const double *D, double omega, const void *r, void *out,
+                 cudaStream_t st);
+void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2,
+                cudaStream_t st);
+void apply_denominator(int o, int v, const double *eps, void *t2, cudaStream_t st);
+void set_diag(int n, const double *d, void *out, cudaStream_t st);
+
+// Particle-particle ladder on tcgen05 tensor cores (complex64 operands in TF32):
+// out[i,j,a,b] += alpha * sum_{e,f} <ab|ef>~ X[i,j,e,f] with <ab|ef>~ = sum_P L[P,a,e] L[P,b,f].
+struct LadderTC;
+bool ladder_tc_available();
+
+}  // namespace cclr

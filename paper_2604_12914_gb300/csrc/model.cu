@@ -1,0 +1,442 @@
+// Device-side LR-CCSD model: input upload, T1 dressing of the Cholesky vectors, the stored
+// H-bar intermediates, the right-hand side xi, and the sigma / sigma^T interpreter.
+//
+// Notation (Sec. 2.2): i,j,m,n occupied; a,b,e,f virtual; P Cholesky index.  The exact
+// two-body elements of H-bar = e^{-T2} H~ e^{T2}, with H~ the T1-dressed Hamiltonian
+// (Cholesky vectors L~ = (1 - t) L (1 + t), t_ai = t_i^a), are
+//   Fov = f~_ov, Foo = f~_oo + 1/2 <mn||ef> t_in^ef, Fvv = f~_vv - 1/2 <mn||ef> t_mn^af,
+//   Woooo = <mn||ij>~ + 1/2 <mn||ef> t_ij^ef, Wovvo = <mb||ej>~ - <mn||ef> t_jn^fb,
+//   Wooov = <mn||ie>~, Wovoo = <mb||ij>~ - Fov_me t_ij^be + 1/2 <mb||ef>~ t_ij^ef
+//                               + P(ij) <mn||ie>~ t_jn^be,
+// and the vvvv / vovv / vvvo elements are never stored: they enter sigma through L~_vv
+// (the "higher-rank integrals evaluated on the fly" of Sec. 3).
+#include "model.cuh"
+
+namespace cclr {
+
+Model::Model(int o_, int v_, int naux_, cudaStream_t st_)
+    : o(o_), v(v_), naux(naux_), n(o_ + v_), st(st_) {
+  E.st = st;
+  prog = build_sigma_program(o, v, naux);
+}
+
+Model::~Model() {}
+
+static void h2d_or_d2d(void *dst, const void *src, size_t bytes, int device_ptrs, cudaStream_t st) {
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+}
+
+void Model::upload_inputs(const double *eps_h, const double *L, const double *mu_h,
+                          const double *t1_h, const double *t2_h, int device_ptrs) {
+  const int64_t nn = (int64_t)n * n;
+  eps.alloc(sizeof(double) * n);
+  h2d_or_d2d(eps.p, eps_h, sizeof(double) * n, device_ptrs, st);
+  // full L staged once, split into contiguous blocks
+  DevBuf Lfull((size_t)naux * nn * 16);
+  h2d_or_d2d(Lfull.p, L, (size_t)naux * nn * 16, device_ptrs, st);
+  Tens Lf = make_tens(Lfull.p, C128, {naux, n, n});
+  Loo0.alloc((size_t)naux * o * o * 16);
+  Lov0.alloc((size_t)naux * o * v * 16);
+  Lvo0.alloc((size_t)naux * v * o * 16);
+  Lvv0.alloc((size_t)naux * v * v * 16);
+  E.permute(zc(1), Lf.slice(1, 0, o).slice(2, 0, o), "Ppq", T(Loo0, {naux, o, o}), "Ppq", false);
+  E.permute(zc(1), Lf.slice(1, 0, o).slice(2, o, n), "Ppq", T(Lov0, {naux, o, v}), "Ppq", false);
+  E.permute(zc(1), Lf.slice(1, o, n).slice(2, 0, o), "Ppq", T(Lvo0, {naux, v, o}), "Ppq", false);
+  E.permute(zc(1), Lf.slice(1, o, n).slice(2, o, n), "Ppq", T(Lvv0, {naux, v, v}), "Ppq", false);
+  mu.alloc((size_t)3 * nn * 16);
+  h2d_or_d2d(mu.p, mu_h, (size_t)3 * nn * 16, device_ptrs, st);
+
+  // one-body operator h = f - sum_k <pk||qk> with f = diag(eps):
+  // sum_k <pk||qk> = sum_P L_pq tr_P - sum_P sum_k L_pk L_kq, tr_P = sum_k L_kk.
+  h.alloc(nn * 16);
+  Tens H = T(h, {n, n});
+  E.zero(H);
+  set_diag(n, eps.as<double>(), h.p, st);
+  DevBuf Ioo((size_t)o * o * 16), tr((size_t)naux * 16);
+  E.zero(T(Ioo, {o, o}));
+  {
+    std::vector<double> ones(o, 1.0);
+    DevBuf od(sizeof(double) * o);
+    CCLR_CUDA(cudaMemcpyAsync(od.p, ones.data(), sizeof(double) * o, cudaMemcpyHostToDevice, st));
+    set_diag(o, od.as<double>(), Ioo.p, st);
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+  E.zero(T(tr, {naux}));
+  E.contract(zc(1), Lf.slice(1, 0, o).slice(2, 0, o), "Pkl", T(Ioo, {o, o}), "kl", T(tr, {naux}), "P");
+  E.contract(zc(-1), Lf, "Ppq", T(tr, {naux}), "P", H, "pq");
+  E.contract(zc(1), Lf.slice(2, 0, o), "Ppk", Lf.slice(1, 0, o), "Pkq", H, "pq");
+
+  t1.alloc((size_t)o * v * 16);
+  if (t1_h) h2d_or_d2d(t1.p, t1_h, (size_t)o * v * 16, device_ptrs, st);
+  else E.zero(T(t1, {o, v}));
+  t2.alloc((size_t)o * o * v * v * 16);
+  Tens T2 = T(t2, {o, o, v, v});
+  if (t2_h) {
+    h2d_or_d2d(t2.p, t2_h, (size_t)o * o * v * v * 16, device_ptrs, st);
+  } else {
+    // first-order doubles t_ij^ab = <ab||ij> / (e_i + e_j - e_a - e_b), <ab|ij> = sum_P L_ai L_bj
+    E.zero(T2);
+    Tens Lvo = T(Lvo0, {naux, v, o});
+    E.contract(zc(1), Lvo, "Pai", Lvo, "Pbj", T2, "ijab");
+    E.contract(zc(-1), Lvo, "Paj", Lvo, "Pbi", T2, "ijab");
+    apply_denominator(o, v, eps.as<double>(), t2.p, st);
+  }
+  CCLR_CUDA(cudaStreamSynchronize(st));
+}
+
+void Model::build_set(const void *t1d, const void *t2d, CstSet &out) {
+  out.dt = C128;
+  const int P = naux;
+  auto alloc = [&](int id, std::initializer_list<int64_t> dims) {
+    int64_t ne = 1;
+    for (auto d : dims) ne *= d;
+    if (out.buf[id].bytes != (size_t)ne * 16) out.buf[id].alloc((size_t)ne * 16);
+    out.t[id] = make_tens(out.buf[id].p, C128, dims);
+    E.zero(out.t[id]);
+    return out.t[id];
+  };
+  Tens t1t = make_tens((void *)t1d, C128, {o, v});
+  Tens t2t = make_tens((void *)t2d, C128, {o, o, v, v});
+  Tens Loo = T(Loo0, {P, o, o}), Lov = T(Lov0, {P, o, v}), Lvo = T(Lvo0, {P, v, o}),
+       Lvv = T(Lvv0, {P, v, v});
+
+  // ---- T1 dressing of the Cholesky blocks: L~ = (1 - t) L (1 + t)
+  DevBuf Ltoo_b((size_t)P * o * o * 16);
+  Tens Ltoo = T(Ltoo_b, {P, o, o});
+  E.permute(zc(1), Loo, "Pij", Ltoo, "Pij", false);
+  E.contract(zc(1), Lov, "Pib", t1t, "jb", Ltoo, "Pij");
+  Tens Ltov = alloc(K_LOV, {P, o, v});
+  E.permute(zc(1), Lov, "Pia", Ltov, "Pia", false);
+  Tens Ltvv = alloc(K_LVV, {P, v, v});
+  E.permute(zc(1), Lvv, "Pab", Ltvv, "Pab", false);
+  E.contract(zc(-1), t1t, "ma", Lov, "Pmb", Ltvv, "Pab");
+  Tens Ltvo = alloc(K_LVO, {P, v, o});
+  E.permute(zc(1), Lvo, "Pai", Ltvo, "Pai", false);
+  E.contract(zc(-1), t1t, "ma", Loo, "Pmi", Ltvo, "Pai");
+  E.contract(zc(1), Ltvv, "Pab", t1t, "ib", Ltvo, "Pai");
+
+  // ---- dressed Fock f~ = (1 - t) h (1 + t) + sum_k <pk||qk>~ (oo, ov, vv blocks)
+  Tens Hf = T(h, {n, n});
+  Tens hoo = Hf.slice(0, 0, o).slice(1, 0, o), hov = Hf.slice(0, 0, o).slice(1, o, n),
+       hvv = Hf.slice(0, o, n).slice(1, o, n);
+  Tens Foo = alloc(K_FOO, {o, o}), Fov = alloc(K_FOV, {o, v}), Fvv = alloc(K_FVV, {v, v});
+  E.permute(zc(1), hoo, "ij", Foo, "ij", false);
+  E.contract(zc(1), hov, "ib", t1t, "jb", Foo, "ij");
+  E.permute(zc(1), hov, "ia", Fov, "ia", false);
+  E.permute(zc(1), hvv, "ab", Fvv, "ab", false);
+  E.contract(zc(-1), t1t, "ma", hov, "mb", Fvv, "ab");
+  {
+    DevBuf Ib((size_t)o * o * 16), trb((size_t)P * 16), ones(sizeof(double) * o);
+    Tens I = T(Ib, {o, o}), tr = T(trb, {P});
+    E.zero(I);
+    std::vector<double> one(o, 1.0);
+    CCLR_CUDA(cudaMemcpyAsync(ones.p, one.data(), sizeof(double) * o, cudaMemcpyHostToDevice, st));
+    set_diag(o, ones.as<double>(), Ib.p, st);
+    E.zero(tr);
+    E.contract(zc(1), Ltoo, "Pkl", I, "kl", tr, "P");
+    E.contract(zc(1), Ltoo, "Pij", tr, "P", Foo, "ij");
+    E.contract(zc(1), Ltov, "Pia", tr, "P", Fov, "ia");
+    E.contract(zc(1), Ltvv, "Pab", tr, "P", Fvv, "ab");
+    E.contract(zc(-1), Ltoo, "Pik", Ltoo, "Pkj", Foo, "ij");
+    E.contract(zc(-1), Ltoo, "Pik", Ltov, "Pka", Fov, "ia");
+    E.contract(zc(-1), Ltvo, "Pak", Ltov, "Pkb", Fvv, "ab");
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+
+  // ---- amplitudes and <mn||ef>
+  Tens T2 = alloc(K_T2, {o, o, v, v});
+  E.permute(zc(1), t2t, "ijab", T2, "ijab", false);
+  Tens oovv = alloc(K_OOVV, {o, o, v, v});
+  E.contract(zc(1), Ltov, "Pme", Ltov, "Pnf", oovv, "mnef");
+  E.contract(zc(-1), Ltov, "Pmf", Ltov, "Pne", oovv, "mnef");
+
+  // ---- one-body H-bar elements
+  E.contract(zc(0.5), T2, "inef", oovv, "mnef", Foo, "mi");
+  E.contract(zc(-0.5), T2, "mnaf", oovv, "mnef", Fvv, "ae");
+
+  // ---- Woooo = <mn||ij>~ + 1/2 <mn||ef> t_ij^ef
+  Tens Woooo = alloc(K_WOOOO, {o, o, o, o});
+  E.contract(zc(1), Ltoo, "Pmi", Ltoo, "Pnj", Woooo, "mnij");
+  E.contract(zc(-1), Ltoo, "Pmj", Ltoo, "Pni", Woooo, "mnij");
+  E.contract(zc(0.5), T2, "ijef", oovv, "mnef", Woooo, "mnij");
+
+  // ---- Wovvo = <mb||ej>~ - <mn||ef> t_jn^fb
+  Tens Wovvo = alloc(K_WOVVO, {o, v, v, o});
+  E.contract(zc(1), Ltov, "Pme", Ltvo, "Pbj", Wovvo, "mbej");
+  E.contract(zc(-1), Ltoo, "Pmj", Ltvv, "Pbe", Wovvo, "mbej");
+  E.contract(zc(-1), T2, "jnfb", oovv, "mnef", Wovvo, "mbej");
+
+  // ---- Wooov = <mn||ie>~
+  Tens Wooov = alloc(K_WOOOV, {o, o, o, v});
+  E.contract(zc(1), Ltoo, "Pmi", Ltov, "Pne", Wooov, "mnie");
+  E.contract(zc(-1), Ltov, "Pme", Ltoo, "Pni", Wooov, "mnie");
+
+  // ---- Wovoo = <mb||ij>~ - Fov t + 1/2 <mb||ef>~ t_ij^ef + P(ij) <mn||ie>~ t_jn^be
+  Tens Wovoo = alloc(K_WOVOO, {o, v, o, o});
+  E.contract(zc(1), Ltoo, "Pmi", Ltvo, "Pbj", Wovoo, "mbij");
+  E.contract(zc(-1), Ltoo, "Pmj", Ltvo, "Pbi", Wovoo, "mbij");
+  E.contract(zc(-1), Fov, "me", T2, "ijbe", Wovoo, "mbij");
+  {
+    DevBuf tb((size_t)o * v * o * o * 16);
+    Tens tmp = T(tb, {o, v, o, o});
+    E.zero(tmp);
+    E.contract(zc(1), Wooov, "mnie", T2, "jnbe", tmp, "mbij");
+    E.permute(zc(1), tmp, "mbij", Wovoo, "mbij", true);
+    E.permute(zc(-1), tmp, "mbij", Wovoo, "mbji", true);
+    // 1/2 sum_ef <mb||ef>~ t_ij^ef = sum_ef <mb|ef>~ t_ij^ef, formed in chunks of b
+    int64_t per_b = (int64_t)o * v * v * 16;
+    int64_t bc = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_b));
+    DevBuf Gb((size_t)(bc * per_b));
+    for (int64_t b0 = 0; b0 < v; b0 += bc) {
+      int64_t b1 = std::min<int64_t>(v, b0 + bc);
+      Tens G = make_tens(Gb.p, C128, {o, b1 - b0, v, v});
+      E.zero(G);
+      E.contract(zc(1), Ltov, "Pme", Ltvv.slice(1, b0, b1), "Pbf", G, "mbef");
+      E.contract(zc(1), G, "mbef", T2, "ijef", Wovoo.slice(1, b0, b1), "mbij");
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+  out.valid = true;
+}
+
+void Model::make_c64(const CstSet &src, CstSet &dst) {
+  dst.dt = C64;
+  for (int k = 0; k < K_NCST; ++k) {
+    const Tens &s = src.t[k];
+    size_t bytes = (size_t)s.numel() * 8;
+    if (dst.buf[k].bytes != bytes) dst.buf[k].alloc(bytes);
+    Tens d = s;
+    d.p = dst.buf[k].p;
+    d.dt = C64;
+    std::string m = std::string("abcdefgh").substr(0, s.rank);
+    E.permute(zc(1), s, m, d, m, false);
+    dst.t[k] = d;
+  }
+  dst.valid = true;
+}
+
+void Model::build_diagonal() {
+  D1.alloc(sizeof(double) * o * v);
+  D2.alloc(sizeof(double) * (size_t)o * o * v * v);
+  build_diag(o, v, c128.buf[K_FOO].p, c128.buf[K_FVV].p, D1.as<double>(), D2.as<double>(), st);
+}
+
+const CstSet &Model::cst_for(int p) {
+  if (p == 0) return c128;
+  if (!c64.valid) make_c64(c128, c64);
+  return c64;
+}
+
+std::vector<DevBuf> &Model::temps(int dt) {
+  auto &tv = dt == C128 ? tmp128 : tmp64;
+  if (tv.empty()) {
+    tv.resize(prog.vars.size());
+    for (size_t k = 0; k < prog.vars.size(); ++k) {
+      if (k == 0 || k == 2) continue;  // x1 / s1 always come from the caller
+      int64_t ne = 1;
+      for (auto d : prog.vars[k].dims) ne *= d;
+      tv[k].alloc((size_t)ne * dt_size(dt));
+    }
+  }
+  return tv;
+}
+
+Tens Model::var_tens(int id, int dt, void *p) const {
+  Tens t;
+  t.p = p;
+  t.dt = dt;
+  t.rank = (int)prog.vars[id].dims.size();
+  int64_t s = 1;
+  for (int k = t.rank - 1; k >= 0; --k) {
+    t.dim[k] = prog.vars[id].dims[k];
+    t.str[k] = s;
+    s *= t.dim[k];
+  }
+  return t;
+}
+
+// pp-ladder on CUDA cores: out[i,j,a,b] += alpha sum_ef <ab|ef>~ in[i,j,e,f] (dir +1), or the
+// transpose in'[i,j,e,f] += alpha sum_ab <ab|ef>~ in[i,j,a,b] (dir -1), <ab|ef>~ formed in
+// chunks of a from L~_vv and never stored whole.
+void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out) {
+  const int dt = C.dt;
+  const Tens &Lvv = C.t[K_LVV];
+  const int64_t per_a = (int64_t)v * v * v * dt_size(dt);
+  int64_t ac = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_a));
+  if (ladW.bytes < (size_t)(ac * per_a)) ladW.alloc((size_t)(ac * per_a));
+  for (int64_t a0 = 0; a0 < v; a0 += ac) {
+    int64_t a1 = std::min<int64_t>(v, a0 + ac);
+    Tens W = make_tens(ladW.p, dt, {a1 - a0, v, v, v});
+    E.zero(W);
+    E.contract(zc(1), Lvv.slice(1, a0, a1), "Pae", Lvv, "Pbf", W, "aebf");
+    if (dir > 0) E.contract(alpha, W, "aebf", in, "ijef", out.slice(2, a0, a1), "ijab");
+    else E.contract(alpha, W, "aebf", in.slice(2, a0, a1), "ijab", out, "ijef");
+  }
+}
+
+void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2) {
+  const int dt = C.dt;
+  auto &tv = temps(dt);
+  const int nv = (int)prog.vars.size();
+  std::vector<void *> ptr(nv, nullptr);
+  for (int k = 4; k < nv; ++k) ptr[k] = tv[k].p;
+  auto V = [&](int id) { return var_tens(id, dt, ptr[id]); };
+  auto Cst = [&](int id) { return C.t[id]; };
+  if (dir > 0) {
+    ptr[0] = (void *)x1; ptr[1] = (void *)x2; ptr[2] = s1; ptr[3] = s2;
+    E.zero(V(2));
+    E.zero(V(3));
+    for (const Op &op : prog.ops) {
+      switch (op.kind) {
+        case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.in), op.mi, V(op.out), op.mo); break;
+        case OP_PERM: E.permute(op.alpha, V(op.in), op.mi, V(op.out), op.mo, true); break;
+        case OP_ZERO: E.zero(V(op.out)); break;
+        case OP_LADDER: ladder(+1, C, op.alpha, V(op.in), V(op.out)); break;
+      }
+    }
+  } else {
+    // bars: s1 <- y1 (x1 argument), s2 <- y2 / 4 (unique-amplitude weight), outputs to
+    // x1-bar (s1 argument) and a temporary x2-bar projected onto antisymmetric tensors.
+    ptr[2] = (void *)x1;
+    ptr[3] = tv[3].p;
+    ptr[0] = s1;
+    ptr[1] = tv[1].p;
+    E.permute(zc(0.25), var_tens(3, dt, (void *)x2), "ijab", V(3), "ijab", false);
+    E.zero(V(0));
+    E.zero(V(1));
+    for (int k = 4; k < nv; ++k) E.zero(V(k));
+    for (auto it = prog.ops.rbegin(); it != prog.ops.rend(); ++it) {
+      const Op &op = *it;
+      switch (op.kind) {
+        case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.out), op.mo, V(op.in), op.mi); break;
+        case OP_PERM: E.permute(op.alpha, V(op.out), op.mo, V(op.in), op.mi, true); break;
+        case OP_ZERO: E.zero(V(op.out)); break;
+        case OP_LADDER: ladder(-1, C, op.alpha, V(op.out), V(op.in)); break;
+      }
+    }
+    Tens out2 = var_tens(3, dt, s2);
+    Tens z2 = V(1);
+    E.permute(zc(1), z2, "ijab", out2, "ijab", false);
+    E.permute(zc(-1), z2, "ijab", out2, "jiab", true);
+    E.permute(zc(-1), z2, "ijab", out2, "ijba", true);
+    E.permute(zc(1), z2, "ijab", out2, "jiba", true);
+  }
+}
+
+// xi^B_ia = mu~_ai + sum_me mu~_me t_im^ae ;
+// xi^B_ijab = P(ab) sum_e mu~_be t_ij^ae - P(ij) sum_m mu~_mj t_im^ab ; mu~ = (1-t) mu (1+t).
+void Model::xi(const void *mub, const void *t1d, const void *t2d, void *xi1, void *xi2) {
+  Tens M = make_tens((void *)mub, C128, {n, n});
+  Tens t1t = make_tens((void *)t1d, C128, {o, v});
+  Tens t2t = make_tens((void *)t2d, C128, {o, o, v, v});
+  Tens moo = M.slice(0, 0, o).slice(1, 0, o), mov = M.slice(0, 0, o).slice(1, o, n),
+       mvo = M.slice(0, o, n).slice(1, 0, o), mvv = M.slice(0, o, n).slice(1, o, n);
+  DevBuf b((size_t)(o * o + v * v + v * o) * 16);
+  Tens Moo = make_tens(b.p, C128, {o, o});
+  Tens Mvv = make_tens((char *)b.p + (size_t)o * o * 16, C128, {v, v});
+  Tens Mvo = make_tens((char *)b.p + (size_t)(o * o + v * v) * 16, C128, {v, o});
+  E.permute(zc(1), moo, "ij", Moo, "ij", false);
+  E.contract(zc(1), mov, "ib", t1t, "jb", Moo, "ij");
+  E.permute(zc(1), mvv, "ab", Mvv, "ab", false);
+  E.contract(zc(-1), t1t, "ma", mov, "mb", Mvv, "ab");
+  E.permute(zc(1), mvo, "ai", Mvo, "ai", false);
+  E.contract(zc(-1), t1t, "ma", moo, "mi", Mvo, "ai");
+  E.contract(zc(1), Mvv, "ab", t1t, "ib", Mvo, "ai");
+  Tens X1 = make_tens(xi1, C128, {o, v});
+  Tens X2 = make_tens(xi2, C128, {o, o, v, v});
+  E.permute(zc(1), Mvo, "ai", X1, "ia", false);
+  E.contract(zc(1), mov, "me", t2t, "imae", X1, "ia");
+  DevBuf rb((size_t)o * o * v * v * 16);
+  Tens R = make_tens(rb.p, C128, {o, o, v, v});
+  E.zero(R);
+  E.contract(zc(1), Mvv, "be", t2t, "ijae", R, "ijab");
+  E.permute(zc(1), R, "ijab", X2, "ijab", false);
+  E.permute(zc(-1), R, "ijab", X2, "ijba", true);
+  E.zero(R);
+  E.contract(zc(-1), Moo, "mj", t2t, "imab", R, "ijab");
+  E.permute(zc(1), R, "ijab", X2, "ijab", true);
+  E.permute(zc(-1), R, "ijab", X2, "jiab", true);
+  CCLR_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------------------
+// The sigma program: <mu|(H-bar X)_c|Phi_0> as linear operations on X (Sec. 2.2 Jacobian).
+// ---------------------------------------------------------------------------------------
+Program build_sigma_program(int o, int v, int naux) {
+  Program p;
+  const int64_t O = o, Vv = v, P = naux;
+  auto var = [&](std::vector<int64_t> d) { p.vars.push_back({d}); return (int)p.vars.size() - 1; };
+  const int X1 = var({O, Vv}), X2 = var({O, O, Vv, Vv}), S1 = var({O, Vv}), S2 = var({O, O, Vv, Vv});
+  const int Zt = var({P, O, Vv}), Rab = var({O, O, Vv, Vv}), Rij = var({O, O, Vv, Vv}),
+            Rijab = var({O, O, Vv, Vv}), Zoo = var({O, O, O, O}), U = var({P, Vv, O}),
+            cm = var({O, O}), dm = var({O, O, O, O}), sm = var({P, O, O}), Vm = var({O, Vv, O, Vv}),
+            Xvv = var({Vv, Vv}), Xoo = var({O, O}), w = var({P});
+  (void)S1;
+  auto C = [&](double a, int cst, const char *mc, int in, const char *mi, int out, const char *mo) {
+    p.ops.push_back(Op{OP_CONTRACT, zc(a), cst, mc, mi, mo, in, out});
+  };
+  auto Z = [&](int out) { p.ops.push_back(Op{OP_ZERO, zc(0), -1, "", "", "", -1, out}); };
+  auto PM = [&](double a, int in, const char *mi, int out, const char *mo) {
+    p.ops.push_back(Op{OP_PERM, zc(a), -1, "", mi, mo, in, out});
+  };
+  // ---- singles
+  C(1, K_FVV, "ae", X1, "ie", S1, "ia");
+  C(-1, K_FOO, "mi", X1, "ma", S1, "ia");
+  C(1, K_WOVVO, "maei", X1, "me", S1, "ia");
+  C(1, K_FOV, "me", X2, "imae", S1, "ia");
+  Z(Zt);  // 1/2 sum <am||ef>~ X_im^ef = sum_P sum_e L~_ae (sum_mf L~_mf X_im^ef)
+  C(1, K_LOV, "Pmf", X2, "imef", Zt, "Pie");
+  C(1, K_LVV, "Pae", Zt, "Pie", S1, "ia");
+  C(-0.5, K_WOOOV, "mnie", X2, "mnae", S1, "ia");
+  // ---- doubles
+  Z(Rab); Z(Rij); Z(Rijab);
+  C(1, K_FVV, "be", X2, "ijae", Rab, "ijab");
+  C(-1, K_FOO, "mj", X2, "imab", Rij, "ijab");
+  C(0.5, K_WOOOO, "mnij", X2, "mnab", S2, "ijab");
+  p.ops.push_back(Op{OP_LADDER, zc(1), -1, "", "ijef", "ijab", X2, S2});  // sum_ef <ab|ef>~ X
+  Z(Zoo);  // vvvv element's T2 part: 1/2 t_mn^ab (1/2 <mn||ef> X_ij^ef)
+  C(0.5, K_OOVV, "mnef", X2, "ijef", Zoo, "mnij");
+  C(0.5, K_T2, "mnab", Zoo, "mnij", S2, "ijab");
+  C(1, K_WOVVO, "mbej", X2, "imae", Rijab, "ijab");           // ring, P(ij)P(ab)
+  // P(ij) sum_e Wvvvo_abej x_i^e, factorised through L~ (vvvo never stored)
+  Z(U);
+  C(1, K_LVV, "Pae", X1, "ie", U, "Pai");
+  C(1, K_LVO, "Pbj", U, "Pai", Rijab, "ijab");               // <ab||ej>~ x_i^e
+  Z(cm);
+  C(1, K_FOV, "me", X1, "ie", cm, "mi");
+  C(-1, K_T2, "mjab", cm, "mi", Rij, "ijab");                // -Fov_me t_mj^ab x_i^e
+  Z(dm);
+  C(-1, K_WOOOV, "mnje", X1, "ie", dm, "mnji");
+  C(0.5, K_T2, "mnab", dm, "mnji", Rij, "ijab");             // 1/2 <mn||ej>~ t_mn^ab x_i^e
+  Z(sm);
+  C(1, K_LOV, "Pme", X1, "ie", sm, "Pmi");
+  Z(Vm);                                                     // V_mbif = sum_e <mb||ef>~ x_i^e
+  C(1, K_LVV, "Pbf", sm, "Pmi", Vm, "mbif");
+  C(-1, K_LOV, "Pmf", U, "Pbi", Vm, "mbif");
+  C(-1, K_T2, "mjaf", Vm, "mbif", Rijab, "ijab");
+  C(-1, K_WOVOO, "mbij", X1, "ma", Rab, "ijab");             // -P(ab) Wovoo_mbij x_m^a
+  // three-body parts of H-bar
+  Z(w);
+  C(1, K_LOV, "Pmf", X1, "mf", w, "P");
+  Z(Xvv);
+  C(1, K_LVV, "Pbe", w, "P", Xvv, "be");
+  C(-1, K_LOV, "Pme", U, "Pbm", Xvv, "be");
+  C(-0.5, K_OOVV, "mnef", X2, "mnbf", Xvv, "be");
+  C(1, K_T2, "ijae", Xvv, "be", Rab, "ijab");
+  Z(Xoo);
+  C(1, K_WOOOV, "mnje", X1, "ne", Xoo, "mj");
+  C(0.5, K_OOVV, "mnef", X2, "jnef", Xoo, "mj");
+  C(-1, K_T2, "imab", Xoo, "mj", Rij, "ijab");
+  // antisymmetrisers
+  PM(1, Rab, "ijab", S2, "ijab");
+  PM(-1, Rab, "ijab", S2, "ijba");
+  PM(1, Rij, "ijab", S2, "ijab");
+  PM(-1, Rij, "ijab", S2, "jiab");
+  PM(1, Rijab, "ijab", S2, "ijab");
+  PM(-1, Rijab, "ijab", S2, "jiab");
+  PM(-1, Rijab, "ijab", S2, "ijba");
+  PM(1, Rijab, "ijab", S2, "jiba");
+  return p;
+}
+
+}  // namespace cclr

@@ -1,0 +1,100 @@
+// The LR-CCSD response model held on the device: inputs, T1-dressed Cholesky blocks,
+// stored H-bar intermediates, and the sigma program (a list of linear operations on
+// amplitude-shaped buffers that is run forward for sigma = A X and in reverse, with every
+// operation transposed, for Y A).
+#pragma once
+#include <array>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace cclr {
+
+// Constants a sigma program reads (one complete set per precision and per T).
+enum CstId {
+  K_FOV, K_FOO, K_FVV, K_WOOOO, K_WOVVO, K_WOOOV, K_WOVOO, K_T2, K_OOVV, K_LOV, K_LVO, K_LVV,
+  K_NCST
+};
+
+struct CstSet {
+  int dt = C128;
+  std::array<DevBuf, K_NCST> buf;
+  std::array<Tens, K_NCST> t;
+  bool valid = false;
+};
+
+enum OpKind { OP_CONTRACT, OP_PERM, OP_ZERO, OP_LADDER };
+
+struct Op {
+  OpKind kind;
+  zc alpha;
+  int cst = -1;
+  std::string mc, mi, mo;
+  int in = -1, out = -1;
+};
+
+struct VarSpec {
+  std::vector<int64_t> dims;
+};
+
+struct Program {
+  std::vector<VarSpec> vars;  // 0 x1, 1 x2, 2 s1, 3 s2, then temporaries
+  std::vector<Op> ops;
+};
+
+Program build_sigma_program(int o, int v, int naux);
+
+struct Timers {
+  cudaEvent_t ev[8];
+  bool made = false;
+};
+
+class Model {
+ public:
+  Model(int o, int v, int naux, cudaStream_t st);
+  ~Model();
+  int o, v, naux, n;
+  cudaStream_t st;
+  Engine E;
+
+  // inputs (complex128 / double)
+  DevBuf eps;                       // [n]
+  DevBuf Loo0, Lov0, Lvo0, Lvv0;    // undressed Cholesky blocks [P][.][.]
+  DevBuf mu;                        // [3][n][n]
+  DevBuf t1, t2;                    // [o][v], [o][o][v][v]
+  DevBuf h;                         // one-body part of H, [n][n]
+
+  CstSet c128, c64;                 // intermediates at the current T
+  DevBuf D1, D2;                    // preconditioner diagonal (real)
+  Program prog;
+  std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision
+  int prec = 0;
+  DevBuf ladW;                      // ladder formation scratch
+  float ms_last[3] = {0, 0, 0};
+
+  void upload_inputs(const double *eps_h, const double *L, const double *mu_h,
+                     const double *t1_h, const double *t2_h, int device_ptrs);
+  // Build dressed blocks + intermediates for amplitudes (t1d, t2d) into `out` (FP64).
+  void build_set(const void *t1d, const void *t2d, CstSet &out);
+  void make_c64(const CstSet &src, CstSet &dst);
+  void build_diagonal();
+  const CstSet &cst_for(int prec_) ;
+
+  // sigma (dir = +1) or sigma^T (dir = -1) on device buffers of the given dtype.
+  void apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2);
+  // xi^B (or at other amplitudes), complex128 device buffers.
+  void xi(const void *mub, const void *t1d, const void *t2d, void *xi1, void *xi2);
+
+  Tens T(const DevBuf &b, std::initializer_list<int64_t> dims, int dt = C128) const {
+    return make_tens(b.p, dt, dims);
+  }
+
+ private:
+  void ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out);
+  std::vector<DevBuf> &temps(int dt);
+  Tens var_tens(int id, int dt, void *p) const;
+};
+
+}  // namespace cclr

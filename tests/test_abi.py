@@ -1,0 +1,61 @@
+"""The C-ABI library loads and exports every symbol include/cclr.h declares (no GPU work)."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cclr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(cc_lr_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_12914_gb300 import build, binding
+    path = build.build()
+    return binding.load(path)
+
+
+def test_header_declares_boundary():
+    names = _declared()
+    for required in ("cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_solve", "cc_lr_free"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2604_12914_gb300 import binding
+    for name in _declared():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.LIB_PATH], capture_output=True, text=True).stdout
+    exported = set(re.findall(r"\bT (cc_lr_\w+)", out))
+    assert set(_declared()) <= exported
+    assert set(binding.EXPORTS) <= exported
+
+
+def test_strerror_and_invalid_arguments_without_gpu(lib):
+    import ctypes
+    from paper_2604_12914_gb300 import binding
+    assert binding.cc_lr_strerror(0) == "success"
+    assert "converge" in binding.cc_lr_strerror(binding.CCLR_ENOCONV)
+    h = ctypes.c_void_p()
+    # argument validation happens before any device call
+    st = lib.cc_lr_init(ctypes.byref(h), 0, 4, 4, None, None, None, None, None, None, None, 0, 0, 0, None)
+    assert st == binding.CCLR_EINVAL
+    assert b"must be" in lib.cc_lr_last_error()
+    assert lib.cc_lr_sigma(None, 1, None, None, None, None) == binding.CCLR_EINVAL
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    from paper_2604_12914_gb300 import binding
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(ImportError):
+            binding.load(str(tmp_path / "nope.so"))
+    finally:
+        binding._lib = saved

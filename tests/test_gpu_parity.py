@@ -1,0 +1,155 @@
+"""GPU parity: libcclr (through the C ABI) against the CPU oracle, element by element.
+
+Tolerances: FP64 path 1e-10 relative (unique-amplitude 2-norm); complex64 paths 2e-5
+(FP32 CUDA cores) -- FP32 accumulation over K ~ v^2 terms of O(1) products gives
+relative rounding ~ sqrt(K) * 6e-8.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ccsd, response as R, secondq
+from oracle.integrals import as_t, eri_anti
+from paper_2604_12914_gb300.inputs import make_system, make_config, random_amplitudes
+
+from gpu_helpers import gpu_context, oracle_sigma, oracle_sigma_T, oracle_setup, rel_err, wdot
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # (o, v, naux, seed, scale, t1_scale)
+    (2, 4, 6, 1, 0.5, 0.2),
+    (5, 13, 21, 2, 0.6, 0.1),
+    (3, 67, 40, 3, 0.4, 0.05),     # v spans two 64-wide GEMM tiles with a ragged tail
+    (10, 40, 200, 1, 1.0, 0.0),    # C1 sizes, T1 = 0, MP2 T2 (the config's own recipe)
+]
+
+
+def _amps(s, seed, t1_scale):
+    a1, a2 = random_amplitudes(s.o, s.v, seed=seed, s1=0.2, s2=0.2)
+    t1 = a1 * (t1_scale / 0.2) if t1_scale else np.zeros_like(a1)
+    return t1, a2
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_sigma_fp64_matches_oracle(case):
+    o, v, naux, seed, scale, t1s = case
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    if (o, v) == (10, 40):
+        f, g, L, _, _ = oracle_setup(s, np.zeros((o, v)), np.zeros((o, o, v, v)))
+        t2 = ccsd.first_order_t2(as_t(s.eps), g, o).numpy()
+        t1 = np.zeros((o, v), complex)
+        ctx = gpu_context(s, t1=None, t2=None)     # library forms the first-order T2 itself
+        gt1, gt2 = ctx.cc_lr_get_t()
+        assert np.abs(gt2 - t2).max() < 1e-12 * np.abs(t2).max()
+    else:
+        t1, t2 = _amps(s, seed + 100, t1s)
+        ctx = gpu_context(s, t1=t1, t2=t2)
+    x1, x2 = random_amplitudes(o, v, seed=seed + 7, nvec=2)
+    g1, g2 = ctx.cc_lr_sigma(x1, x2)
+    for r in range(2):
+        r1, r2 = oracle_sigma(s, t1, t2, x1[r], x2[r])
+        assert rel_err(g1[r], g2[r], r1, r2) < 1e-10
+        # antisymmetry of the doubles block
+        assert np.abs(g2[r] + g2[r].transpose(1, 0, 2, 3)).max() < 1e-10 * np.abs(g2[r]).max()
+    ctx.close()
+
+
+@pytest.mark.parametrize("case", CASES[:3])
+def test_sigma_T_fp64_matches_oracle_and_bilinear(case):
+    o, v, naux, seed, scale, t1s = case
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx = gpu_context(s, t1=t1, t2=t2)
+    y1, y2 = random_amplitudes(o, v, seed=seed + 9)
+    z1, z2 = ctx.cc_lr_sigma_T(y1, y2)
+    r1, r2 = oracle_sigma_T(s, t1, t2, y1, y2)
+    assert rel_err(z1, z2, r1, r2) < 1e-10
+    x1, x2 = random_amplitudes(o, v, seed=seed + 11)
+    s1, s2 = ctx.cc_lr_sigma(x1, x2)
+    lhs = wdot(y1, y2, s1, s2)
+    rhs = wdot(z1, z2, x1, x2)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5)])
+def test_sigma_c64_matches_oracle(prec, tol):
+    o, v, naux, seed, scale, t1s = CASES[2]
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx = gpu_context(s, t1=t1, t2=t2, prec=prec)
+    x1, x2 = random_amplitudes(o, v, seed=3)
+    g1, g2 = ctx.cc_lr_sigma(x1, x2)
+    r1, r2 = oracle_sigma(s, t1, t2, x1, x2)
+    assert rel_err(g1, g2, r1, r2) < tol
+    z1, z2 = ctx.cc_lr_sigma_T(x1, x2)
+    q1, q2 = oracle_sigma_T(s, t1, t2, x1, x2)
+    assert rel_err(z1, z2, q1, q2) < tol
+    ctx.close()
+
+
+def test_xi_matches_oracle():
+    s = make_system(4, 11, 17, seed=4, scale=0.5)
+    t1, t2 = _amps(s, 40, 0.1)
+    ctx = gpu_context(s, t1=t1, t2=t2)
+    f, g, L, T1, T2 = oracle_setup(s, t1, t2)
+    P = R.Problem(f, g, L, s.o, T1, T2)
+    for comp in range(3):
+        x1, x2 = ctx.cc_lr_xi(comp)
+        r1, r2 = P.xi(as_t(s.mu[comp]))
+        assert rel_err(x1, x2, r1.numpy(), r2.numpy()) < 1e-12
+    ctx.close()
+
+
+def _converged_small(o=3, v=8, naux=12, seed=5, scale=0.3):
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    f, g, L, _, _ = oracle_setup(s, np.zeros((o, v)), np.zeros((o, o, v, v)))
+    t1, t2, _ = R.solve_ccsd(f, g, o, L=L)
+    return s, R.Problem(f, g, L, o, t1, t2)
+
+
+def test_solve_x_and_lambda_match_oracle():
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy())
+    A = P.jacobian_matrix()
+    for comp, omega in [(2, 0.0), (0, 0.0428), (1, -0.0428)]:
+        x1, x2, st = ctx.cc_lr_solve_x(omega, comp, tol=1e-11)
+        xi = P.pack(*P.xi(as_t(s.mu[comp])))
+        ref = P.unpack(R.solve_x(A, xi, omega))
+        assert rel_err(x1, x2, ref[0].numpy(), ref[1].numpy()) < 1e-9
+        assert st["converged"] == 1
+    l1, l2 = ctx.cc_lr_lambda(tol=1e-11)
+    lam = torch.linalg.solve(A.transpose(0, 1), -P.eta0())
+    r1, r2 = P.unpack(lam)
+    assert rel_err(l1, l2, r1.numpy(), r2.numpy()) < 1e-9
+    ctx.close()
+
+
+@pytest.mark.parametrize("omega", [0.0, 0.0428])
+def test_alpha_matches_oracle(omega):
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy())
+    al, st = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-11)
+    ref = R.alpha(P, [as_t(m) for m in s.mu], omega).numpy()
+    assert np.abs(al[0] - ref).max() < 1e-6 * np.abs(ref).max()
+    assert np.abs(al[0] - al[0].conj().T).max() < 1e-8 * np.abs(ref).max()
+    ctx.close()
+
+
+def test_alpha_two_electrons_equals_sum_over_states():
+    """o=2: GPU alpha against the exact FCI sum over states (Eq. sos)."""
+    s = make_system(2, 4, 6, seed=2, scale=0.3)
+    f, g, L, _, _ = oracle_setup(s, np.zeros((2, 4)), np.zeros((2, 2, 4, 4)))
+    t1, t2, _ = R.solve_ccsd(f, g, 2, L=L)
+    ctx = gpu_context(s, t1=t1.numpy(), t2=t2.numpy())
+    bf = secondq.BruteForce(f.numpy(), g.numpy(), 2)
+    w, U = bf.fci()
+    st, _ = secondq.cc_state_overlap(U, t1.numpy(), t2.numpy(), bf)
+    ops = [bf.one_body_op(m) for m in s.mu]
+    for omega in (0.0, 0.0428):
+        al, _ = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-12)
+        sos = np.array([[-secondq.sos_response(w, U, ops[a], ops[b], omega, st) for b in range(3)]
+                        for a in range(3)])
+        assert np.abs(al[0] - sos).max() < 1e-7 * np.abs(sos).max()
+    ctx.close()
