@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Throughput of the LR-CCSD Jacobian-vector product sigma = A X on GB300.
+
+One step = one complete sigma(X) (singles + doubles, one right-hand side) of the hot path:
+the particle-particle ladder with <ab|ef>~ formed on the fly from the T1-dressed Cholesky
+vectors, the ring / crossed, hole-hole and three-body terms, and the antisymmetrisers.
+Workload: o=32 occupied, v=240 virtual spinors, naux=1200 Cholesky vectors (synthetic,
+seeded; T1 = 0, first-order T2), the single-RHS sigma configuration.
+
+  python bench.py [--gpus N --steps K --warmup W --prec tf32|3xtf32|fp32|fp64]
+  python bench.py --impl reference     (the CPU oracle on a bounded sample)
+
+Prints one JSON line (rank 0).  N > 1 (torchrun): independent replicas, one per GPU
+(right-hand sides are independent problems), no data-path collective; timing is the max
+over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sigma-vectors/s and time-to-alpha(omega) vs FP64 GPU path at |dalpha|<1e-4 a.u."
+WORKLOAD = "C2"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cclr", choices=["cclr", "reference"])
+    ap.add_argument("--prec", default=os.environ.get("CCLR_BENCH_PREC", "fp32"))
+    ap.add_argument("--config", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+def algorithmic(o, v, naux):
+    """cMAC counts per sigma (one RHS) with packed pair indices (i<j, a<b, e<f)."""
+    Po, Pv = o * (o - 1) // 2, v * (v - 1) // 2
+    form = naux * Pv * v * v          # <ab|ef>~ for a<b, all (e, f)
+    contr = Po * Pv * Pv              # sum_{e<f} <ab||ef>~ X_ij^ef
+    ring = o ** 3 * v ** 3
+    return {"ladder_cmac": form + contr, "ring_cmac": ring,
+            "n_unique": o * v + Po * Pv}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def ladder_peak(prec):
+    """Peak (TFLOP/s) of the unit the ladder runs on, and how it was obtained."""
+    d, how = peaks()
+    if prec in ("tf32", "3xtf32"):
+        # tf32 dense is half the bf16 dense rate (1.1 vs 2.25 PFLOP/s nominal)
+        return "tensor", d["bf16_tflops"] * (1.1 / 2.25), f"{how} bf16 x nominal tf32/bf16 ratio"
+    if prec == "fp32":
+        # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
+        return "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "derived: SM count x FP32 lanes x max clock"
+    # FP64: nominal per-GPU rate (no measured figure on this machine)
+    return "alu", 1.25, "nominal FP64 rate"
+
+
+class Clocks:
+    """Sample SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        import statistics
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class OracleSample:
+    """The oracle, as it is, on a bounded sample: sigma entries evaluated one by one."""
+
+    def __init__(self, cfg, seed):
+        import torch
+        from oracle import ccsd, sampled
+        from oracle.integrals import as_t
+        from paper_2604_12914_gb300.inputs import make_config, random_amplitudes
+
+        s = make_config(cfg, seed=seed)
+        self.cfg, self.o, self.v, self.naux = cfg, s.o, s.v, s.naux
+        L, eps = as_t(s.L), as_t(s.eps)
+        t0 = time.perf_counter()
+        t2 = ccsd.first_order_t2_from_L(eps, L, s.o)
+        self.E = sampled.EntrySigma(eps, L, torch.zeros(s.o, s.v, dtype=torch.complex128), t2)
+        x1, x2 = map(as_t, random_amplitudes(s.o, s.v, seed=seed + 1000))
+        self.E.set_x(x1, x2)
+        self.setup = time.perf_counter() - t0
+        self.threads = torch.get_num_threads()
+        import numpy as np
+        self.rng = np.random.default_rng(seed)
+
+    def sample(self, seconds):
+        o, v, E, rng = self.o, self.v, self.E, self.rng
+        n2 = n1 = 0
+        t2 = t1 = 0.0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds or n1 == 0:
+            i, j = rng.choice(o, 2, replace=False)
+            a, b = rng.choice(v, 2, replace=False)
+            ta = time.perf_counter()
+            E.sigma2(int(i), int(j), int(a), int(b))
+            t2 += time.perf_counter() - ta
+            n2 += 1
+            if n2 % 8 == 0 or n1 == 0:
+                ta = time.perf_counter()
+                E.sigma1(int(rng.integers(o)), int(rng.integers(v)))
+                t1 += time.perf_counter() - ta
+                n1 += 1
+        alg = algorithmic(o, v, self.naux)
+        # time of one vector = per-entry time x number of unique entries of each block
+        t_vec = (t2 / n2) * (alg["n_unique"] - o * v) + (t1 / n1) * (o * v)
+        return {"value": 1.0 / t_vec, "unit": "sigma-vectors/s", "cores": self.threads,
+                "kind": "oracle",
+                "sample": f"{n2} doubles + {n1} singles entries of sigma at {self.cfg} "
+                          f"(oracle.sampled, {t1 + t2:.1f} s; setup {self.setup:.1f} s excluded), "
+                          f"scaled by the {alg['n_unique']} unique amplitudes of one vector"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2604_12914_gb300.inputs import CONFIGS
+    c = CONFIGS[args.config]
+    S = OracleSample(args.config, 2)
+    per = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
+    vals = []
+    last = None
+    for k in range(args.warmup + args.steps):
+        last = S.sample(per)
+        if k >= args.warmup:
+            vals.append(last["value"])
+    v = sum(vals) / len(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sigma-vectors/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c128", "data": "synthetic (seeded; T1=0, first-order T2)",
+           "config": {"workload": f"{args.config} o={c['o']} v={c['v']} naux={c['naux']} single-RHS sigma"},
+           "cpu_baseline": {**last, "value": v},
+           "e2e": {"value": v, "unit": "sigma-vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "gpu_launches": 0}
+    print(json.dumps(out), flush=True)
+
+
+def run_cclr(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = OracleSample(args.config, 2).sample(args.cpu_seconds)   # before any GPU call
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import CONFIGS, make_config, random_amplitudes
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    s = make_config(args.config, seed=2)
+    o, v, naux = s.o, s.v, s.naux
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context(o, v, naux, s.eps, s.L, s.mu, prec=args.prec, stream=stream.cuda_stream)
+    x1h, x2h = random_amplitudes(o, v, seed=3 + rank)
+    x1 = torch.from_numpy(x1h).cuda()
+    x2 = torch.from_numpy(x2h).cuda()
+    s1 = torch.empty_like(x1)
+    s2 = torch.empty_like(x2)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        ctx.sigma_into(x1, x2, s1, s2)
+    barrier()
+    n0 = binding.cc_lr_launch_count()
+    lad = []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as ck:
+        torch.cuda.profiler.start()       # profiler range = the timed region (ncu --profile-from-start off)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.sigma_into(x1, x2, s1, s2)
+            lad.append(float(ctx.cc_lr_last_timings()[0]))
+        e1.record(stream)
+        barrier()
+        torch.cuda.profiler.stop()
+    ms = e0.elapsed_time(e1)
+    launches = binding.cc_lr_launch_count() - n0
+    ms_t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = world * args.steps / (ms_max / 1e3)
+    clk = ck.summary()
+
+    # end to end through the public API with host buffers (pinned)
+    x1p = torch.from_numpy(x1h).pin_memory()
+    x2p = torch.from_numpy(x2h).pin_memory()
+    s1p = torch.empty_like(x1p).pin_memory()
+    s2p = torch.empty_like(x2p).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        ctx.sigma_into(x1p, x2p, s1p, s2p)
+    barrier()
+    e0.record(stream)
+    for _ in range(args.steps):
+        ctx.sigma_into(x1p, x2p, s1p, s2p)
+    e1.record(stream)
+    barrier()
+    ms_e = torch.tensor([e0.elapsed_time(e1)], device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
+    e2e = world * args.steps / (float(ms_e.item()) / 1e3)
+    bytes_io = (x1p.numel() + x2p.numel()) * 16
+
+    alg = algorithmic(o, v, naux)
+    lad_ms = sum(lad) / len(lad)
+    bound, peak, how = ladder_peak(args.prec)
+    achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
+    ctx.close()
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"tf32": "c64-tf32", "3xtf32": "c64-3xtf32", "fp32": "c64", "fp64": "c128"}[args.prec],
+            "data": "synthetic (seeded; T1=0, first-order T2, random X)",
+            "config": {"workload": f"{args.config} o={o} v={v} naux={naux} single-RHS sigma",
+                       "precision_mode": args.prec, "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (X2 c128 %.2f GB, L~vv %.2f GB)" % (x2.numel() * 16 / 1e9, naux * v * v * 16 / 1e9)},
+            "roofline": {"kernel": "pp-ladder (formation + contraction)", "bound": bound,
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": how, "traffic": None,
+                         "ladder_ms": lad_ms, "ladder_share": lad_ms / (ms_max / args.steps)},
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": "sigma-vectors/s", "h2d_bytes_per_step": bytes_io,
+                    "d2h_bytes_per_step": bytes_io},
+            "gpu_launches": int(launches),
+        }
+        if cpu is not None:
+            out["cpu_baseline"] = cpu
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_cclr(a)

@@ -123,14 +123,18 @@ cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
 /* Switch the arithmetic of subsequent sigma / sigma^T / solves. */
 cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
 
-/* Device-side timing of the last cc_lr_sigma call, split by kernel family
- * (milliseconds): [0] pp-ladder, [1] other contractions, [2] elementwise/permute. */
+/* Device-side timing (CUDA events on the context's stream) of the last sigma or
+ * sigma^T vector, in milliseconds: [0] particle-particle ladder (formation of <ab|ef>~
+ * from L~_vv and its contraction with X), [1] every other kernel, [2] total. */
 cclr_status cc_lr_last_timings(cclr_ctx *ctx, double *ms3);
 
 void cc_lr_free(cclr_ctx *ctx);
 const char *cc_lr_strerror(cclr_status status);
 /* Thread-local text of the most recent failure (never NULL). */
 const char *cc_lr_last_error(void);
+
+/* Diagnostic: number of GPU kernels this library has launched in this process. */
+unsigned long long cc_lr_launch_count(void);
 
 #ifdef __cplusplus
 }

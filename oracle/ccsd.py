@@ -113,6 +113,15 @@ def first_order_t2(eps: torch.Tensor, g: torch.Tensor, no: int) -> torch.Tensor:
     return torch.einsum("abij->ijab", g[v, v, o, o]) / D
 
 
+def first_order_t2_from_L(eps: torch.Tensor, L: torch.Tensor, no: int) -> torch.Tensor:
+    """Same amplitudes as first_order_t2, with <ab|ij> = sum_P L^P_ai L^P_bj formed directly."""
+    Lvo = L[:, no:, :no]
+    w = torch.einsum("Pai,Pbj->ijab", Lvo, Lvo)
+    eo, ev = eps[:no], eps[no:]
+    D = eo[:, None, None, None] + eo[None, :, None, None] - ev[None, None, :, None] - ev[None, None, None, :]
+    return (w - w.transpose(0, 1)) / D
+
+
 # ---- unique-amplitude packing: vec = [t1 (o*v), t2 for i<j, a<b (P_o*P_v)] ----
 
 def pair_index(n: int):

@@ -59,8 +59,8 @@ def sigma_T(f, g, t1, t2, y1, y2):
     a2 = t2.detach().clone().requires_grad_(True)
     r1, r2 = ccsd.residual(f, g, a1, a2)
     gy1, gy2 = torch.autograd.grad((r1, r2), (a1, a2), grad_outputs=(y1.conj(), 0.25 * y2.conj()))
-    z1 = gy1.conj()
-    z2 = gy2.conj()
+    z1 = gy1.conj().resolve_conj()
+    z2 = gy2.conj().resolve_conj()
     # weight 1/4 on doubles and projection onto antisymmetric tensors
     z2 = _P(_P(z2, 0, 1), 2, 3)
     return z1, z2

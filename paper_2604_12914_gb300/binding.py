@@ -22,7 +22,7 @@ PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
            "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_last_timings",
-           "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error"]
+           "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
 
 class CclrError(RuntimeError):
@@ -67,6 +67,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_free": [P],
         "cc_lr_strerror": [I],
         "cc_lr_last_error": [],
+        "cc_lr_launch_count": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -75,6 +76,7 @@ def load(path: str = LIB_PATH):
     lib.cc_lr_free.restype = None
     lib.cc_lr_strerror.restype = ctypes.c_char_p
     lib.cc_lr_last_error.restype = ctypes.c_char_p
+    lib.cc_lr_launch_count.restype = ctypes.c_ulonglong
     _lib = lib
     return lib
 
@@ -157,6 +159,11 @@ class Context:
         _check(fn(self._h, nr, _ptr(x1), _ptr(x2), _ptr(s1), _ptr(s2)))
         return s1, s2
 
+    def sigma_into(self, x1, x2, s1, s2, nrhs=1, transpose=False):
+        """sigma (or sigma^T) of caller-owned arrays (host or device memory), no allocation."""
+        fn = load().cc_lr_sigma_T if transpose else load().cc_lr_sigma
+        _check(fn(self._h, nrhs, _ptr(x1), _ptr(x2), _ptr(s1), _ptr(s2)))
+
     def cc_lr_sigma_T(self, y1, y2):
         return self.cc_lr_sigma(y1, y2, transpose=True)
 
@@ -211,6 +218,10 @@ class Context:
         out = np.zeros(3, dtype=np.float64)
         _check(load().cc_lr_last_timings(self._h, _ptr(out)))
         return out
+
+
+def cc_lr_launch_count() -> int:
+    return int(load().cc_lr_launch_count())
 
 
 def cc_lr_strerror(status: int) -> str:

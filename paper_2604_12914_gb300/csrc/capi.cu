@@ -297,11 +297,13 @@ template <typename F> int guarded(F &&f) {
   }
 }
 
+// cudaMemcpyDefault: the direction follows from the pointers (unified addressing), so host
+// and device arrays are both accepted whatever device_ptrs said at init.
 void to_dev(cclr_ctx *c, const double *src, void *dst, size_t bytes) {
-  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, c->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->st));
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->st));
 }
 void from_dev(cclr_ctx *c, const void *src, double *dst, size_t bytes) {
-  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, c->device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st));
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->st));
 }
 }  // namespace
 
@@ -542,5 +544,7 @@ const char *cc_lr_strerror(cclr_status s) {
 }
 
 const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
+
+unsigned long long cc_lr_launch_count(void) { return cclr::launch_count(); }
 
 }  // extern "C"

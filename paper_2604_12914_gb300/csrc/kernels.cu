@@ -4,7 +4,13 @@
 // preconditioner, precision conversion).
 #include "kernels.cuh"
 
+#include <atomic>
+
 namespace cclr {
+
+static std::atomic<unsigned long long> g_launches{0};
+unsigned long long launch_count() { return g_launches.load(); }
+void count_launch(unsigned long long n) { g_launches += n; }
 
 // --------------------------------------------------------------------------------------
 // Complex GEMM, C[b](m,n) (+)= alpha * sum_k A[b](m,k) B[b](k,n); arbitrary strides.
@@ -121,6 +127,7 @@ void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st) {
       dim3 grid((unsigned)tiles, 1, (unsigned)nb);
       zgemm_simt<float, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g, b0);
     }
+    count_launch();
     CCLR_CUDA(cudaGetLastError());
   }
 }
@@ -171,7 +178,8 @@ void launch_permute(const PermArgs &a, int dt_in, int dt_out, cudaStream_t st) {
   else if (dt_in == C64 && dt_out == C64) permute_kernel<float, float><<<(unsigned)blocks, threads, 0, st>>>(a);
   else if (dt_in == C128 && dt_out == C64) permute_kernel<double, float><<<(unsigned)blocks, threads, 0, st>>>(a);
   else permute_kernel<float, double><<<(unsigned)blocks, threads, 0, st>>>(a);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // --------------------------------------------------------------------------------------
@@ -211,14 +219,16 @@ void vec_axpy(int dt, int64_t n, zc a, const void *x, void *y, cudaStream_t st) 
   if (n <= 0) return;
   if (dt == C128) axpy_kernel<double><<<grid_for(n), 256, 0, st>>>(n, a.re, a.im, (const double2 *)x, (double2 *)y);
   else axpy_kernel<float><<<grid_for(n), 256, 0, st>>>(n, a.re, a.im, (const float2 *)x, (float2 *)y);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 void vec_scal(int dt, int64_t n, zc a, void *y, cudaStream_t st) {
   if (n <= 0) return;
   if (dt == C128) scal_kernel<double><<<grid_for(n), 256, 0, st>>>(n, a.re, a.im, (double2 *)y);
   else scal_kernel<float><<<grid_for(n), 256, 0, st>>>(n, a.re, a.im, (float2 *)y);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // Dot products with FP64 accumulation: mode 0 bilinear sum x*y, mode 1 Hermitian
@@ -290,7 +300,8 @@ void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 
   if (dt == C128) dot_partial<double><<<nb, 256, 0, st>>>(n, (const double2 *)x, (const double2 *)y, herm, part);
   else dot_partial<float><<<nb, 256, 0, st>>>(n, (const float2 *)x, (const float2 *)y, herm, part);
   dot_final<<<1, 256, 0, st>>>(nb, part, out, slot);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch(2);
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // Delta = r / (D - omega), D real; in place allowed.
@@ -314,7 +325,8 @@ void vec_precond(int dt, int64_t n, const double *D, double omega, const void *r
   if (n <= 0) return;
   if (dt == C128) precond_kernel<double><<<grid_for(n), 256, 0, st>>>(n, D, omega, (const double2 *)r, (double2 *)out);
   else precond_kernel<float><<<grid_for(n), 256, 0, st>>>(n, D, omega, (const float2 *)r, (float2 *)out);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // D1[i,a] = Fvv_aa - Foo_ii ; D2[i,j,a,b] = Fvv_aa + Fvv_bb - Foo_ii - Foo_jj (real parts).
@@ -342,7 +354,8 @@ void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, doub
                 cudaStream_t st) {
   int64_t n = (int64_t)o * v * (1 + (int64_t)o * v);
   diag_kernel<<<grid_for(n), 256, 0, st>>>(o, v, (const double2 *)Foo, (const double2 *)Fvv, D1, D2);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // t2[i,j,a,b] = w[i,j,a,b] / (e_i + e_j - e_a - e_b)
@@ -364,7 +377,8 @@ __global__ void denom_kernel(int o, int v, const double *eps, double2 *t2) {
 void apply_denominator(int o, int v, const double *eps, void *t2, cudaStream_t st) {
   int64_t n = (int64_t)o * o * v * v;
   denom_kernel<<<grid_for(n), 256, 0, st>>>(o, v, eps, (double2 *)t2);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 // out[p,q] = value on the diagonal (complex128 square matrix), used for diag(eps).
@@ -375,7 +389,8 @@ __global__ void set_diag_kernel(int n, const double *d, double2 *out) {
 
 void set_diag(int n, const double *d, void *out, cudaStream_t st) {
   set_diag_kernel<<<(n + 255) / 256, 256, 0, st>>>(n, d, (double2 *)out);
-  CCLR_CUDA(cudaGetLastError());
+  count_launch();
+    CCLR_CUDA(cudaGetLastError());
 }
 
 }  // namespace cclr

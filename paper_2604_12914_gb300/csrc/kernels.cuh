@@ -30,6 +30,10 @@ struct PermArgs {
   int64_t total = 0;
 };
 
+// Number of kernels this library has launched (all streams, process lifetime).
+unsigned long long launch_count();
+void count_launch(unsigned long long n = 1);
+
 void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st);
 void launch_permute(const PermArgs &a, int dt_in, int dt_out, cudaStream_t st);
 void vec_axpy(int dt, int64_t n, zc a, const void *x, void *y, cudaStream_t st);

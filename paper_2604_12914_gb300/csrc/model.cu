@@ -23,7 +23,8 @@ Model::Model(int o_, int v_, int naux_, cudaStream_t st_)
 Model::~Model() {}
 
 static void h2d_or_d2d(void *dst, const void *src, size_t bytes, int device_ptrs, cudaStream_t st) {
-  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  (void)device_ptrs;  // unified addressing: the copy direction follows from the pointers
+  CCLR_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st));
 }
 
 void Model::upload_inputs(const double *eps_h, const double *L, const double *mu_h,
@@ -282,6 +283,21 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
   for (int k = 4; k < nv; ++k) ptr[k] = tv[k].p;
   auto V = [&](int id) { return var_tens(id, dt, ptr[id]); };
   auto Cst = [&](int id) { return C.t[id]; };
+  if (!tm.made) {
+    for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
+    tm.made = true;
+  }
+  float lad_ms = 0.f;
+  auto run_ladder = [&](int d, zc a, const Tens &in, const Tens &out) {
+    CCLR_CUDA(cudaEventRecord(tm.ev[1], st));
+    ladder(d, C, a, in, out);
+    CCLR_CUDA(cudaEventRecord(tm.ev[2], st));
+    CCLR_CUDA(cudaEventSynchronize(tm.ev[2]));
+    float ms = 0.f;
+    CCLR_CUDA(cudaEventElapsedTime(&ms, tm.ev[1], tm.ev[2]));
+    lad_ms += ms;
+  };
+  CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
   if (dir > 0) {
     ptr[0] = (void *)x1; ptr[1] = (void *)x2; ptr[2] = s1; ptr[3] = s2;
     E.zero(V(2));
@@ -291,7 +307,7 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
         case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.in), op.mi, V(op.out), op.mo); break;
         case OP_PERM: E.permute(op.alpha, V(op.in), op.mi, V(op.out), op.mo, true); break;
         case OP_ZERO: E.zero(V(op.out)); break;
-        case OP_LADDER: ladder(+1, C, op.alpha, V(op.in), V(op.out)); break;
+        case OP_LADDER: run_ladder(+1, op.alpha, V(op.in), V(op.out)); break;
       }
     }
   } else {
@@ -311,7 +327,7 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
         case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.out), op.mo, V(op.in), op.mi); break;
         case OP_PERM: E.permute(op.alpha, V(op.out), op.mo, V(op.in), op.mi, true); break;
         case OP_ZERO: E.zero(V(op.out)); break;
-        case OP_LADDER: ladder(-1, C, op.alpha, V(op.out), V(op.in)); break;
+        case OP_LADDER: run_ladder(-1, op.alpha, V(op.out), V(op.in)); break;
       }
     }
     Tens out2 = var_tens(3, dt, s2);
@@ -321,6 +337,13 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
     E.permute(zc(-1), z2, "ijab", out2, "ijba", true);
     E.permute(zc(1), z2, "ijab", out2, "jiba", true);
   }
+  CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
+  CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
+  float tot = 0.f;
+  CCLR_CUDA(cudaEventElapsedTime(&tot, tm.ev[0], tm.ev[3]));
+  ms_last[0] = lad_ms;
+  ms_last[1] = tot - lad_ms;
+  ms_last[2] = tot;
 }
 
 // xi^B_ia = mu~_ai + sum_me mu~_me t_im^ae ;

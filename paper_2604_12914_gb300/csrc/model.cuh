@@ -72,7 +72,8 @@ class Model {
   std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision
   int prec = 0;
   DevBuf ladW;                      // ladder formation scratch
-  float ms_last[3] = {0, 0, 0};
+  float ms_last[3] = {0, 0, 0};   // last apply(): ladder, everything else, total (ms)
+  Timers tm;
 
   void upload_inputs(const double *eps_h, const double *L, const double *mu_h,
                      const double *t1_h, const double *t2_h, int device_ptrs);

@@ -102,7 +102,7 @@ def test_xi_matches_oracle():
     ctx.close()
 
 
-def _converged_small(o=3, v=8, naux=12, seed=5, scale=0.3):
+def _converged_small(o=3, v=8, naux=12, seed=5, scale=0.2):
     s = make_system(o, v, naux, seed=seed, scale=scale)
     f, g, L, _, _ = oracle_setup(s, np.zeros((o, v)), np.zeros((o, o, v, v)))
     t1, t2, _ = R.solve_ccsd(f, g, o, L=L)

@@ -256,3 +256,25 @@ def test_first_order_amplitudes_cancel_first_order_residual():
         res.append(float(r2.abs().max()))
     # remaining residual is second order in the interaction
     assert 3.5 < res[1] / res[0] < 4.5
+
+
+def test_entrywise_sigma_matches_term_list():
+    """oracle.sampled (per-entry, Cholesky on the fly) = jacobian.sigma_terms entry by entry."""
+    from oracle import sampled
+    o, v = 4, 9
+    s = _system(o, v, 13, seed=3, scale=0.5, t1_scale=0.2)
+    L = as_t(s.L)
+    f = torch.diag(as_t(s.eps).to(C))
+    _, a2 = random_amplitudes(o, v, seed=9, s1=0.2, s2=0.3)
+    t1, t2 = as_t(s.t1), as_t(a2)
+    x1, x2 = map(as_t, random_amplitudes(o, v, seed=11))
+    q1, q2 = J.sigma_terms(J.Dressed(f, L, t1, t2), x1, x2)
+    E = sampled.EntrySigma(as_t(s.eps), L, t1, t2)
+    E.set_x(x1, x2)
+    rng = np.random.default_rng(1)
+    sc = float(q2.abs().max())
+    for _ in range(12):
+        i, j = rng.integers(0, o, 2)
+        a, b = rng.integers(0, v, 2)
+        assert abs(E.sigma2(i, j, a, b) - q2[i, j, a, b]) < 1e-12 * sc
+        assert abs(E.sigma1(i, a) - q1[i, a]) < 1e-12 * sc
