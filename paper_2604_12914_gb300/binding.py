@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_strerror": [I],
         "cc_lr_last_error": [],
         "cc_lr_launch_count": [],
+        "cc_lr_selftest_gemm": [I, I, I, I, ctypes.c_uint, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +219,13 @@ class Context:
         out = np.zeros(3, dtype=np.float64)
         _check(load().cc_lr_last_timings(self._h, _ptr(out)))
         return out
+
+
+def cc_lr_selftest_gemm(M, N, K, mode, seed=1):
+    """(tensor-core error, FP32 CUDA-core error) of a random complex64 GEMM vs FP64."""
+    err = np.zeros(2, dtype=np.float64)
+    _check(load().cc_lr_selftest_gemm(M, N, K, mode, seed, _ptr(err)))
+    return float(err[0]), float(err[1])
 
 
 def cc_lr_launch_count() -> int:

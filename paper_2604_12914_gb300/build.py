@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libcclr.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kernels.cu", "engine.cu", "model.cu", "capi.cu", "ladder_tc.cu"]
+SOURCES = ["kernels.cu", "engine.cu", "model.cu", "capi.cu", "tc_gemm.cu", "ladder_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -52,7 +52,7 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(lambda s: _compile(s, verbose), srcs))
     if os.path.exists(OUT) and os.path.getmtime(OUT) >= max(os.path.getmtime(o) for o in objs):
         return OUT
-    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT + ".tmp", *objs, "-lcuda"]
+    cmd = [nvcc(), *ARCH, "-shared", "-o", OUT + ".tmp", *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -7,7 +7,11 @@
 #include <memory>
 
 #include "../../include/cclr.h"
+#include "../../include/cclr_testing.h"
+
+#include <random>
 #include "model.cuh"
+#include "tc_gemm.cuh"
 
 using namespace cclr;
 using zd = std::complex<double>;
@@ -546,5 +550,52 @@ const char *cc_lr_strerror(cclr_status s) {
 const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
 
 unsigned long long cc_lr_launch_count(void) { return cclr::launch_count(); }
+
+int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *err) {
+  if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || !err) return fail(CCLR_EINVAL, "bad selftest arguments");
+  return guarded([&] {
+    std::mt19937_64 g(seed);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<double> a((size_t)2 * M * K), b((size_t)2 * K * N);
+    for (auto &x : a) x = nd(g);
+    for (auto &x : b) x = nd(g);
+    Engine E;
+    CCLR_CUDA(cudaStreamCreate(&E.st));
+    DevBuf A128((size_t)M * K * 16), B128((size_t)K * N * 16), C128b((size_t)M * N * 16);
+    DevBuf A64((size_t)M * K * 8), B64((size_t)K * N * 8), Ct((size_t)M * N * 8), Cs((size_t)M * N * 8);
+    CCLR_CUDA(cudaMemcpy(A128.p, a.data(), a.size() * 8, cudaMemcpyHostToDevice));
+    CCLR_CUDA(cudaMemcpy(B128.p, b.data(), b.size() * 8, cudaMemcpyHostToDevice));
+    Tens a128 = make_tens(A128.p, C128, {M, K}), b128 = make_tens(B128.p, C128, {K, N});
+    Tens a64 = make_tens(A64.p, C64, {M, K}), b64 = make_tens(B64.p, C64, {K, N});
+    Tens c128 = make_tens(C128b.p, C128, {M, N}), ct = make_tens(Ct.p, C64, {M, N}), cs = make_tens(Cs.p, C64, {M, N});
+    E.permute(zc(1), a128, "mk", a64, "mk", false);
+    E.permute(zc(1), b128, "kn", b64, "kn", false);
+    E.zero(c128); E.zero(ct); E.zero(cs);
+    E.contract(zc(1), a128, "mk", b128, "kn", c128, "mn");
+    E.tc_mode = mode;
+    E.tc_force = true;
+    E.contract(zc(1), a64, "mk", b64, "kn", ct, "mn");
+    E.tc_force = false;
+    const bool used_tc = E.tc_calls > 0;
+    E.tc_mode = 0;
+    E.contract(zc(1), a64, "mk", b64, "kn", cs, "mn");
+    CCLR_CUDA(cudaStreamSynchronize(E.st));
+    if (tc_error(E.st)) throw Error(CCLR_ETIMEOUT, "tensor-core kernel gave up on a bounded wait");
+    std::vector<double> r((size_t)2 * M * N);
+    std::vector<float> t((size_t)2 * M * N), q((size_t)2 * M * N);
+    CCLR_CUDA(cudaMemcpy(r.data(), C128b.p, r.size() * 8, cudaMemcpyDeviceToHost));
+    CCLR_CUDA(cudaMemcpy(t.data(), Ct.p, t.size() * 4, cudaMemcpyDeviceToHost));
+    CCLR_CUDA(cudaMemcpy(q.data(), Cs.p, q.size() * 4, cudaMemcpyDeviceToHost));
+    double mx = 0, e1 = 0, e2 = 0;
+    for (size_t i = 0; i < r.size(); ++i) {
+      mx = std::max(mx, std::abs(r[i]));
+      e1 = std::max(e1, std::abs(r[i] - (double)t[i]));
+      e2 = std::max(e2, std::abs(r[i] - (double)q[i]));
+    }
+    err[0] = used_tc ? e1 / mx : -1.0;
+    err[1] = e2 / mx;
+    CCLR_CUDA(cudaStreamDestroy(E.st));
+  });
+}
 
 }  // extern "C"

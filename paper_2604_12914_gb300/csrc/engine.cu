@@ -4,6 +4,7 @@
 #include <atomic>
 
 #include "engine.cuh"
+#include "tc_gemm.cuh"
 
 namespace cclr {
 
@@ -200,6 +201,33 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
       permute(zc(1.0), B, mb, T, order, false);
       g.B = T.p; g.sBb = K * N; g.sBk = N; g.sBn = 1;
     }
+  }
+  // complex64 on tensor cores: operands prepared from the strided views, result written as
+  // interleaved complex pairs straight into C when its N modes are contiguous.
+  if (dt == C64 && tc_mode && nb <= 16 &&
+      (tc_force || ((double)M * N * K >= 3.0e7 && M >= 16 && K >= 8))) {
+    const int seg = tc_mode == 2 ? 3 : 1;
+    const int64_t ld = 2 * tc_kpad(K) * seg;
+    float *Ao = (float *)ws(3, (size_t)M * ld * 4);
+    float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
+    int64_t c0, c1, c2, zz;
+    bool direct = group_view(C, mc, bat, zz, c0) && group_view(C, mc, Mm, zz, c1) &&
+                  group_view(C, mc, Nm, zz, c2) && (N == 1 || c2 == 1);
+    Tens T;
+    if (!direct) {
+      std::string order = bat + Mm + Nm;
+      T = contiguous_like(ws(2, nb * M * N * es), dt, C, mc, order);
+      c0 = M * N; c1 = N; c2 = 1;
+    }
+    for (int64_t b = 0; b < nb; ++b) {
+      tc_prep_a((const char *)g.A + b * g.sAb * es, g.sAm, g.sAk, M, K, seg, Ao, ld, st);
+      tc_prep_b((const char *)g.B + b * g.sBb * es, g.sBk, g.sBn, K, N, seg, Bo, ld, st);
+      float *Cp = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
+      tc_gemm_seg(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, 2 * c1, alpha, direct, st);
+      ++tc_calls;
+    }
+    if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);
+    return;
   }
   // C as [batch][M][N]
   int64_t s0, s1, s2, z;

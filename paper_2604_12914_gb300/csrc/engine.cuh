@@ -32,6 +32,11 @@ size_t device_bytes_in_use();
 class Engine {
  public:
   cudaStream_t st = nullptr;
+  // complex64 contractions above a size threshold run on the tcgen05 tensor cores:
+  // 0 = never (CUDA-core FP32), 1 = TF32, 2 = 3xTF32 split.
+  int tc_mode = 0;
+  bool tc_force = false;  // route every complex64 contraction to the tensor cores (self-test)
+  int64_t tc_calls = 0;
   // Workspace slot s of at least `bytes` bytes (grown on demand, reused across calls).
   void *ws(int slot, size_t bytes);
   // C[mc] += alpha * sum A[ma] B[mb] over the modes not in mc (einsum semantics; every

@@ -1,0 +1,237 @@
+// Packed particle-particle ladder on tcgen05 tensor cores; see ladder_tc.cuh.
+#include <vector>
+
+#include "ladder_tc.cuh"
+#include "tc_gemm.cuh"
+
+namespace cclr {
+namespace {
+
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0x1000u) & 0xFFFFE000u;
+  return __uint_as_float(u);
+}
+
+// store complex value v as element k of an A-format row (K-major, [hi|hi|lo] when seg = 3)
+__device__ __forceinline__ void put_a(float *row, int64_t k, int64_t Kp, int seg, float2 v) {
+  if (seg == 1) {
+    row[2 * k] = v.x;
+    row[2 * k + 1] = v.y;
+  } else {
+    const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
+    row[2 * k] = hr; row[2 * k + 1] = hi;
+    row[2 * Kp + 2 * k] = hr; row[2 * Kp + 2 * k + 1] = hi;
+    row[4 * Kp + 2 * k] = v.x - hr; row[4 * Kp + 2 * k + 1] = v.y - hi;
+  }
+}
+
+// store complex value v as element k of the embedded B rows r0 (re, -im), r1 (im, re)
+__device__ __forceinline__ void put_b(float *r0, float *r1, int64_t k, int64_t Kp, int seg, float2 v) {
+  if (seg == 1) {
+    r0[2 * k] = v.x; r0[2 * k + 1] = -v.y; r1[2 * k] = v.y; r1[2 * k + 1] = v.x;
+  } else {
+    const float hr = tf32_hi(v.x), hi = tf32_hi(v.y), lr = v.x - hr, li = v.y - hi;
+    r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
+    r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
+    r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
+  }
+}
+
+// Packed X as the contraction B operand: B(k = (e<f), n = (i<j)) = X[i,j,e,f].
+__global__ void pack_x_b(const float2 *X, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
+                         int64_t Pv, int64_t Kp, int seg, float *dst, int64_t ldd) {
+  const int64_t total = Po * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / Kp, k = e % Kp;
+    float2 val = make_float2(0.f, 0.f);
+    if (k < Pv) {
+      const int2 ij = op[n], ef = vp[k];
+      val = X[(((int64_t)ij.x * o + ij.y) * v + ef.x) * v + ef.y];
+    }
+    put_b(dst + (2 * n) * ldd, dst + (2 * n + 1) * ldd, k, Kp, seg, val);
+  }
+}
+
+// Y (transpose direction) as the A operand over a group of (a<b) pairs:
+// A(m = (i<j), k = r) = Y[i,j,a,b] - Y[j,i,a,b] - Y[i,j,b,a] + Y[j,i,b,a], (a,b) = pair(p0 + r).
+__global__ void pack_y_a(const float2 *Y, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
+                         int64_t p0, int64_t np, int64_t Kp, int seg, float *dst, int64_t ldd) {
+  const int64_t total = Po * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e / Kp, k = e % Kp;
+    float2 val = make_float2(0.f, 0.f);
+    if (k < np) {
+      const int2 ij = op[m], ab = vp[p0 + k];
+      const int64_t i = ij.x, j = ij.y, a = ab.x, b = ab.y;
+      const float2 y1 = Y[((i * o + j) * v + a) * v + b], y2 = Y[((j * o + i) * v + a) * v + b];
+      const float2 y3 = Y[((i * o + j) * v + b) * v + a], y4 = Y[((j * o + i) * v + b) * v + a];
+      val = make_float2(y1.x - y2.x - y3.x + y4.x, y1.y - y2.y - y3.y + y4.y);
+    }
+    put_a(dst + m * ldd, k, Kp, seg, val);
+  }
+}
+
+// Antisymmetrised packed block of the group, from W[(b - a0) v + f][(a - a0) v + e] = <ab|ef>~:
+//   <ab||ef>~ = W[(b-a0)v+f][(a-a0)v+e] - W[(b-a0)v+e][(a-a0)v+f],  a in group, b > a, e < f.
+// mode 0: A operand rows r = (a,b) pair - p0, K = (e<f)      (forward contraction)
+// mode 1: B operand rows 2(e<f), 2(e<f)+1, K = r              (transpose contraction)
+__global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *vp, int64_t p0,
+                       int64_t np, int64_t Pv, int64_t Kp, int seg, int mode, float *dst, int64_t ldd) {
+  const int64_t total = mode == 0 ? np * Kp : Pv * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r, q;  // r: (a,b) pair within the group; q: (e<f) pair
+    if (mode == 0) { r = e / Kp; q = e % Kp; } else { q = e / Kp; r = e % Kp; }
+    const bool inside = mode == 0 ? (q < Pv) : (r < np);
+    float2 val = make_float2(0.f, 0.f);
+    if (inside) {
+      const int2 ab = vp[p0 + r], ef = vp[q];
+      const int64_t rb = (int64_t)(ab.y - a0) * v, ca = (int64_t)(ab.x - a0) * v;
+      const float2 w1 = W[(rb + ef.y) * ldw + ca + ef.x];
+      const float2 w2 = W[(rb + ef.x) * ldw + ca + ef.y];
+      val = make_float2(w1.x - w2.x, w1.y - w2.y);
+    }
+    if (mode == 0) put_a(dst + r * ldd, q, Kp, seg, val);
+    else put_b(dst + (2 * q) * ldd, dst + (2 * q + 1) * ldd, r, Kp, seg, val);
+  }
+}
+
+// out[i,j,a,b] += alpha * S[(ab)][(ij)] with the four antisymmetric images (S [Pv][Po]).
+__global__ void unpack_sig(const float2 *S, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
+                           int64_t Pv, float ar, float ai, float2 *out) {
+  const int64_t total = Po * Pv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / Pv, k = e % Pv;  // n = (i<j), k = (a<b)
+    const int2 ij = op[n], ab = vp[k];
+    const float2 s = S[k * Po + n];
+    const float2 val = make_float2(ar * s.x - ai * s.y, ar * s.y + ai * s.x);
+    const int64_t i = ij.x, j = ij.y, a = ab.x, b = ab.y;
+    float2 *p;
+    p = out + ((i * o + j) * v + a) * v + b; p->x += val.x; p->y += val.y;
+    p = out + ((j * o + i) * v + a) * v + b; p->x -= val.x; p->y -= val.y;
+    p = out + ((i * o + j) * v + b) * v + a; p->x -= val.x; p->y -= val.y;
+    p = out + ((j * o + i) * v + b) * v + a; p->x += val.x; p->y += val.y;
+  }
+}
+
+// out[i,j,e,f] += alpha * Z[(ij)][(ef)] for i<j, e<f only (Z [Po][Pv]).
+__global__ void unpack_z(const float2 *Z, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
+                         int64_t Pv, float ar, float ai, float2 *out) {
+  const int64_t total = Po * Pv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n = e / Pv, k = e % Pv;
+    const int2 ij = op[n], ef = vp[k];
+    const float2 z = Z[n * Pv + k];
+    float2 *p = out + (((int64_t)ij.x * o + ij.y) * v + ef.x) * v + ef.y;
+    p->x += ar * z.x - ai * z.y;
+    p->y += ar * z.y + ai * z.x;
+  }
+}
+
+unsigned grid1d(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+}
+
+std::vector<int2> pairs(int n) {
+  std::vector<int2> t;
+  t.reserve((size_t)n * (n - 1) / 2);
+  for (int p = 0; p < n; ++p)
+    for (int q = p + 1; q < n; ++q) t.push_back(make_int2(p, q));
+  return t;
+}
+
+int64_t pair_start(int v, int a) { return (int64_t)a * v - (int64_t)a * (a + 1) / 2; }
+
+}  // namespace
+
+void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg) {
+  cudaStream_t st = E.st;
+  o_ = o; v_ = v; naux_ = naux; seg_ = seg;
+  Po_ = (int64_t)o * (o - 1) / 2;
+  Pv_ = (int64_t)v * (v - 1) / 2;
+  const int64_t ld = 2 * tc_kpad(naux) * seg;
+  const int64_t vv = (int64_t)v * v;
+  LA.alloc((size_t)vv * ld * 4);
+  LB.alloc((size_t)2 * vv * ld * 4);
+  // A(m = (b,f), k = P) = L[P,b,f]; B(k = P, n = (a,e)) = L[P,a,e]
+  tc_prep_a(Lvv.p, 1, vv, vv, naux, seg, LA.as<float>(), ld, st);
+  tc_prep_b(Lvv.p, vv, 1, naux, vv, seg, LB.as<float>(), ld, st);
+  auto op = pairs(o), vp = pairs(v);
+  opairs.alloc(std::max<size_t>(1, op.size()) * sizeof(int2));
+  vpairs.alloc(std::max<size_t>(1, vp.size()) * sizeof(int2));
+  if (!op.empty()) CCLR_CUDA(cudaMemcpyAsync(opairs.p, op.data(), op.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  if (!vp.empty()) CCLR_CUDA(cudaMemcpyAsync(vpairs.p, vp.data(), vp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+  CCLR_CUDA(cudaStreamSynchronize(st));
+}
+
+void LadderTC::apply(Engine &E, int dir, zc alpha, const void *in, void *out) {
+  cudaStream_t st = E.st;
+  const int o = o_, v = v_, seg = seg_;
+  const int64_t Po = Po_, Pv = Pv_;
+  if (Po == 0 || Pv == 0) return;
+  const int64_t vv = (int64_t)v * v;
+  const int64_t ldL = 2 * tc_kpad(naux_) * seg;
+  const int64_t KpPv = tc_kpad(Pv), ldPv = 2 * KpPv * seg;
+  const int ga = std::min(ga_, v);
+  // buffers sized for the first (largest) group
+  const int64_t maxpairs = pair_start(v, ga);
+  if (W.bytes < (size_t)vv * ga * v * 8) W.alloc((size_t)vv * ga * v * 8);
+  const int64_t kpg = tc_kpad(maxpairs);
+  const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldPv * 4 : (size_t)2 * Pv * (2 * kpg * seg) * 4;
+  if (Wp.bytes < wp_bytes) Wp.alloc(wp_bytes);
+  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * ldPv * 4 : (size_t)Po * (2 * kpg * seg) * 4;
+  if (Xp.bytes < xp_bytes) Xp.alloc(xp_bytes);
+  if (sig.bytes < (size_t)Po * Pv * 8) sig.alloc((size_t)Po * Pv * 8);
+  const int2 *op = opairs.as<int2>(), *vp = vpairs.as<int2>();
+  if (dir > 0) {
+    pack_x_b<<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in, o, v, op, vp, Po, Pv, KpPv, seg, Xp.as<float>(), ldPv);
+    count_launch();
+  } else {
+    CCLR_CUDA(cudaMemsetAsync(sig.p, 0, (size_t)Po * Pv * 8, st));
+  }
+  for (int a0 = 0; a0 < v - 1; a0 += ga) {
+    const int a1 = std::min(v, a0 + ga);
+    const int64_t p0 = pair_start(v, a0), np = pair_start(v, a1) - p0;
+    if (np == 0) continue;
+    // formation: W[(b - a0, f)][(a - a0, e)] = sum_P L[P,b,f] L[P,a,e], b >= a0
+    const int64_t rows = (int64_t)(v - a0) * v, cols = (int64_t)(a1 - a0) * v;
+    tc_gemm_seg(LA.as<float>() + (int64_t)a0 * v * ldL, ldL, LB.as<float>() + 2 * (int64_t)a0 * v * ldL, ldL,
+                rows, 2 * cols, ldL / seg, seg, W.as<float>(), 2 * cols, zc(1.0), false, st);
+    if (dir > 0) {
+      pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
+                                                Wp.as<float>(), ldPv);
+      count_launch();
+      // sigT[(ab)][(ij)] = sum_{e<f} <ab||ef>~ X[i,j,e,f]  for the group's pairs
+      tc_gemm_seg(Wp.as<float>(), ldPv, Xp.as<float>(), ldPv, np, 2 * Po, ldPv / seg, seg,
+                  sig.as<float>() + 2 * p0 * Po, 2 * Po, zc(1.0), false, st);
+    } else {
+      const int64_t kg = tc_kpad(np), ldg = 2 * kg * seg;
+      pack_w<<<grid1d(Pv * kg), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, kg, seg, 1,
+                                              Wp.as<float>(), ldg);
+      count_launch();
+      pack_y_a<<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in, o, v, op, vp, Po, p0, np, kg, seg,
+                                                 Xp.as<float>(), ldg);
+      count_launch();
+      // Z[(ij)][(ef)] += sum_{(ab) in group} Y'[(ij)][(ab)] <ab||ef>~
+      tc_gemm_seg(Xp.as<float>(), ldg, Wp.as<float>(), ldg, Po, 2 * Pv, ldg / seg, seg, sig.as<float>(),
+                  2 * Pv, zc(1.0), true, st);
+    }
+    CCLR_CUDA(cudaGetLastError());
+  }
+  if (dir > 0) {
+    unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>(), o, v, op, vp, Po, Pv, (float)alpha.re,
+                                                 (float)alpha.im, (float2 *)out);
+  } else {
+    unpack_z<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>(), o, v, op, vp, Po, Pv, (float)alpha.re,
+                                               (float)alpha.im, (float2 *)out);
+  }
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+}  // namespace cclr

@@ -1,0 +1,31 @@
+// Particle-particle ladder on tcgen05 tensor cores (complex64 data, TF32 or 3xTF32):
+//   out[i,j,a,b] += alpha * sum_{e<f} <ab||ef>~ X[i,j,e,f],   <ab|ef>~ = sum_P L~[P,a,e] L~[P,b,f]
+// over packed pairs i<j, a<b, e<f (the four antisymmetric images of each output are written).
+// <ab|ef>~ is formed on the fly from L~_vv for one group of a at a time and never stored
+// whole: formation GEMM (rows (b,f), b >= a0; columns (a,e), a in the group; K = naux),
+// antisymmetrise/pack to <ab||ef>~ over (a<b) x (e<f), contraction GEMM with packed X.
+// The transpose product (dir -1) contracts the same packed block over (a<b) instead.
+#pragma once
+#include "engine.cuh"
+
+namespace cclr {
+
+class LadderTC {
+ public:
+  // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (TF32) or 3 (3xTF32).
+  void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg);
+  bool ready(int seg) const { return seg_ == seg && LA.p != nullptr; }
+  // dir +1: out += alpha * ladder(in);  dir -1: out += alpha * ladder^T(in).
+  // in/out: complex64 [o][o][v][v].
+  void apply(Engine &E, int dir, zc alpha, const void *in, void *out);
+
+ private:
+  int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0;
+  int64_t Po_ = 0, Pv_ = 0;
+  DevBuf LA, LB;            // formation operands: rows (b,f) and embedded rows (a,e), K = naux
+  DevBuf opairs, vpairs;    // pair tables (p, q), p < q, row-major pair order
+  DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result
+  int ga_ = 32;             // a values per group
+};
+
+}  // namespace cclr

@@ -11,6 +11,7 @@
 // and the vvvv / vovv / vvvo elements are never stored: they enter sigma through L~_vv
 // (the "higher-rank integrals evaluated on the fly" of Sec. 3).
 #include "model.cuh"
+#include "tc_gemm.cuh"
 
 namespace cclr {
 
@@ -261,6 +262,15 @@ Tens Model::var_tens(int id, int dt, void *p) const {
 // chunks of a from L~_vv and never stored whole.
 void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out) {
   const int dt = C.dt;
+  if (dt == C64 && E.tc_mode) {
+    const int seg = E.tc_mode == 2 ? 3 : 1;
+    if (!ltc.ready(seg) || ltc_src != C.t[K_LVV].p) {
+      ltc.prepare(E, C.t[K_LVV], o, v, naux, seg);
+      ltc_src = C.t[K_LVV].p;
+    }
+    ltc.apply(E, dir, alpha, in.p, out.p);
+    return;
+  }
   const Tens &Lvv = C.t[K_LVV];
   const int64_t per_a = (int64_t)v * v * v * dt_size(dt);
   int64_t ac = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_a));
@@ -277,6 +287,8 @@ void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Ten
 
 void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2) {
   const int dt = C.dt;
+  // tensor cores for complex64: TF32 (prec 1) or 3xTF32 (prec 2); FP32 CUDA cores for prec 3
+  E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : 0) : 0;
   auto &tv = temps(dt);
   const int nv = (int)prog.vars.size();
   std::vector<void *> ptr(nv, nullptr);
@@ -344,6 +356,7 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
   ms_last[0] = lad_ms;
   ms_last[1] = tot - lad_ms;
   ms_last[2] = tot;
+  if (E.tc_mode && tc_error(st)) throw Error(5, "a tensor-core kernel gave up on a bounded wait");
 }
 
 // xi^B_ia = mu~_ai + sum_me mu~_me t_im^ae ;

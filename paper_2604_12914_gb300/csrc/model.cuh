@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "ladder_tc.cuh"
 
 namespace cclr {
 
@@ -71,7 +72,9 @@ class Model {
   Program prog;
   std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision
   int prec = 0;
-  DevBuf ladW;                      // ladder formation scratch
+  DevBuf ladW;                      // ladder formation scratch (CUDA-core path)
+  LadderTC ltc;                     // packed tensor-core ladder (complex64 modes)
+  const void *ltc_src = nullptr;
   float ms_last[3] = {0, 0, 0};   // last apply(): ladder, everything else, total (ms)
   Timers tm;
 

@@ -1,0 +1,404 @@
+// tcgen05 TF32 GEMM for sm_103a: TMA (128-byte swizzle) -> 4-stage shared-memory ring ->
+// tcgen05.mma issued by one thread -> FP32 accumulator in TMEM -> tcgen05.ld epilogue.
+// Every mbarrier wait is bounded (globaltimer); on timeout the kernel raises a device
+// flag, drains its own copies with a bounded wait, frees its TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "tc_gemm.cuh"
+
+namespace cclr {
+namespace {
+
+constexpr int BM = 128;      // UMMA M
+constexpr int BK = 32;       // fp32 elements per K block = 128 bytes = one swizzle row
+constexpr int STAGES = 4;
+constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
+
+struct TcParams {
+  int M, N, K, BN;
+  float *C;
+  long long ldc;
+  float ar, ai;
+  int accumulate;
+  int *err;
+};
+
+__device__ __forceinline__ uint32_t su32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtime() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (gtime() - t0 > TIMEOUT_NS) {
+      atomicExch(err, 1);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+      :
+      : "r"(su32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused with 128B swizzle)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                         uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+      :
+      : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__global__ void __launch_bounds__(128, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   TcParams p) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int BN = p.BN;
+  float *sA = (float *)smem;
+  float *sB = (float *)(smem + STAGES * BM * BK * 4);
+  uint64_t *bars = (uint64_t *)(smem + STAGES * (BM + BN) * BK * 4);  // full[S], empty[S], acc
+  uint32_t *tslot = (uint32_t *)(bars + 2 * STAGES + 1);
+  int *progress = (int *)(tslot + 1);  // [0] loads issued, [1] stages consumed
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = (p.K + BK - 1) / BK;
+  const uint32_t tcols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < 2 * STAGES + 1; ++s)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bars + s)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
+    progress[0] = 0;
+    progress[1] = 0;
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    const uint32_t bytes = (uint32_t)(BM + BN) * BK * 4;
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (kb >= STAGES && !mbar_wait(su32(bars + STAGES + s), ph ^ 1u, p.err)) break;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bars + s)), "r"(bytes)
+                   : "memory");
+      tma_load_2d(sA + s * BM * BK, &tmA, kb * BK, m0, su32(bars + s));
+      tma_load_2d(sB + s * BN * BK, &tmB, kb * BK, n0, su32(bars + s));
+    }
+    progress[0] = kb;
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    const uint32_t idesc = idesc_tf32(BM, BN);
+    int kb = 0;
+    for (; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
+      if (!mbar_wait(su32(bars + s), ph, p.err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t da = sw128_desc(su32(sA + s * BM * BK));
+      const uint64_t db = sw128_desc(su32(sB + s * BN * BK));
+#pragma unroll
+      for (int kk = 0; kk < BK / 8; ++kk)  // 8 tf32 = 32 bytes per instruction
+        mma_tf32(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
+      mma_commit(su32(bars + STAGES + s));
+    }
+    progress[1] = kb;
+    mma_commit(su32(bars + 2 * STAGES));  // arrives once every MMA issued above has completed
+  }
+  __syncwarp();
+
+  // epilogue: TMEM lanes 32w..32w+31 hold rows m0 + 32w + lane
+  bool ok = mbar_wait(su32(bars + 2 * STAGES), 0, p.err);
+  ok = __all_sync(0xffffffffu, ok) && (*(volatile int *)p.err == 0);
+  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok) {
+    const int row = m0 + warp * 32 + lane;
+    float *crow = p.C + (long long)row * p.ldc;
+    for (int c0 = 0; c0 < BN; c0 += 16) {
+      uint32_t r[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
+      if (row < p.M) {
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+          const int n = n0 + c0 + j;
+          if (n < p.N) {
+            const float re = __uint_as_float(r[j]), im = __uint_as_float(r[j + 1]);
+            float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
+            if (p.accumulate) {
+              vr += crow[n];
+              vi += crow[n + 1];
+            }
+            crow[n] = vr;
+            crow[n + 1] = vi;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x == 0 && progress[1] < progress[0]) {
+    // error path: drain TMA copies issued but never consumed (bounded)
+    for (int kb = progress[1]; kb < progress[0]; ++kb)
+      mbar_wait(su32(bars + kb % STAGES), (uint32_t)(kb / STAGES) & 1u, p.err);
+  }
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
+}
+
+// ---------------- operand preparation ----------------
+__device__ __forceinline__ float tf32_hi(float x) {
+  uint32_t u = __float_as_uint(x);
+  u = (u + 0x1000u) & 0xFFFFE000u;  // round the 13 dropped mantissa bits to nearest
+  return __uint_as_float(u);
+}
+
+__global__ void prep_a_kernel(const float2 *A, int64_t sam, int64_t sak, int64_t M, int64_t K,
+                              int64_t Kp, int seg, float *dst, int64_t ldd) {
+  const int64_t total = M * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t m, k;
+    if (sak == 1 || sam != 1) { k = e % Kp; m = e / Kp; } else { m = e % M; k = e / M; }
+    float2 v = make_float2(0.f, 0.f);
+    if (k < K) v = A[m * sam + k * sak];
+    float *row = dst + m * ldd;
+    if (seg == 1) {
+      row[2 * k] = v.x;
+      row[2 * k + 1] = v.y;
+    } else {
+      const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
+      row[2 * k] = hr;                 // [hi | hi | lo]
+      row[2 * k + 1] = hi;
+      row[2 * Kp + 2 * k] = hr;
+      row[2 * Kp + 2 * k + 1] = hi;
+      row[4 * Kp + 2 * k] = v.x - hr;
+      row[4 * Kp + 2 * k + 1] = v.y - hi;
+    }
+  }
+}
+
+__global__ void prep_b_kernel(const float2 *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
+                              int64_t Kp, int seg, float *dst, int64_t ldd) {
+  const int64_t total = N * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t n, k;
+    if (sbk == 1 || sbn != 1) { k = e % Kp; n = e / Kp; } else { n = e % N; k = e / N; }
+    float2 v = make_float2(0.f, 0.f);
+    if (k < K) v = B[k * sbk + n * sbn];
+    float *r0 = dst + (2 * n) * ldd, *r1 = dst + (2 * n + 1) * ldd;
+    if (seg == 1) {
+      r0[2 * k] = v.x;
+      r0[2 * k + 1] = -v.y;
+      r1[2 * k] = v.y;
+      r1[2 * k + 1] = v.x;
+    } else {
+      const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
+      const float lr = v.x - hr, li = v.y - hi;
+      // [hi | lo | hi]
+      r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
+      r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
+      r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
+    }
+  }
+}
+
+int *g_err = nullptr;
+std::once_flag g_once;
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+void init_once() {
+  // the driver entry point is fetched through the runtime, so the library does not link
+  // against libcuda itself (it still loads on machines without a driver)
+  cudaDriverEntryPointQueryResult q;
+  void *fn = nullptr;
+  CCLR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !fn) throw Error(4, "cuTensorMapEncodeTiled not available");
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  CCLR_CUDA(cudaMalloc(&g_err, sizeof(int)));
+  CCLR_CUDA(cudaMemset(g_err, 0, sizeof(int)));
+  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+}
+
+CUtensorMap make_map(const float *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+  CUtensorMap m;
+  cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, gdim, gstride,
+                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) throw Error(4, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+int pick_bn(int64_t N) {
+  if (N <= 256) return (int)((N + 15) / 16 * 16);
+  int best = 256;
+  int64_t best_waste = -1;
+  for (int bn = 256; bn >= 128; bn -= 16) {
+    int64_t tiles = (N + bn - 1) / bn;
+    int64_t waste = tiles * bn - N;
+    if (best_waste < 0 || waste < best_waste) {
+      best = bn;
+      best_waste = waste;
+    }
+  }
+  return best;
+}
+
+unsigned grid1d(int64_t n) {
+  return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+}
+
+}  // namespace
+
+void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, float *dst,
+               int64_t ldd, cudaStream_t st) {
+  const int64_t Kp = tc_kpad(K);
+  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_a: row too short");
+  prep_a_kernel<<<grid1d(M * Kp), 256, 0, st>>>((const float2 *)A, sam, sak, M, K, Kp, seg, dst, ldd);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, float *dst,
+               int64_t ldd, cudaStream_t st) {
+  const int64_t Kp = tc_kpad(K);
+  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_b: row too short");
+  prep_b_kernel<<<grid1d(N * Kp), 256, 0, st>>>((const float2 *)B, sbk, sbn, K, N, Kp, seg, dst, ldd);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+             int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
+  std::call_once(g_once, init_once);
+  if (M <= 0 || Nreal <= 0) return;
+  CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
+  CCLR_REQUIRE(lda % 4 == 0 && ldb % 4 == 0, "tc_gemm: leading dimensions must be multiples of 16 bytes");
+  CCLR_REQUIRE(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, "tc_gemm: operands must be 16-byte aligned");
+  CCLR_REQUIRE(M < (1ll << 31) && Nreal < (1ll << 31) && Kreal < (1ll << 31), "tc_gemm: dimension too large");
+  const int BN = pick_bn(Nreal);
+  const CUtensorMap ma = make_map(A, M, Kreal, lda, BM);
+  const CUtensorMap mb = make_map(B, Nreal, Kreal, ldb, BN);
+  TcParams p;
+  p.M = (int)M;
+  p.N = (int)Nreal;
+  p.K = (int)Kreal;
+  p.BN = BN;
+  p.C = C;
+  p.ldc = ldc_floats;
+  p.ar = (float)alpha.re;
+  p.ai = (float)alpha.im;
+  p.accumulate = accumulate ? 1 : 0;
+  p.err = g_err;
+  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (2 * STAGES + 1) * 8 + 16;
+  const int64_t gy = (Nreal + BN - 1) / BN;
+  CCLR_REQUIRE(gy <= 65535, "tc_gemm: too many N tiles");
+  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)gy);
+  tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, p);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                 int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
+                 cudaStream_t st) {
+  if (seg == 1) {
+    tc_gemm(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, accumulate, st);
+    return;
+  }
+  tc_gemm(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, ldc_floats, alpha, accumulate, st);
+  tc_gemm(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, true, st);
+}
+
+int tc_error(cudaStream_t st) {
+  if (!g_err) return 0;
+  int h = 0;
+  CCLR_CUDA(cudaMemcpyAsync(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CCLR_CUDA(cudaStreamSynchronize(st));
+  if (h) CCLR_CUDA(cudaMemsetAsync(g_err, 0, sizeof(int), st));
+  return h;
+}
+
+}  // namespace cclr

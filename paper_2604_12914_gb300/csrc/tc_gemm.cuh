@@ -1,0 +1,43 @@
+// tcgen05 tensor-core GEMM (TF32 inputs, FP32 accumulation in TMEM) and the operand
+// preparation that maps complex products onto it.
+//
+// Real kernel:   D[m][n] = sum_k A[m][k] * B[n][k]     (A, B row-major, K contiguous)
+// Complex use:   C[M][N] = A[M][K] . B[K][N] (complex64) becomes one real GEMM with
+//   A_real = A as interleaved (re, im) pairs, [M][2K]            (no transformation)
+//   B_real rows 2n, 2n+1 = (Re b_kn, -Im b_kn), (Im b_kn, Re b_kn) over k, [2N][2K]
+// so that D[m][2n] = Re C[m][n] and D[m][2n+1] = Im C[m][n]: the FP32 output is already
+// the interleaved complex result (4 real multiplies per complex multiply-add).
+// 3xTF32 (split) mode: x = hi + lo with hi rounded to TF32; A_real = [hi | hi | lo],
+// B_real = [hi | lo | hi] along K gives hi.hi + hi.lo + lo.hi (about FP32 accuracy).
+#pragma once
+#include "kernels.cuh"
+
+namespace cclr {
+
+// Complex K padded so that every operand row is a whole number of 16-byte units.
+inline int64_t tc_kpad(int64_t K) { return (K + 1) / 2 * 2; }
+
+// seg = 1 (TF32) or 3 (3xTF32 split).  dst rows have ldd floats (>= 2*tc_kpad(K)*seg).
+void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, float *dst,
+               int64_t ldd, cudaStream_t st);
+void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, float *dst,
+               int64_t ldd, cudaStream_t st);
+
+// Real tensor-core GEMM; C is written as complex pairs: C[m][n..n+1] (+)= alpha * D[m][n..n+1]
+// for even n.  Nreal must be even; lda/ldb multiples of 4 floats; A, B 16-byte aligned.
+void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+             int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st);
+
+// Complex GEMM on prepared operands with seg segments of Kseg floats each (Kseg = 2*Kp).
+// seg = 1: one pass.  seg = 3: the correction terms hi.lo + lo.hi (segments 1-2) and the
+// main term hi.hi (segment 0) run as two passes with separate TMEM accumulators, summed
+// into C in FP32 by the epilogues.
+void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                 int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
+                 cudaStream_t st);
+
+// Reads (and clears) the device-side error flag of the tensor-core kernels: 0 = fine,
+// 1 = a bounded wait gave up.
+int tc_error(cudaStream_t st);
+
+}  // namespace cclr
