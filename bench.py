@@ -37,10 +37,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cclr", choices=["cclr", "reference"])
-    ap.add_argument("--prec", default=os.environ.get("CCLR_BENCH_PREC", "fp32"))
+    ap.add_argument("--prec", default=os.environ.get("CCLR_BENCH_PREC", "tf32"))
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--no-alpha", action="store_true")
+    ap.add_argument("--alpha-config", default="C1")
+    ap.add_argument("--alpha-scale", type=float, default=0.2)
     return ap.parse_args()
 
 
@@ -202,6 +205,32 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428), tol=1e-8):
+    """Wall time of cc_lr_solve (Lambda + X(+-w) solves + alpha), FP64 path vs mixed path,
+    on the same synthetic system; returns both times and max |delta alpha| (a.u.)."""
+    import numpy as np
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import make_config
+    s = make_config(cfg, scale=scale)
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
+           "components": list(comps), "omegas": list(omegas), "tol": tol}
+    res = {}
+    for tag, prec in (("fp64", "fp64"), ("mixed", prec_mixed)):
+        ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec)
+        t0 = time.perf_counter()
+        al, st = ctx.cc_lr_solve(list(omegas), comps, tol=tol, allow_noconv=True)
+        el = time.perf_counter() - t0
+        ctx.close()
+        res[tag] = al
+        out[tag] = {"seconds": el, "precision_mode": prec, "iterations": st["iterations"],
+                    "sigma_calls": st["sigma_calls"], "fp64_refinements": st["refinements"],
+                    "converged": st["converged"], "max_rel_residual": st["max_rel_residual"]}
+    out["max_abs_delta_alpha_au"] = float(np.abs(res["fp64"] - res["mixed"]).max())
+    out["alpha_zz_fp64"] = [float(res["fp64"][w, -1, -1].real) for w in range(len(omegas))]
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["seconds"] / out["mixed"]["seconds"]
+    return out
+
+
 def run_cclr(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -282,6 +311,9 @@ def run_cclr(args):
     bound, peak, how = ladder_peak(args.prec)
     achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
     ctx.close()
+    tta = None
+    if rank == 0 and not args.no_alpha:
+        tta = time_to_alpha(args.alpha_config, args.alpha_scale, "tf32" if args.prec in ("tf32", "fp64") else args.prec)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,
@@ -301,6 +333,8 @@ def run_cclr(args):
                     "d2h_bytes_per_step": bytes_io},
             "gpu_launches": int(launches),
         }
+        if tta is not None:
+            out["time_to_alpha"] = tta
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)

@@ -15,6 +15,11 @@ extern "C" {
  * cclr_status code. */
 int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *err);
 
+/* Times the tensor-core complex GEMM C[M][N] = A[M][K] B[K][N] (operand preparation
+ * excluded) on seeded data: reps launches, CUDA events; ms[0] = mean milliseconds per
+ * GEMM, ms[1] = the corresponding TFLOP/s at 8 real flops per complex multiply-add. */
+int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -69,6 +69,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_last_error": [],
         "cc_lr_launch_count": [],
         "cc_lr_selftest_gemm": [I, I, I, I, ctypes.c_uint, P],
+        "cc_lr_bench_gemm": [I, I, I, I, I, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -226,6 +227,13 @@ def cc_lr_selftest_gemm(M, N, K, mode, seed=1):
     err = np.zeros(2, dtype=np.float64)
     _check(load().cc_lr_selftest_gemm(M, N, K, mode, seed, _ptr(err)))
     return float(err[0]), float(err[1])
+
+
+def cc_lr_bench_gemm(M, N, K, mode, reps=5):
+    """(ms per GEMM, TFLOP/s) of the tensor-core complex GEMM path alone."""
+    out = np.zeros(2, dtype=np.float64)
+    _check(load().cc_lr_bench_gemm(M, N, K, mode, reps, _ptr(out)))
+    return float(out[0]), float(out[1])
 
 
 def cc_lr_launch_count() -> int:

@@ -9,6 +9,8 @@
 #include "../../include/cclr.h"
 #include "../../include/cclr_testing.h"
 
+#include <cstdio>
+#include <cstdlib>
 #include <random>
 #include "model.cuh"
 #include "tc_gemm.cuh"
@@ -47,6 +49,11 @@ struct cclr_ctx {
   int sigma_calls = 0;
 
   int64_t ntot() const { return n1 + n2; }
+  // CCLR_VERBOSE=1 prints solver residual histories to stderr (diagnostics)
+  static bool verbose() {
+    static const bool v = std::getenv("CCLR_VERBOSE") && std::getenv("CCLR_VERBOSE")[0] == '1';
+    return v;
+  }
 
   void alloc_vec(AVec &v_) { if (!v_.b.p) v_.b.alloc((size_t)ntot() * 16); }
 
@@ -87,10 +94,55 @@ struct cclr_ctx {
     M->E.permute(zc(1), si, "a", so, "a", false);
   }
 
-  // Solve (Op - omega) x = b with the diagonal preconditioner (D - omega) and DIIS.
-  // Returns relative residual; iterations added to *its.
+  // Solve (Op - omega) x = b.  FP64 mode: preconditioned DIIS.  Mixed modes: iterative
+  // refinement -- the residual r = b - (Op - omega) x is formed with the FP64 sigma and
+  // normed and applied in FP64; each correction (Op - omega) d = r is solved by DIIS with
+  // the tensor-core sigma (TF32: two digits per correction, 3xTF32: five).
+  int refinements = 0;
   double solve(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
                int *its) {
+    if (M->prec == CCLR_FP64) return solve_diis(dir, omega, b, x, tol, depth, maxit, its);
+    const int lo = M->prec;
+    const double inner_tol = lo == CCLR_C64_TF32 ? 1e-2 : 1e-5;
+    AVec s, r, d;
+    alloc_vec(s);
+    alloc_vec(r);
+    alloc_vec(d);
+    const double bn = std::max(norm(b), 1e-300);
+    CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
+    copy(b, r.b.p);
+    double rel = 1.0;
+    int used = 0;
+    // each correction gets a bounded number of DIIS steps: near its precision floor the
+    // low-precision DIIS stalls, and one more FP64 residual is cheaper than stalling
+    const int inner_cap = lo == CCLR_C64_TF32 ? 30 : 40;
+    for (int outer = 0; outer < 40 && used < maxit; ++outer) {
+      if (outer > 0) {
+        M->prec = CCLR_FP64;
+        op(dir, x, s.b.p);
+        M->prec = lo;
+        ++refinements;
+        copy(b, r.b.p);
+        axpy(zd(-1), s.b.p, r.b.p);
+        axpy(zd(omega), x, r.b.p);
+      }
+      rel = norm(r.b.p) / bn;
+      if (verbose()) std::fprintf(stderr, "cclr refine dir=%d omega=%g outer=%d rel=%.3e\n", dir, omega, outer, rel);
+      if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
+      if (rel < tol) break;
+      int inner = 0;
+      solve_diis(dir, omega, r.b.p, d.b.p, std::max(inner_tol, 0.3 * tol / rel), depth,
+                 std::min(inner_cap, maxit - used), &inner);
+      used += inner;
+      if (its) *its += inner;
+      axpy(zd(1), d.b.p, x);
+    }
+    return rel;
+  }
+
+  // Preconditioned DIIS on (Op - omega) x = b in the current precision.
+  double solve_diis(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+                    int *its) {
     depth = std::max(2, std::min(depth, 16));
     std::vector<AVec> X(depth), Er(depth);
     for (auto &a : X) alloc_vec(a);
@@ -110,6 +162,7 @@ struct cclr_ctx {
       axpy(zd(omega), x, r.b.p);
       rel = norm(r.b.p) / bn;
       if (its) ++*its;
+      if (verbose()) std::fprintf(stderr, "cclr diis dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega, it, rel, M->prec);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
       if (rel < tol) break;
       int k = head;
@@ -187,12 +240,12 @@ struct cclr_ctx {
 
   // eta0 = dE/dT = [ sum_jb <ij||ab> t_jb ; <ij||ab> ] (canonical Fock: f_ia = 0)
   void eta0(void *out) {
-    const CstSet &C = M->c128;
+    const Tens &oovv = M->oovv128();
     Tens e1 = make_tens(out, C128, {o, v});
     Tens e2 = make_tens((char *)out + n1 * 16, C128, {o, o, v, v});
     M->E.zero(e1);
-    M->E.contract(zc(1), C.t[K_OOVV], "ijab", make_tens(M->t1.p, C128, {o, v}), "jb", e1, "ia");
-    M->E.permute(zc(1), C.t[K_OOVV], "ijab", e2, "ijab", false);
+    M->E.contract(zc(1), oovv, "ijab", make_tens(M->t1.p, C128, {o, v}), "jb", e1, "ia");
+    M->E.permute(zc(1), oovv, "ijab", e2, "ijab", false);
     // f_ia of diag(eps) is zero; the one-body h keeps any ov part of the input Fock
   }
 
@@ -278,13 +331,16 @@ struct cclr_ctx {
     CCLR_CUDA(cudaMemsetAsync(out, 0, (size_t)ntot() * 16, st));
     for (int s = 0; s < 4; ++s) {
       shifted(x, ks[s] * h, ts);
-      M->build_set(ts.p1(), ts.p2(n1), shift);
+      M->build_set(ts.p1(), ts.p2(n1), shift, C128);
+      const int saved = M->prec;
+      M->prec = CCLR_FP64;
       op(-1, lam.b.p, sv.b.p, &shift);
+      M->prec = saved;
       axpy(zd(cs[s] / (12.0 * h)), sv.b.p, out);
     }
     // d eta0 / dT along X: sum_jb <ij||ab> X_jb (singles only)
     Tens o1 = make_tens(out, C128, {o, v});
-    M->E.contract(zc(1), M->c128.t[K_OOVV], "ijab", make_tens((void *)x, C128, {o, v}), "jb", o1, "ia");
+    M->E.contract(zc(1), M->oovv128(), "ijab", make_tens((void *)x, C128, {o, v}), "jb", o1, "ia");
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
 };
@@ -336,9 +392,8 @@ cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps
     c->M.reset(new Model(o, v, naux, c->st));
     c->M->prec = prec;
     c->M->upload_inputs(eps, L, mu, t1, t2, device_ptrs);
-    c->M->build_set(c->M->t1.p, c->M->t2.p, c->M->c128);
+    c->M->cst_for(prec);      // intermediates in the working precision
     c->M->build_diagonal();
-    if (prec != CCLR_FP64) c->M->cst_for(prec);
     if (lam1) {
       c->alloc_vec(c->lam);
       to_dev(c, lam1, c->lam.p1(), (size_t)c->n1 * 16);
@@ -414,6 +469,7 @@ cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int d
     if (stats) {
       std::memset(stats, 0, sizeof(*stats));
       stats->iterations = its;
+      stats->refinements = c->refinements;
       stats->sigma_calls = c->sigma_calls - calls0;
       stats->converged = rel < tol;
       stats->max_rel_residual = rel;
@@ -496,6 +552,7 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
       loc.time_alpha_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
     }
     loc.sigma_calls = c->sigma_calls - calls0;
+    loc.refinements = c->refinements;
   });
   if (stats) *stats = loc;
   if (st != CCLR_OK) return (cclr_status)st;
@@ -550,6 +607,40 @@ const char *cc_lr_strerror(cclr_status s) {
 const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
 
 unsigned long long cc_lr_launch_count(void) { return cclr::launch_count(); }
+
+int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
+  if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || reps < 1 || !ms) return fail(CCLR_EINVAL, "bad bench_gemm arguments");
+  return guarded([&] {
+    cudaStream_t st;
+    CCLR_CUDA(cudaStreamCreate(&st));
+    const int seg = mode == 2 ? 3 : 1;
+    const int64_t ld = 2 * tc_kpad(K) * seg;
+    DevBuf A((size_t)M * ld * 4), B((size_t)2 * N * ld * 4), C((size_t)M * N * 8);
+    // deterministic small values (exact content is irrelevant for timing)
+    CCLR_CUDA(cudaMemsetAsync(A.p, 0, A.bytes, st));
+    CCLR_CUDA(cudaMemsetAsync(B.p, 0, B.bytes, st));
+    CCLR_CUDA(cudaMemsetAsync(C.p, 0, C.bytes, st));
+    cudaEvent_t e0, e1;
+    CCLR_CUDA(cudaEventCreate(&e0));
+    CCLR_CUDA(cudaEventCreate(&e1));
+    tc_gemm_seg(A.as<float>(), ld, B.as<float>(), ld, M, 2 * N, 2 * tc_kpad(K), seg, C.as<float>(), 2 * N,
+                zc(1), false, st);
+    CCLR_CUDA(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r)
+      tc_gemm_seg(A.as<float>(), ld, B.as<float>(), ld, M, 2 * N, 2 * tc_kpad(K), seg, C.as<float>(), 2 * N,
+                  zc(1), false, st);
+    CCLR_CUDA(cudaEventRecord(e1, st));
+    CCLR_CUDA(cudaEventSynchronize(e1));
+    float t = 0;
+    CCLR_CUDA(cudaEventElapsedTime(&t, e0, e1));
+    ms[0] = t / reps;
+    ms[1] = 8.0 * M * (double)N * K / (ms[0] * 1e-3) / 1e12;
+    if (tc_error(st)) throw Error(CCLR_ETIMEOUT, "tensor-core kernel gave up on a bounded wait");
+    CCLR_CUDA(cudaEventDestroy(e0));
+    CCLR_CUDA(cudaEventDestroy(e1));
+    CCLR_CUDA(cudaStreamDestroy(st));
+  });
+}
 
 int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *err) {
   if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || !err) return fail(CCLR_EINVAL, "bad selftest arguments");

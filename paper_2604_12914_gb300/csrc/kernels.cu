@@ -5,6 +5,7 @@
 #include "kernels.cuh"
 
 #include <atomic>
+#include <type_traits>
 
 namespace cclr {
 
@@ -132,6 +133,29 @@ void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st) {
   }
 }
 
+// out = alpha * v (+ out): arithmetic in double only when either side is complex128 (the
+// FP64 pipe of this GPU is far slower than its memory, even for a streaming copy).
+template <typename TI, typename TO>
+__device__ __forceinline__ typename cpx<TO>::t scale_acc(typename cpx<TI>::t v, double ar, double ai,
+                                                         int acc, const typename cpx<TO>::t *dst) {
+  using CT = typename std::conditional<sizeof(TI) == 8 || sizeof(TO) == 8, double, float>::type;
+  const CT vr = (CT)v.x, vi = (CT)v.y;
+  CT wr, wi;
+  if (ar == 1.0 && ai == 0.0) { wr = vr; wi = vi; }
+  else if (ai == 0.0) { wr = (CT)ar * vr; wi = (CT)ar * vi; }
+  else { wr = (CT)ar * vr - (CT)ai * vi; wi = (CT)ar * vi + (CT)ai * vr; }
+  typename cpx<TO>::t res;
+  if (acc) {
+    const typename cpx<TO>::t o = *dst;
+    res.x = (TO)(wr + (CT)o.x);
+    res.y = (TO)(wi + (CT)o.y);
+  } else {
+    res.x = (TO)wr;
+    res.y = (TO)wi;
+  }
+  return res;
+}
+
 // --------------------------------------------------------------------------------------
 // Permute / accumulate: out[idx] = alpha * in[perm idx] (+ out[idx]).  Iterates in the
 // order of the output's own mode list (rank <= 8); strides in elements.
@@ -153,33 +177,193 @@ __global__ void permute_kernel(PermArgs a) {
       oi += c * a.sin[d];
       oo += c * a.sout[d];
     }
-    CI v = in[oi];
-    double vr = (double)v.x, vi = (double)v.y;
-    double wr = a.alr * vr - a.ali * vi;
-    double wi = a.alr * vi + a.ali * vr;
-    CO res;
-    if (a.acc) {
-      CO o = out[oo];
-      res.x = (TO)(wr + (double)o.x);
-      res.y = (TO)(wi + (double)o.y);
-    } else {
-      res.x = (TO)wr;
-      res.y = (TO)wi;
+    out[oo] = scale_acc<TI, TO>(in[oi], a.alr, a.ali, a.acc, out + oo);
+  }
+}
+
+// Contiguous-enough case: 32-bit index math over at most 4 merged modes.
+template <typename TI, typename TO>
+__global__ void permute_kernel32(PermArgs a) {
+  using CI = typename cpx<TI>::t;
+  using CO = typename cpx<TO>::t;
+  const CI *in = (const CI *)a.in;
+  CO *out = (CO *)a.out;
+  const int rank = a.rank;
+  const int d0 = (int)a.dim[0], d1 = (int)a.dim[1], d2 = (int)a.dim[2], d3 = (int)a.dim[3];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    unsigned r = (unsigned)e;
+    int64_t oi = 0, oo = 0;
+    if (rank > 3) { unsigned c = r % d3; r /= d3; oi += c * a.sin[3]; oo += c * a.sout[3]; }
+    if (rank > 2) { unsigned c = r % d2; r /= d2; oi += c * a.sin[2]; oo += c * a.sout[2]; }
+    if (rank > 1) { unsigned c = r % d1; r /= d1; oi += c * a.sin[1]; oo += c * a.sout[1]; }
+    oi += (int64_t)r * a.sin[0];
+    oo += (int64_t)r * a.sout[0];
+    (void)d0;
+    out[oo] = scale_acc<TI, TO>(in[oi], a.alr, a.ali, a.acc, out + oo);
+  }
+}
+
+// Transpose-like case: the input's unit-stride mode (din) is not the output's innermost
+// mode (dout).  32 x 32 tiles through shared memory, remaining modes as a batch.
+struct TileArgs {
+  int64_t Din, Dout;        // extents of the two tiled modes
+  int64_t sin_din, sin_dout, sout_din, sout_dout;
+  int nb_rank;
+  int64_t bdim[6], bsin[6], bsout[6];
+  int64_t nbatch;
+};
+
+template <typename TI, typename TO>
+__global__ void permute_tiled(PermArgs a, TileArgs t) {
+  using CI = typename cpx<TI>::t;
+  using CO = typename cpx<TO>::t;
+  __shared__ CI tile[32][33];
+  const CI *in = (const CI *)a.in;
+  CO *out = (CO *)a.out;
+  const unsigned tin = (unsigned)((t.Din + 31) / 32), tout = (unsigned)((t.Dout + 31) / 32);
+  const unsigned per = tin * tout;
+  for (unsigned bt = blockIdx.x; bt < (unsigned)t.nbatch * per; bt += gridDim.x) {
+    unsigned b = bt / per;
+    const unsigned tt = bt - b * per;
+    const int64_t i0 = (int64_t)(tt % tin) * 32, o0 = (int64_t)(tt / tin) * 32;
+    int64_t bi = 0, bo = 0;
+    for (int d = t.nb_rank - 1; d >= 0; --d) {
+      const unsigned bd = (unsigned)t.bdim[d];
+      const unsigned c = b % bd;
+      b /= bd;
+      bi += (int64_t)c * t.bsin[d];
+      bo += (int64_t)c * t.bsout[d];
     }
-    out[oo] = res;
+    // load: threadIdx.x along din (unit stride in the input)
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t iin = i0 + threadIdx.x, iout = o0 + r;
+      if (iin < t.Din && iout < t.Dout) tile[r][threadIdx.x] = in[bi + iin * t.sin_din + iout * t.sin_dout];
+    }
+    __syncthreads();
+    // store: threadIdx.x along dout (unit stride in the output)
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t iout = o0 + threadIdx.x, iin = i0 + r;
+      if (iin < t.Din && iout < t.Dout) {
+        CO *dst = out + bo + iin * t.sout_din + iout * t.sout_dout;
+        *dst = scale_acc<TI, TO>(tile[threadIdx.x][r], a.alr, a.ali, a.acc, dst);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename TI, typename TO>
+static void permute_dispatch(PermArgs a, cudaStream_t st) {
+  // merge output-adjacent modes that are also adjacent (same order) in the input
+  PermArgs m = a;
+  int r = 0;
+  for (int d = 0; d < a.rank; ++d) {
+    if (r > 0 && m.sout[r - 1] == a.sout[d] * a.dim[d] && m.sin[r - 1] == a.sin[d] * a.dim[d]) {
+      m.dim[r - 1] *= a.dim[d];
+      m.sout[r - 1] = a.sout[d];
+      m.sin[r - 1] = a.sin[d];
+    } else {
+      m.dim[r] = a.dim[d];
+      m.sout[r] = a.sout[d];
+      m.sin[r] = a.sin[d];
+      ++r;
+    }
+  }
+  m.rank = r;
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((m.total + threads - 1) / threads, 152 * 32);
+  // unit-stride input mode that is not the output's innermost one -> tiled transpose
+  int din = -1;
+  for (int d = 0; d < m.rank; ++d)
+    if (m.sin[d] == 1 && m.dim[d] > 1) din = d;
+  const int dout = m.rank - 1;
+  if (din >= 0 && din != dout && m.sout[dout] == 1 && m.dim[dout] >= 8 && m.dim[din] >= 8 && m.rank <= 8 &&
+      m.total < (1ll << 40)) {
+    TileArgs t;
+    t.Din = m.dim[din]; t.Dout = m.dim[dout];
+    t.sin_din = m.sin[din]; t.sin_dout = m.sin[dout];
+    t.sout_din = m.sout[din]; t.sout_dout = m.sout[dout];
+    t.nb_rank = 0;
+    t.nbatch = 1;
+    for (int d = 0; d < m.rank; ++d) {
+      if (d == din || d == dout) continue;
+      t.bdim[t.nb_rank] = m.dim[d];
+      t.bsin[t.nb_rank] = m.sin[d];
+      t.bsout[t.nb_rank] = m.sout[d];
+      t.nbatch *= m.dim[d];
+      ++t.nb_rank;
+    }
+    const int64_t ntile = t.nbatch * ((t.Din + 31) / 32) * ((t.Dout + 31) / 32);
+    CCLR_REQUIRE(ntile < (1ll << 32), "permute: too many tiles");
+    permute_tiled<TI, TO><<<(unsigned)std::min<int64_t>(ntile, 152 * 64), dim3(32, 8), 0, st>>>(m, t);
+  } else if (m.rank <= 4 && m.total < (1ll << 31)) {
+    permute_kernel32<TI, TO><<<(unsigned)blocks, threads, 0, st>>>(m);
+  } else {
+    permute_kernel<TI, TO><<<(unsigned)blocks, threads, 0, st>>>(m);
   }
 }
 
 void launch_permute(const PermArgs &a, int dt_in, int dt_out, cudaStream_t st) {
   if (a.total <= 0) return;
-  int threads = 256;
-  int64_t blocks = std::min<int64_t>((a.total + threads - 1) / threads, 152 * 32);
-  if (dt_in == C128 && dt_out == C128) permute_kernel<double, double><<<(unsigned)blocks, threads, 0, st>>>(a);
-  else if (dt_in == C64 && dt_out == C64) permute_kernel<float, float><<<(unsigned)blocks, threads, 0, st>>>(a);
-  else if (dt_in == C128 && dt_out == C64) permute_kernel<double, float><<<(unsigned)blocks, threads, 0, st>>>(a);
-  else permute_kernel<float, double><<<(unsigned)blocks, threads, 0, st>>>(a);
+  if (dt_in == C128 && dt_out == C128) permute_dispatch<double, double>(a, st);
+  else if (dt_in == C64 && dt_out == C64) permute_dispatch<float, float>(a, st);
+  else if (dt_in == C128 && dt_out == C64) permute_dispatch<double, float>(a, st);
+  else permute_dispatch<float, double>(a, st);
   count_launch();
-    CCLR_CUDA(cudaGetLastError());
+  CCLR_CUDA(cudaGetLastError());
+}
+
+// --------------------------------------------------------------------------------------
+// Antisymmetriser, one pass (o, o, v, v tensors):
+//   S[ijab] += Rab[ijab] - Rab[ijba] + Rij[ijab] - Rij[jiab]
+//            + R4[ijab] - R4[jiab] - R4[ijba] + R4[jiba]
+// and its transpose (dir -1):  Rab += S - S(ab), Rij += S - S(ij), R4 += (1-P(ij))(1-P(ab)) S.
+// --------------------------------------------------------------------------------------
+template <typename T>
+__global__ void antisym_kernel(int o, int v, int dir, const typename cpx<T>::t *Rab_c,
+                               const typename cpx<T>::t *Rij_c, const typename cpx<T>::t *R4_c,
+                               typename cpx<T>::t *S, typename cpx<T>::t *Rab, typename cpx<T>::t *Rij,
+                               typename cpx<T>::t *R4) {
+  using C = typename cpx<T>::t;
+  const int64_t vv = (int64_t)v * v, n = (int64_t)o * o * vv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = e % vv, ij = e / vv;
+    const int a = (int)(ab / v), b = (int)(ab % v), i = (int)(ij / o), j = (int)(ij % o);
+    const int64_t e_ba = ij * vv + (int64_t)b * v + a;
+    const int64_t e_ji = ((int64_t)j * o + i) * vv + ab;
+    const int64_t e_jiba = ((int64_t)j * o + i) * vv + (int64_t)b * v + a;
+    if (dir > 0) {
+      C r1 = Rab_c[e], r2 = Rab_c[e_ba], r3 = Rij_c[e], r4 = Rij_c[e_ji];
+      C q1 = R4_c[e], q2 = R4_c[e_ji], q3 = R4_c[e_ba], q4 = R4_c[e_jiba];
+      C s = S[e];
+      s.x += r1.x - r2.x + r3.x - r4.x + q1.x - q2.x - q3.x + q4.x;
+      s.y += r1.y - r2.y + r3.y - r4.y + q1.y - q2.y - q3.y + q4.y;
+      S[e] = s;
+    } else {
+      const C s1 = S[e], s2 = S[e_ba], s3 = S[e_ji], s4 = S[e_jiba];
+      C t;
+      t = Rab[e]; t.x += s1.x - s2.x; t.y += s1.y - s2.y; Rab[e] = t;
+      t = Rij[e]; t.x += s1.x - s3.x; t.y += s1.y - s3.y; Rij[e] = t;
+      t = R4[e]; t.x += s1.x - s3.x - s2.x + s4.x; t.y += s1.y - s3.y - s2.y + s4.y; R4[e] = t;
+    }
+  }
+}
+
+void antisym_apply(int dt, int o, int v, int dir, void *S, void *Rab, void *Rij, void *R4, cudaStream_t st) {
+  const int64_t n = (int64_t)o * o * v * v;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+  if (dt == C128)
+    antisym_kernel<double><<<g, 256, 0, st>>>(o, v, dir, (const double2 *)Rab, (const double2 *)Rij,
+                                              (const double2 *)R4, (double2 *)S, (double2 *)Rab,
+                                              (double2 *)Rij, (double2 *)R4);
+  else
+    antisym_kernel<float><<<g, 256, 0, st>>>(o, v, dir, (const float2 *)Rab, (const float2 *)Rij,
+                                             (const float2 *)R4, (float2 *)S, (float2 *)Rab, (float2 *)Rij,
+                                             (float2 *)R4);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
 }
 
 // --------------------------------------------------------------------------------------

@@ -86,25 +86,60 @@ void Model::upload_inputs(const double *eps_h, const double *L, const double *mu
   CCLR_CUDA(cudaStreamSynchronize(st));
 }
 
-void Model::build_set(const void *t1d, const void *t2d, CstSet &out) {
-  out.dt = C128;
+// Complex64 copies of the undressed inputs (made once, for complex64 rebuilds).
+void Model::ensure_src64() {
+  if (Loo64.p) return;
+  auto conv = [&](const DevBuf &src, DevBuf &dst, int64_t ne) {
+    dst.alloc((size_t)ne * 8);
+    E.permute(zc(1), make_tens(src.p, C128, {ne}), "a", make_tens(dst.p, C64, {ne}), "a", false);
+  };
+  conv(Loo0, Loo64, (int64_t)naux * o * o);
+  conv(Lov0, Lov64, (int64_t)naux * o * v);
+  conv(Lvo0, Lvo64, (int64_t)naux * v * o);
+  conv(Lvv0, Lvv64, (int64_t)naux * v * v);
+  conv(h, h64, (int64_t)n * n);
+}
+
+void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
+  out.dt = dt;
+  const size_t es = dt_size(dt);
   const int P = naux;
+  // complex64 builds run on the FP32 CUDA cores (FP32-accurate: the stored intermediates
+  // enter every sigma, so their error is systematic)
+  const int tc_saved = E.tc_mode;
+  E.tc_mode = 0;
   auto alloc = [&](int id, std::initializer_list<int64_t> dims) {
     int64_t ne = 1;
     for (auto d : dims) ne *= d;
-    if (out.buf[id].bytes != (size_t)ne * 16) out.buf[id].alloc((size_t)ne * 16);
-    out.t[id] = make_tens(out.buf[id].p, C128, dims);
+    if (out.buf[id].bytes != (size_t)ne * es) out.buf[id].alloc((size_t)ne * es);
+    out.t[id] = make_tens(out.buf[id].p, dt, dims);
     E.zero(out.t[id]);
     return out.t[id];
   };
+  if (dt == C64) ensure_src64();
+  auto src = [&](const DevBuf &b128, const DevBuf &b64, std::initializer_list<int64_t> dims) {
+    return make_tens(dt == C128 ? b128.p : b64.p, dt, dims);
+  };
+  Tens Loo = src(Loo0, Loo64, {P, o, o}), Lov = src(Lov0, Lov64, {P, o, v}),
+       Lvo = src(Lvo0, Lvo64, {P, v, o}), Lvv = src(Lvv0, Lvv64, {P, v, v});
+  Tens Hf = src(h, h64, {n, n});
+  // amplitudes in the build precision
+  DevBuf t1b, t2b;
   Tens t1t = make_tens((void *)t1d, C128, {o, v});
   Tens t2t = make_tens((void *)t2d, C128, {o, o, v, v});
-  Tens Loo = T(Loo0, {P, o, o}), Lov = T(Lov0, {P, o, v}), Lvo = T(Lvo0, {P, v, o}),
-       Lvv = T(Lvv0, {P, v, v});
+  if (dt == C64) {
+    t1b.alloc((size_t)o * v * 8);
+    t2b.alloc((size_t)o * o * v * v * 8);
+    Tens a = make_tens(t1b.p, C64, {o, v}), b = make_tens(t2b.p, C64, {o, o, v, v});
+    E.permute(zc(1), t1t, "ia", a, "ia", false);
+    E.permute(zc(1), t2t, "ijab", b, "ijab", false);
+    t1t = a;
+    t2t = b;
+  }
 
   // ---- T1 dressing of the Cholesky blocks: L~ = (1 - t) L (1 + t)
-  DevBuf Ltoo_b((size_t)P * o * o * 16);
-  Tens Ltoo = T(Ltoo_b, {P, o, o});
+  DevBuf Ltoo_b((size_t)P * o * o * es);
+  Tens Ltoo = make_tens(Ltoo_b.p, dt, {P, o, o});
   E.permute(zc(1), Loo, "Pij", Ltoo, "Pij", false);
   E.contract(zc(1), Lov, "Pib", t1t, "jb", Ltoo, "Pij");
   Tens Ltov = alloc(K_LOV, {P, o, v});
@@ -118,7 +153,6 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out) {
   E.contract(zc(1), Ltvv, "Pab", t1t, "ib", Ltvo, "Pai");
 
   // ---- dressed Fock f~ = (1 - t) h (1 + t) + sum_k <pk||qk>~ (oo, ov, vv blocks)
-  Tens Hf = T(h, {n, n});
   Tens hoo = Hf.slice(0, 0, o).slice(1, 0, o), hov = Hf.slice(0, 0, o).slice(1, o, n),
        hvv = Hf.slice(0, o, n).slice(1, o, n);
   Tens Foo = alloc(K_FOO, {o, o}), Fov = alloc(K_FOV, {o, v}), Fvv = alloc(K_FVV, {v, v});
@@ -128,12 +162,13 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out) {
   E.permute(zc(1), hvv, "ab", Fvv, "ab", false);
   E.contract(zc(-1), t1t, "ma", hov, "mb", Fvv, "ab");
   {
-    DevBuf Ib((size_t)o * o * 16), trb((size_t)P * 16), ones(sizeof(double) * o);
-    Tens I = T(Ib, {o, o}), tr = T(trb, {P});
-    E.zero(I);
+    DevBuf Ib((size_t)o * o * 16), Id((size_t)o * o * es), trb((size_t)P * es), ones(sizeof(double) * o);
+    Tens I128 = T(Ib, {o, o}), I = make_tens(Id.p, dt, {o, o}), tr = make_tens(trb.p, dt, {P});
+    E.zero(I128);
     std::vector<double> one(o, 1.0);
     CCLR_CUDA(cudaMemcpyAsync(ones.p, one.data(), sizeof(double) * o, cudaMemcpyHostToDevice, st));
     set_diag(o, ones.as<double>(), Ib.p, st);
+    E.permute(zc(1), I128, "kl", I, "kl", false);
     E.zero(tr);
     E.contract(zc(1), Ltoo, "Pkl", I, "kl", tr, "P");
     E.contract(zc(1), Ltoo, "Pij", tr, "P", Foo, "ij");
@@ -179,54 +214,80 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out) {
   E.contract(zc(-1), Ltoo, "Pmj", Ltvo, "Pbi", Wovoo, "mbij");
   E.contract(zc(-1), Fov, "me", T2, "ijbe", Wovoo, "mbij");
   {
-    DevBuf tb((size_t)o * v * o * o * 16);
-    Tens tmp = T(tb, {o, v, o, o});
+    DevBuf tb((size_t)o * v * o * o * es);
+    Tens tmp = make_tens(tb.p, dt, {o, v, o, o});
     E.zero(tmp);
     E.contract(zc(1), Wooov, "mnie", T2, "jnbe", tmp, "mbij");
     E.permute(zc(1), tmp, "mbij", Wovoo, "mbij", true);
     E.permute(zc(-1), tmp, "mbij", Wovoo, "mbji", true);
     // 1/2 sum_ef <mb||ef>~ t_ij^ef = sum_ef <mb|ef>~ t_ij^ef, formed in chunks of b
-    int64_t per_b = (int64_t)o * v * v * 16;
+    int64_t per_b = (int64_t)o * v * v * es;
     int64_t bc = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_b));
     DevBuf Gb((size_t)(bc * per_b));
     for (int64_t b0 = 0; b0 < v; b0 += bc) {
       int64_t b1 = std::min<int64_t>(v, b0 + bc);
-      Tens G = make_tens(Gb.p, C128, {o, b1 - b0, v, v});
+      Tens G = make_tens(Gb.p, dt, {o, b1 - b0, v, v});
       E.zero(G);
       E.contract(zc(1), Ltov, "Pme", Ltvv.slice(1, b0, b1), "Pbf", G, "mbef");
       E.contract(zc(1), G, "mbef", T2, "ijef", Wovoo.slice(1, b0, b1), "mbij");
     }
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
+  E.tc_mode = tc_saved;
   out.valid = true;
-}
-
-void Model::make_c64(const CstSet &src, CstSet &dst) {
-  dst.dt = C64;
-  for (int k = 0; k < K_NCST; ++k) {
-    const Tens &s = src.t[k];
-    size_t bytes = (size_t)s.numel() * 8;
-    if (dst.buf[k].bytes != bytes) dst.buf[k].alloc(bytes);
-    Tens d = s;
-    d.p = dst.buf[k].p;
-    d.dt = C64;
-    std::string m = std::string("abcdefgh").substr(0, s.rank);
-    E.permute(zc(1), s, m, d, m, false);
-    dst.t[k] = d;
-  }
-  dst.valid = true;
 }
 
 void Model::build_diagonal() {
   D1.alloc(sizeof(double) * o * v);
   D2.alloc(sizeof(double) * (size_t)o * o * v * v);
-  build_diag(o, v, c128.buf[K_FOO].p, c128.buf[K_FVV].p, D1.as<double>(), D2.as<double>(), st);
+  const CstSet &C = c128.valid ? c128 : c64;
+  DevBuf f((size_t)(o * o + v * v) * 16);
+  Tens foo = make_tens(f.p, C128, {o, o}), fvv = make_tens((char *)f.p + (size_t)o * o * 16, C128, {v, v});
+  E.permute(zc(1), C.t[K_FOO], "ij", foo, "ij", false);
+  E.permute(zc(1), C.t[K_FVV], "ab", fvv, "ab", false);
+  build_diag(o, v, foo.p, fvv.p, D1.as<double>(), D2.as<double>(), st);
+  CCLR_CUDA(cudaStreamSynchronize(st));
 }
 
+// The working intermediates are built in FP64; the complex64 modes read a rounded copy.
 const CstSet &Model::cst_for(int p) {
+  if (!c128.valid) build_set(t1.p, t2.p, c128, C128);
   if (p == 0) return c128;
-  if (!c64.valid) make_c64(c128, c64);
+  if (!c64.valid) {
+    c64.dt = C64;
+    for (int k = 0; k < K_NCST; ++k) {
+      const Tens &s = c128.t[k];
+      const size_t bytes = (size_t)s.numel() * 8;
+      if (c64.buf[k].bytes != bytes) c64.buf[k].alloc(bytes);
+      Tens d = s;
+      d.p = c64.buf[k].p;
+      d.dt = C64;
+      const std::string m = std::string("abcdefgh").substr(0, s.rank);
+      E.permute(zc(1), s, m, d, m, false);
+      c64.t[k] = d;
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    c64.valid = true;
+  }
   return c64;
+}
+
+// <ij||ab> in complex128 (the T1-independent oovv block), for dE/dT and the F X stencil.
+const Tens &Model::oovv128() {
+  if (!oovv_b.p) {
+    oovv_b.alloc((size_t)o * o * v * v * 16);
+    oovv_t = make_tens(oovv_b.p, C128, {o, o, v, v});
+    if (c128.valid) {
+      E.permute(zc(1), c128.t[K_OOVV], "mnef", oovv_t, "mnef", false);
+    } else {
+      Tens Lov = T(Lov0, {naux, o, v});
+      E.zero(oovv_t);
+      E.contract(zc(1), Lov, "Pme", Lov, "Pnf", oovv_t, "mnef");
+      E.contract(zc(-1), Lov, "Pmf", Lov, "Pne", oovv_t, "mnef");
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+  return oovv_t;
 }
 
 std::vector<DevBuf> &Model::temps(int dt) {
@@ -263,12 +324,12 @@ Tens Model::var_tens(int id, int dt, void *p) const {
 void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out) {
   const int dt = C.dt;
   if (dt == C64 && E.tc_mode) {
-    const int seg = E.tc_mode == 2 ? 3 : 1;
-    if (!ltc.ready(seg) || ltc_src != C.t[K_LVV].p) {
-      ltc.prepare(E, C.t[K_LVV], o, v, naux, seg);
-      ltc_src = C.t[K_LVV].p;
+    const int seg = E.tc_mode == 2 ? 3 : 1, k = E.tc_mode == 2 ? 1 : 0;
+    if (!ltc[k].ready(seg) || ltc_src[k] != C.t[K_LVV].p) {
+      ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg);
+      ltc_src[k] = C.t[K_LVV].p;
     }
-    ltc.apply(E, dir, alpha, in.p, out.p);
+    ltc[k].apply(E, dir, alpha, in.p, out.p);
     return;
   }
   const Tens &Lvv = C.t[K_LVV];
@@ -320,6 +381,7 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
         case OP_PERM: E.permute(op.alpha, V(op.in), op.mi, V(op.out), op.mo, true); break;
         case OP_ZERO: E.zero(V(op.out)); break;
         case OP_LADDER: run_ladder(+1, op.alpha, V(op.in), V(op.out)); break;
+        case OP_ANTISYM: antisym_apply(dt, o, v, +1, ptr[op.out], ptr[op.in], ptr[op.in2], ptr[op.in3], st); break;
       }
     }
   } else {
@@ -340,6 +402,7 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
         case OP_PERM: E.permute(op.alpha, V(op.out), op.mo, V(op.in), op.mi, true); break;
         case OP_ZERO: E.zero(V(op.out)); break;
         case OP_LADDER: run_ladder(-1, op.alpha, V(op.out), V(op.in)); break;
+        case OP_ANTISYM: antisym_apply(dt, o, v, -1, ptr[op.out], ptr[op.in], ptr[op.in2], ptr[op.in3], st); break;
       }
     }
     Tens out2 = var_tens(3, dt, s2);
@@ -463,15 +526,14 @@ Program build_sigma_program(int o, int v, int naux) {
   C(1, K_WOOOV, "mnje", X1, "ne", Xoo, "mj");
   C(0.5, K_OOVV, "mnef", X2, "jnef", Xoo, "mj");
   C(-1, K_T2, "imab", Xoo, "mj", Rij, "ijab");
-  // antisymmetrisers
-  PM(1, Rab, "ijab", S2, "ijab");
-  PM(-1, Rab, "ijab", S2, "ijba");
-  PM(1, Rij, "ijab", S2, "ijab");
-  PM(-1, Rij, "ijab", S2, "jiab");
-  PM(1, Rijab, "ijab", S2, "ijab");
-  PM(-1, Rijab, "ijab", S2, "jiab");
-  PM(-1, Rijab, "ijab", S2, "ijba");
-  PM(1, Rijab, "ijab", S2, "jiba");
+  // antisymmetrisers P(ab), P(ij), P(ij)P(ab), applied in one pass
+  {
+    Op a{OP_ANTISYM, zc(1), -1, "", "", "", Rab, S2};
+    a.in2 = Rij;
+    a.in3 = Rijab;
+    p.ops.push_back(a);
+  }
+  (void)PM;
   return p;
 }
 

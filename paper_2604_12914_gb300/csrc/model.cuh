@@ -26,7 +26,7 @@ struct CstSet {
   bool valid = false;
 };
 
-enum OpKind { OP_CONTRACT, OP_PERM, OP_ZERO, OP_LADDER };
+enum OpKind { OP_CONTRACT, OP_PERM, OP_ZERO, OP_LADDER, OP_ANTISYM };
 
 struct Op {
   OpKind kind;
@@ -34,6 +34,7 @@ struct Op {
   int cst = -1;
   std::string mc, mi, mo;
   int in = -1, out = -1;
+  int in2 = -1, in3 = -1;  // OP_ANTISYM: in = R(ab), in2 = R(ij), in3 = R(ij)(ab)
 };
 
 struct VarSpec {
@@ -66,6 +67,9 @@ class Model {
   DevBuf mu;                        // [3][n][n]
   DevBuf t1, t2;                    // [o][v], [o][o][v][v]
   DevBuf h;                         // one-body part of H, [n][n]
+  DevBuf Loo64, Lov64, Lvo64, Lvv64, h64;  // complex64 copies (complex64 builds)
+  DevBuf oovv_b;
+  Tens oovv_t;
 
   CstSet c128, c64;                 // intermediates at the current T
   DevBuf D1, D2;                    // preconditioner diagonal (real)
@@ -73,16 +77,18 @@ class Model {
   std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision
   int prec = 0;
   DevBuf ladW;                      // ladder formation scratch (CUDA-core path)
-  LadderTC ltc;                     // packed tensor-core ladder (complex64 modes)
-  const void *ltc_src = nullptr;
+  LadderTC ltc[2];                  // packed tensor-core ladder: [0] TF32, [1] 3xTF32
+  const void *ltc_src[2] = {nullptr, nullptr};
   float ms_last[3] = {0, 0, 0};   // last apply(): ladder, everything else, total (ms)
   Timers tm;
 
   void upload_inputs(const double *eps_h, const double *L, const double *mu_h,
                      const double *t1_h, const double *t2_h, int device_ptrs);
-  // Build dressed blocks + intermediates for amplitudes (t1d, t2d) into `out` (FP64).
-  void build_set(const void *t1d, const void *t2d, CstSet &out);
-  void make_c64(const CstSet &src, CstSet &dst);
+  // Build dressed blocks + intermediates for amplitudes (t1d, t2d; complex128 device) in
+  // precision dt (complex64 on the tensor cores with the 3xTF32 split).
+  void build_set(const void *t1d, const void *t2d, CstSet &out, int dt);
+  void ensure_src64();
+  const Tens &oovv128();
   void build_diagonal();
   const CstSet &cst_for(int prec_) ;
 

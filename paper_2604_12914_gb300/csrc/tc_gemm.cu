@@ -19,10 +19,13 @@ constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 
 struct TcParams {
   int M, N, K, BN;
+  int nMt, nNt, band;   // tile counts; M tiles per raster band (N varies fastest inside a band)
+  int kb_per_split;     // K blocks per split (grid.y splits of K, atomically summed)
   float *C;
   long long ldc;
   float ar, ai;
-  int accumulate;
+  int accumulate;       // add to C (always true when split)
+  int atomic;           // split-K: combine partial tiles with atomicAdd
   int *err;
 };
 
@@ -123,8 +126,22 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t *tslot = (uint32_t *)(bars + 2 * STAGES + 1);
   int *progress = (int *)(tslot + 1);  // [0] loads issued, [1] stages consumed
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = (p.K + BK - 1) / BK;
+  // banded rasterisation: consecutive CTAs share one B tile column across a band of M tiles,
+  // so the band's A tiles and the current B tiles stay in L2
+  int m_tile, n_tile;
+  {
+    const int id = blockIdx.x;
+    const int per_band = p.band * p.nNt;
+    const int b = id / per_band;
+    const int local = id - b * per_band;
+    const int mb = min(p.band, p.nMt - b * p.band);
+    m_tile = b * p.band + local % mb;
+    n_tile = local / mb;
+  }
+  const int m0 = m_tile * BM, n0 = n_tile * BN;
+  const int nk_all = (p.K + BK - 1) / BK;
+  const int kb0 = blockIdx.y * p.kb_per_split;
+  const int nk = max(0, min(nk_all - kb0, p.kb_per_split));
   const uint32_t tcols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
 
   if (threadIdx.x == 0) {
@@ -157,8 +174,8 @@ __global__ void __launch_bounds__(128, 1)
       if (kb >= STAGES && !mbar_wait(su32(bars + STAGES + s), ph ^ 1u, p.err)) break;
       asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bars + s)), "r"(bytes)
                    : "memory");
-      tma_load_2d(sA + s * BM * BK, &tmA, kb * BK, m0, su32(bars + s));
-      tma_load_2d(sB + s * BN * BK, &tmB, kb * BK, n0, su32(bars + s));
+      tma_load_2d(sA + s * BM * BK, &tmA, (kb0 + kb) * BK, m0, su32(bars + s));
+      tma_load_2d(sB + s * BN * BK, &tmB, (kb0 + kb) * BK, n0, su32(bars + s));
     }
     progress[0] = kb;
   } else if (warp == 1 && lane == 0) {
@@ -187,7 +204,7 @@ __global__ void __launch_bounds__(128, 1)
   ok = __all_sync(0xffffffffu, ok) && (*(volatile int *)p.err == 0);
   ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok) {
+  if (ok && nk > 0) {
     const int row = m0 + warp * 32 + lane;
     float *crow = p.C + (long long)row * p.ldc;
     for (int c0 = 0; c0 < BN; c0 += 16) {
@@ -200,12 +217,17 @@ __global__ void __launch_bounds__(128, 1)
           if (n < p.N) {
             const float re = __uint_as_float(r[j]), im = __uint_as_float(r[j + 1]);
             float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
-            if (p.accumulate) {
-              vr += crow[n];
-              vi += crow[n + 1];
+            if (p.atomic) {
+              atomicAdd(crow + n, vr);
+              atomicAdd(crow + n + 1, vi);
+            } else {
+              if (p.accumulate) {
+                vr += crow[n];
+                vi += crow[n + 1];
+              }
+              crow[n] = vr;
+              crow[n + 1] = vi;
             }
-            crow[n] = vr;
-            crow[n + 1] = vi;
           }
         }
       }
@@ -281,6 +303,50 @@ __global__ void prep_b_kernel(const float2 *B, int64_t sbk, int64_t sbn, int64_t
   }
 }
 
+// Transposing preparation: the source is contiguous along m (A) or n (B) and strided along
+// k; 32 x 32 tiles through shared memory so that reads and writes are both coalesced.
+__global__ void prep_tiled_kernel(const float2 *src, int64_t s_mn, int64_t s_k, int64_t MN, int64_t K,
+                                  int64_t Kp, int seg, int isB, float *dst, int64_t ldd) {
+  __shared__ float2 tile[32][33];
+  const int64_t tmn = (MN + 31) / 32, tk = (Kp + 31) / 32;
+  for (int64_t t = blockIdx.x; t < tmn * tk; t += gridDim.x) {
+    const int64_t mn0 = (t % tmn) * 32, k0 = (t / tmn) * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t mn = mn0 + threadIdx.x, k = k0 + r;
+      float2 v = make_float2(0.f, 0.f);
+      if (mn < MN && k < K) v = src[mn * s_mn + k * s_k];
+      tile[r][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int64_t mn = mn0 + r, k = k0 + threadIdx.x;
+      if (mn < MN && k < Kp) {
+        const float2 v = tile[threadIdx.x][r];
+        if (!isB) {
+          float *row = dst + mn * ldd;
+          if (seg == 1) { row[2 * k] = v.x; row[2 * k + 1] = v.y; }
+          else {
+            const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
+            row[2 * k] = hr; row[2 * k + 1] = hi;
+            row[2 * Kp + 2 * k] = hr; row[2 * Kp + 2 * k + 1] = hi;
+            row[4 * Kp + 2 * k] = v.x - hr; row[4 * Kp + 2 * k + 1] = v.y - hi;
+          }
+        } else {
+          float *r0 = dst + (2 * mn) * ldd, *r1 = dst + (2 * mn + 1) * ldd;
+          if (seg == 1) { r0[2 * k] = v.x; r0[2 * k + 1] = -v.y; r1[2 * k] = v.y; r1[2 * k + 1] = v.x; }
+          else {
+            const float hr = tf32_hi(v.x), hi = tf32_hi(v.y), lr = v.x - hr, li = v.y - hi;
+            r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
+            r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
+            r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 int *g_err = nullptr;
 std::once_flag g_once;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -336,6 +402,14 @@ void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, in
                int64_t ldd, cudaStream_t st) {
   const int64_t Kp = tc_kpad(K);
   CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_a: row too short");
+  if (sak != 1 && sam == 1 && M >= 8) {
+    const int64_t nt = ((M + 31) / 32) * ((Kp + 31) / 32);
+    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
+        (const float2 *)A, sam, sak, M, K, Kp, seg, 0, dst, ldd);
+    count_launch();
+    CCLR_CUDA(cudaGetLastError());
+    return;
+  }
   prep_a_kernel<<<grid1d(M * Kp), 256, 0, st>>>((const float2 *)A, sam, sak, M, K, Kp, seg, dst, ldd);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
@@ -345,13 +419,22 @@ void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, in
                int64_t ldd, cudaStream_t st) {
   const int64_t Kp = tc_kpad(K);
   CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_b: row too short");
+  if (sbk != 1 && sbn == 1 && N >= 8) {
+    const int64_t nt = ((N + 31) / 32) * ((Kp + 31) / 32);
+    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
+        (const float2 *)B, sbn, sbk, N, K, Kp, seg, 1, dst, ldd);
+    count_launch();
+    CCLR_CUDA(cudaGetLastError());
+    return;
+  }
   prep_b_kernel<<<grid1d(N * Kp), 256, 0, st>>>((const float2 *)B, sbk, sbn, K, N, Kp, seg, dst, ldd);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
-void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-             int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
+static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
+                         int max_kb_per_split, cudaStream_t st) {
   std::call_once(g_once, init_once);
   if (M <= 0 || Nreal <= 0) return;
   CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
@@ -366,30 +449,56 @@ void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M
   p.N = (int)Nreal;
   p.K = (int)Kreal;
   p.BN = BN;
+  p.nMt = (int)((M + BM - 1) / BM);
+  p.nNt = (int)((Nreal + BN - 1) / BN);
+  // band of M tiles whose A rows (about 32 MB) stay in L2 while N sweeps
+  p.band = (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * 4 + 1)));
+  const int nk = (int)((Kreal + BK - 1) / BK);
+  const int64_t tiles = (int64_t)p.nMt * p.nNt;
+  // split K when the tile grid cannot fill the GPU (two CTAs' worth per SM), at least
+  // 16 K blocks per split
+  int splits = 1;
+  if (tiles < 2 * 152 && nk >= 32)
+    splits = (int)std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, nk / 16));
+  // bound the length of each accumulation chain (accuracy of the split-precision passes)
+  if (max_kb_per_split > 0) splits = std::max(splits, (nk + max_kb_per_split - 1) / max_kb_per_split);
+  splits = std::min(splits, 65535);
+  p.kb_per_split = (nk + splits - 1) / splits;
+  splits = (nk + p.kb_per_split - 1) / p.kb_per_split;
   p.C = C;
   p.ldc = ldc_floats;
   p.ar = (float)alpha.re;
   p.ai = (float)alpha.im;
-  p.accumulate = accumulate ? 1 : 0;
+  p.atomic = splits > 1 ? 1 : 0;
+  p.accumulate = (accumulate || splits > 1) ? 1 : 0;
   p.err = g_err;
+  if (splits > 1 && !accumulate)
+    CCLR_CUDA(cudaMemset2DAsync(C, (size_t)ldc_floats * 4, 0, (size_t)Nreal * 4, (size_t)M, st));
   const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (2 * STAGES + 1) * 8 + 16;
-  const int64_t gy = (Nreal + BN - 1) / BN;
-  CCLR_REQUIRE(gy <= 65535, "tc_gemm: too many N tiles");
-  dim3 grid((unsigned)((M + BM - 1) / BM), (unsigned)gy);
+  CCLR_REQUIRE(tiles < (1ll << 31) && splits <= 65535, "tc_gemm: grid too large");
+  dim3 grid((unsigned)tiles, (unsigned)splits);
   tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, p);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
+void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+             int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
+  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kreal, C, ldc_floats, alpha, accumulate, 0, st);
+}
+
+// The tensor-core accumulation error was measured to grow linearly with the chain length,
+// so the split passes keep every accumulator to at most 64 K blocks (2048 real K) and sum
+// the partial tiles in FP32.
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                  int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
                  cudaStream_t st) {
   if (seg == 1) {
-    tc_gemm(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, accumulate, st);
+    tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, accumulate, 0, st);
     return;
   }
-  tc_gemm(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, ldc_floats, alpha, accumulate, st);
-  tc_gemm(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, true, st);
+  tc_gemm_impl(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, ldc_floats, alpha, accumulate, 64, st);
+  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, true, 64, st);
 }
 
 int tc_error(cudaStream_t st) {

@@ -54,8 +54,9 @@ def _sample_check(name, prec, tol, n2=10, n1=6, seed=2):
     assert np.abs(g2 + g2.transpose(0, 1, 3, 2)).max() <= 1e-6 * np.abs(g2).max()
 
 
-def test_c2_sigma_c64_sampled_entries():
-    _sample_check("C2", "fp32", 2e-5)
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-5), ("3xtf32", 5e-5), ("tf32", 3e-3)])
+def test_c2_sigma_c64_sampled_entries(prec, tol):
+    _sample_check("C2", prec, tol)
 
 
 def test_c4_sigma_fp64_sampled_entries():

@@ -170,3 +170,16 @@ def test_tensor_core_gemm_selftest(M, N, K, mode):
     tol = 4e-3 if mode == 1 else 1e-8 * K + 2e-6
     assert e_tc < tol, (e_tc, e_fp32)
     assert e_fp32 < 2e-5
+
+
+@pytest.mark.parametrize("prec", ["tf32", "3xtf32"])
+def test_alpha_mixed_precision_within_1e4(prec):
+    """Mixed-precision alpha (tensor-core sigma, FP64 residual/refinement/subspace/alpha)
+    against the FP64 oracle: |delta alpha| < 1e-4 a.u. for every entry."""
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy(), prec=prec)
+    for omega in (0.0, 0.0428):
+        al, st = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-9)
+        ref = R.alpha(P, [as_t(m) for m in s.mu], omega).numpy()
+        assert np.abs(al[0] - ref).max() < 1e-4, (prec, omega, np.abs(al[0] - ref).max())
+    ctx.close()
