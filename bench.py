@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--no-alpha", action="store_true")
     ap.add_argument("--alpha-config", default="C1")
     ap.add_argument("--alpha-scale", type=float, default=0.2)
+    ap.add_argument("--batch-rhs", type=int, default=9)
     return ap.parse_args()
 
 
@@ -306,6 +307,31 @@ def run_cclr(args):
     e2e = world * args.steps / (float(ms_e.item()) / 1e3)
     bytes_io = (x1p.numel() + x2p.numel()) * 16
 
+    # batched: several right-hand sides share each formed <ab||ef>~ block
+    batched = None
+    if args.batch_rhs > 1:
+        nb = args.batch_rhs
+        xb1h, xb2h = random_amplitudes(o, v, seed=50 + rank, nvec=nb)
+        xb1 = torch.from_numpy(xb1h).cuda()
+        xb2 = torch.from_numpy(xb2h).cuda()
+        del xb2h
+        sb1 = torch.empty_like(xb1)
+        sb2 = torch.empty_like(xb2)
+        ctx.sigma_into(xb1, xb2, sb1, sb2, nrhs=nb)
+        barrier()
+        e0.record(stream)
+        reps = max(1, args.steps // 3)
+        lad_b = []
+        for _ in range(reps):
+            ctx.sigma_into(xb1, xb2, sb1, sb2, nrhs=nb)
+            lad_b.append(float(ctx.cc_lr_last_timings()[0]))
+        e1.record(stream)
+        barrier()
+        msb = e0.elapsed_time(e1) / reps
+        batched = {"nrhs": nb, "sigma_vectors_per_s": world * nb / (msb / 1e3), "ms_per_batch": msb,
+                   "ladder_ms_per_batch": sum(lad_b) / len(lad_b)}
+        del xb1, xb2, sb1, sb2
+
     alg = algorithmic(o, v, naux)
     lad_ms = sum(lad) / len(lad)
     bound, peak, how = ladder_peak(args.prec)
@@ -335,6 +361,8 @@ def run_cclr(args):
         }
         if tta is not None:
             out["time_to_alpha"] = tta
+        if batched is not None:
+            out["batched"] = batched
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)

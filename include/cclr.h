@@ -123,6 +123,13 @@ cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
 /* Switch the arithmetic of subsequent sigma / sigma^T / solves. */
 cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
 
+/* Linear solver of cc_lr_solve / cc_lr_solve_x / cc_lr_lambda: method 1 = restarted
+ * GMRES with the diagonal preconditioner (default; subspace = restart length),
+ * method 0 = DIIS extrapolation of preconditioned Jacobi steps (subspace ignored; the
+ * calls' diis_depth applies).  In the mixed modes either method solves the corrections
+ * of the FP64-residual iterative refinement. */
+cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace);
+
 /* Device-side timing (CUDA events on the context's stream) of the last sigma or
  * sigma^T vector, in milliseconds: [0] particle-particle ladder (formation of <ab|ef>~
  * from L~_vv and its contraction with X), [1] every other kernel, [2] total. */

@@ -21,7 +21,7 @@ CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32 = range(4)
 PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32}
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
-           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_last_timings",
+           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_solver", "cc_lr_last_timings",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
 
@@ -63,6 +63,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_lambda": [P, D, P, P],
         "cc_lr_get_t": [P, P, P],
         "cc_lr_set_precision": [P, I],
+        "cc_lr_set_solver": [P, I, I],
         "cc_lr_last_timings": [P, P],
         "cc_lr_free": [P],
         "cc_lr_strerror": [I],
@@ -97,7 +98,11 @@ def _ptr(a):
     if isinstance(a, np.ndarray):
         assert a.flags["C_CONTIGUOUS"]
         return a.ctypes.data
-    return a.data_ptr()   # torch tensor
+    # torch tensor: the library reads raw memory, so lazy conjugate / negative views and
+    # non-contiguous strides are refused rather than silently misread
+    if a.is_conj() or a.is_neg() or not a.is_contiguous():
+        raise ValueError("pass a contiguous tensor without lazy conj/neg bits (use resolve_conj())")
+    return a.data_ptr()
 
 
 def _c128(a):
@@ -215,6 +220,10 @@ class Context:
     def cc_lr_set_precision(self, prec):
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         _check(load().cc_lr_set_precision(self._h, p))
+
+    def cc_lr_set_solver(self, method="gmres", subspace=30):
+        m = {"gmres": 1, "diis": 0}[method] if isinstance(method, str) else int(method)
+        _check(load().cc_lr_set_solver(self._h, m, int(subspace)))
 
     def cc_lr_last_timings(self):
         out = np.zeros(3, dtype=np.float64)

@@ -43,8 +43,7 @@ struct cclr_ctx {
   size_t budget = 0;
   bool have_lambda = false;
   AVec lam;
-  AVec stage_in, stage_out;       // host <-> device staging (complex128)
-  DevBuf x64, s64;                // complex64 copies for mixed precision sigma
+  std::vector<AVec> stage_in, stage_out;  // host <-> device staging (complex128), per RHS
   CstSet shift;                   // intermediates at shifted amplitudes (F X stencils)
   int sigma_calls = 0;
 
@@ -78,20 +77,38 @@ struct cclr_ctx {
   }
 
   // s = A x (dir +1) or x A (dir -1) in the current precision; x, s complex128 amplitude vectors
-  void op(int dir, const void *x, void *s, const CstSet *set = nullptr) {
-    ++sigma_calls;
-    const int prec = M->prec;
-    if (set == nullptr) set = &M->cst_for(prec);
-    if (set->dt == C128) {
-      M->apply(dir, *set, x, (const char *)x + n1 * 16, s, (char *)s + n1 * 16);
-      return;
+  void op(int dir, const void *x, void *s, const CstSet *set = nullptr) { op_batch(dir, 1, &x, &s, set); }
+
+  // the same for nr vectors at once (the ladder's integral blocks are formed once for all)
+  std::vector<DevBuf> x64, s64;   // complex64 copies for the mixed-precision sigma
+  void op_batch(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set = nullptr) {
+    sigma_calls += nr;
+    if (set == nullptr) set = &M->cst_for(M->prec);
+    std::vector<const void *> a1(nr), a2(nr);
+    std::vector<void *> b1(nr), b2(nr);
+    const size_t es = set->dt == C128 ? 16 : 8;
+    if (set->dt == C64 && (int)x64.size() < nr) {
+      x64.resize(nr);
+      s64.resize(nr);
     }
-    if (!x64.p) { x64.alloc((size_t)ntot() * 8); s64.alloc((size_t)ntot() * 8); }
-    Tens xi = make_tens((void *)x, C128, {ntot()}), xo = make_tens(x64.p, C64, {ntot()});
-    M->E.permute(zc(1), xi, "a", xo, "a", false);
-    M->apply(dir, *set, x64.p, (char *)x64.p + n1 * 8, s64.p, (char *)s64.p + n1 * 8);
-    Tens si = make_tens(s64.p, C64, {ntot()}), so = make_tens(s, C128, {ntot()});
-    M->E.permute(zc(1), si, "a", so, "a", false);
+    for (int r = 0; r < nr; ++r) {
+      const void *x = xs[r];
+      void *s = ss[r];
+      if (set->dt == C64) {
+        if (!x64[r].p) { x64[r].alloc((size_t)ntot() * 8); s64[r].alloc((size_t)ntot() * 8); }
+        M->E.permute(zc(1), make_tens((void *)x, C128, {ntot()}), "a", make_tens(x64[r].p, C64, {ntot()}), "a", false);
+        x = x64[r].p;
+        s = s64[r].p;
+      }
+      a1[r] = x;
+      a2[r] = (const char *)x + n1 * es;
+      b1[r] = s;
+      b2[r] = (char *)s + n1 * es;
+    }
+    M->apply_batch(dir, *set, nr, a1.data(), a2.data(), b1.data(), b2.data());
+    if (set->dt == C64)
+      for (int r = 0; r < nr; ++r)
+        M->E.permute(zc(1), make_tens(s64[r].p, C64, {ntot()}), "a", make_tens(ss[r], C128, {ntot()}), "a", false);
   }
 
   // Solve (Op - omega) x = b.  FP64 mode: preconditioned DIIS.  Mixed modes: iterative
@@ -104,18 +121,20 @@ struct cclr_ctx {
     if (M->prec == CCLR_FP64) return solve_diis(dir, omega, b, x, tol, depth, maxit, its);
     const int lo = M->prec;
     const double inner_tol = lo == CCLR_C64_TF32 ? 1e-2 : 1e-5;
-    AVec s, r, d;
-    alloc_vec(s);
-    alloc_vec(r);
-    alloc_vec(d);
-    const double bn = std::max(norm(b), 1e-300);
-    CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
-    copy(b, r.b.p);
-    double rel = 1.0;
-    int used = 0;
     // each correction gets a bounded number of DIIS steps: near its precision floor the
     // low-precision DIIS stalls, and one more FP64 residual is cheaper than stalling
     const int inner_cap = lo == CCLR_C64_TF32 ? 30 : 40;
+    AVec s, r, d, xb;
+    alloc_vec(s);
+    alloc_vec(r);
+    alloc_vec(d);
+    alloc_vec(xb);
+    const double bn = std::max(norm(b), 1e-300);
+    CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
+    copy(b, r.b.p);
+    double rel = 1.0, rel_prev = 1e300;
+    int used = 0;
+    bool stalled = false;
     for (int outer = 0; outer < 40 && used < maxit; ++outer) {
       if (outer > 0) {
         M->prec = CCLR_FP64;
@@ -129,7 +148,18 @@ struct cclr_ctx {
       rel = norm(r.b.p) / bn;
       if (verbose()) std::fprintf(stderr, "cclr refine dir=%d omega=%g outer=%d rel=%.3e\n", dir, omega, outer, rel);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
+      if (rel > 0.5 * rel_prev) {
+        // the last correction did not help: go back to the best iterate and stop refining
+        if (rel > rel_prev) {
+          copy(xb.b.p, x);
+          rel = rel_prev;
+        }
+        stalled = true;
+        break;
+      }
       if (rel < tol) break;
+      copy(x, xb.b.p);
+      rel_prev = rel;
       int inner = 0;
       solve_diis(dir, omega, r.b.p, d.b.p, std::max(inner_tol, 0.3 * tol / rel), depth,
                  std::min(inner_cap, maxit - used), &inner);
@@ -137,12 +167,128 @@ struct cclr_ctx {
       if (its) *its += inner;
       axpy(zd(1), d.b.p, x);
     }
+    if ((stalled || rel >= tol) && used < maxit) {
+      // finish in FP64, warm-started from the refined solution
+      M->prec = CCLR_FP64;
+      int rest = 0;
+      rel = solve_diis(dir, omega, b, x, tol, depth, maxit - used, &rest, true);
+      M->prec = lo;
+      if (its) *its += rest;
+      if (verbose()) std::fprintf(stderr, "cclr fp64 finish dir=%d iterations=%d rel=%.3e\n", dir, rest, rel);
+    }
     return rel;
   }
 
-  // Preconditioned DIIS on (Op - omega) x = b in the current precision.
+  // Krylov method of the linear solves: 1 = restarted GMRES (default), 0 = DIIS.
+  int method = 1;
+  int krylov = 30;
+
   double solve_diis(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
-                    int *its) {
+                    int *its, bool warm = false) {
+    if (method == 1) return solve_gmres(dir, omega, b, x, tol, krylov, maxit, its, warm);
+    return solve_pulay(dir, omega, b, x, tol, depth, maxit, its, warm);
+  }
+
+  // Right-preconditioned restarted GMRES(m) on (Op - omega) x = b in the current precision:
+  // preconditioner P = (D - omega)^-1 (diagonal of A), modified Gram-Schmidt in the
+  // weighted Hermitian inner product (singles 1, doubles 1/4), Givens rotations and the
+  // small least-squares problem on the host in FP64.
+  std::vector<AVec> kv;  // Krylov basis (kept between calls)
+  double solve_gmres(int dir, double omega, const void *b, void *x, double tol, int m, int maxit,
+                     int *its, bool warm) {
+    m = std::max(2, std::min(m, 100));
+    if ((int)kv.size() < m + 1) kv.resize(m + 1);
+    for (int k = 0; k <= m; ++k) alloc_vec(kv[k]);
+    AVec z, w;
+    alloc_vec(z);
+    alloc_vec(w);
+    const double bn = std::max(norm(b), 1e-300);
+    if (!warm) CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
+    double rel = 1.0;
+    int used = 0;
+    std::vector<zd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
+    while (used < maxit) {
+      // r = b - (Op - omega) x
+      copy(b, kv[0].b.p);
+      if (warm || used > 0) {
+        op(dir, x, w.b.p);
+        axpy(zd(-1), w.b.p, kv[0].b.p);
+        axpy(zd(omega), x, kv[0].b.p);
+      }
+      warm = true;
+      double beta = norm(kv[0].b.p);
+      rel = beta / bn;
+      if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega, used, rel, M->prec);
+      if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
+      if (rel < tol || beta == 0.0) break;
+      scal(zd(1.0 / beta), kv[0].b.p);
+      std::fill(g.begin(), g.end(), zd(0));
+      g[0] = beta;
+      int j = 0;
+      for (; j < m && used < maxit; ++j) {
+        precond(omega, kv[j].b.p, z.b.p);
+        op(dir, z.b.p, w.b.p);
+        axpy(zd(-omega), z.b.p, w.b.p);
+        ++used;
+        if (its) ++*its;
+        for (int i = 0; i <= j; ++i) {
+          const zd hij = dot(kv[i].b.p, w.b.p, 1);
+          H[(size_t)i * m + j] = hij;
+          axpy(-hij, kv[i].b.p, w.b.p);
+        }
+        const double hn = norm(w.b.p);
+        H[(size_t)(j + 1) * m + j] = hn;
+        if (hn > 0) {
+          copy(w.b.p, kv[j + 1].b.p);
+          scal(zd(1.0 / hn), kv[j + 1].b.p);
+        }
+        // apply previous rotations to column j, then a new one
+        for (int i = 0; i < j; ++i) {
+          const zd a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
+          H[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * c;
+          H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * c;
+        }
+        const zd a = H[(size_t)j * m + j], c = H[(size_t)(j + 1) * m + j];
+        const double den = std::sqrt(std::norm(a) + std::norm(c));
+        cs[j] = den > 0 ? a / den : zd(1);
+        sn[j] = den > 0 ? c / den : zd(0);
+        H[(size_t)j * m + j] = std::conj(cs[j]) * a + std::conj(sn[j]) * c;
+        H[(size_t)(j + 1) * m + j] = 0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = std::conj(cs[j]) * g[j];
+        rel = std::abs(g[j + 1]) / bn;
+        if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d est=%.3e\n", dir, omega, used, rel);
+        if (rel < tol || hn == 0.0) { ++j; break; }
+      }
+      // y = H(0:j,0:j)^-1 g(0:j); x += P (sum_i y_i v_i)
+      std::vector<zd> y(j);
+      for (int i = j - 1; i >= 0; --i) {
+        zd t = g[i];
+        for (int k = i + 1; k < j; ++k) t -= H[(size_t)i * m + k] * y[k];
+        const zd d = H[(size_t)i * m + i];
+        y[i] = std::abs(d) > 0 ? t / d : zd(0);
+      }
+      CCLR_CUDA(cudaMemsetAsync(w.b.p, 0, (size_t)ntot() * 16, st));
+      for (int i = 0; i < j; ++i) axpy(y[i], kv[i].b.p, w.b.p);
+      precond(omega, w.b.p, z.b.p);
+      axpy(zd(1), z.b.p, x);
+      if (rel < tol) {
+        // true residual for the return value
+        copy(b, kv[0].b.p);
+        op(dir, x, w.b.p);
+        axpy(zd(-1), w.b.p, kv[0].b.p);
+        axpy(zd(omega), x, kv[0].b.p);
+        rel = norm(kv[0].b.p) / bn;
+        if (rel < tol) break;
+      }
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return rel;
+  }
+
+  // Preconditioned DIIS (Pulay extrapolation over Jacobi steps) on (Op - omega) x = b.
+  double solve_pulay(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+                     int *its, bool warm = false) {
     depth = std::max(2, std::min(depth, 16));
     std::vector<AVec> X(depth), Er(depth);
     for (auto &a : X) alloc_vec(a);
@@ -151,7 +297,7 @@ struct cclr_ctx {
     alloc_vec(s);
     alloc_vec(r);
     const double bn = std::max(norm(b), 1e-300);
-    precond(omega, b, x);
+    if (!warm) precond(omega, b, x);
     std::vector<zd> B((size_t)depth * depth);
     int nh = 0, head = 0;
     double rel = 1e300;
@@ -417,14 +563,31 @@ static cclr_status sigma_common(cclr_ctx *c, int dir, int nrhs, const double *x1
   if (!c || nrhs < 0 || (nrhs > 0 && (!x1 || !x2 || !s1 || !s2)))
     return (cclr_status)fail(CCLR_EINVAL, "bad sigma arguments");
   return (cclr_status)guarded([&] {
-    c->alloc_vec(c->stage_in);
-    c->alloc_vec(c->stage_out);
-    for (int r = 0; r < nrhs; ++r) {
-      to_dev(c, x1 + (size_t)r * c->n1 * 2, c->stage_in.p1(), (size_t)c->n1 * 16);
-      to_dev(c, x2 + (size_t)r * c->n2 * 2, c->stage_in.p2(c->n1), (size_t)c->n2 * 16);
-      c->op(dir, c->stage_in.b.p, c->stage_out.b.p);
-      from_dev(c, c->stage_out.p1(), s1 + (size_t)r * c->n1 * 2, (size_t)c->n1 * 16);
-      from_dev(c, c->stage_out.p2(c->n1), s2 + (size_t)r * c->n2 * 2, (size_t)c->n2 * 16);
+    // all right-hand sides go through the device together (shared integral formation)
+    const int chunk = std::max(1, std::min(nrhs, 32));
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+      const int nr = std::min(chunk, nrhs - r0);
+      if ((int)c->stage_in.size() < nr) {
+        c->stage_in.resize(nr);
+        c->stage_out.resize(nr);
+      }
+      std::vector<const void *> xs(nr);
+      std::vector<void *> ss(nr);
+      for (int q = 0; q < nr; ++q) {
+        const int r = r0 + q;
+        c->alloc_vec(c->stage_in[q]);
+        c->alloc_vec(c->stage_out[q]);
+        to_dev(c, x1 + (size_t)r * c->n1 * 2, c->stage_in[q].p1(), (size_t)c->n1 * 16);
+        to_dev(c, x2 + (size_t)r * c->n2 * 2, c->stage_in[q].p2(c->n1), (size_t)c->n2 * 16);
+        xs[q] = c->stage_in[q].b.p;
+        ss[q] = c->stage_out[q].b.p;
+      }
+      c->op_batch(dir, nr, xs.data(), ss.data());
+      for (int q = 0; q < nr; ++q) {
+        const int r = r0 + q;
+        from_dev(c, c->stage_out[q].p1(), s1 + (size_t)r * c->n1 * 2, (size_t)c->n1 * 16);
+        from_dev(c, c->stage_out[q].p2(c->n1), s2 + (size_t)r * c->n2 * 2, (size_t)c->n2 * 16);
+      }
     }
     CCLR_CUDA(cudaStreamSynchronize(c->st));
   });
@@ -441,10 +604,11 @@ cclr_status cc_lr_sigma_T(cclr_ctx *c, int nrhs, const double *y1, const double 
 cclr_status cc_lr_xi(cclr_ctx *c, int comp, double *xi1, double *xi2) {
   if (!c || comp < 0 || comp > 2 || !xi1 || !xi2) return (cclr_status)fail(CCLR_EINVAL, "bad xi arguments");
   return (cclr_status)guarded([&] {
-    c->alloc_vec(c->stage_out);
-    c->xi_vec(comp, c->M->t1.p, c->M->t2.p, c->stage_out.b.p);
-    from_dev(c, c->stage_out.p1(), xi1, (size_t)c->n1 * 16);
-    from_dev(c, c->stage_out.p2(c->n1), xi2, (size_t)c->n2 * 16);
+    AVec out;
+    c->alloc_vec(out);
+    c->xi_vec(comp, c->M->t1.p, c->M->t2.p, out.b.p);
+    from_dev(c, out.p1(), xi1, (size_t)c->n1 * 16);
+    from_dev(c, out.p2(c->n1), xi2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
   });
 }
@@ -574,6 +738,14 @@ cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
     c->M->prec = prec;
     if (prec != CCLR_FP64) c->M->cst_for(prec);
   });
+}
+
+cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace) {
+  if (!c || (method != 0 && method != 1) || subspace < 0 || subspace > 100)
+    return (cclr_status)fail(CCLR_EINVAL, "bad solver arguments");
+  c->method = method;
+  if (subspace >= 2) c->krylov = subspace;
+  return CCLR_OK;
 }
 
 cclr_status cc_lr_last_timings(cclr_ctx *c, double *ms3) {

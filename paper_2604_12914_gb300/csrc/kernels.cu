@@ -351,6 +351,50 @@ __global__ void antisym_kernel(int o, int v, int dir, const typename cpx<T>::t *
   }
 }
 
+// In-place projection onto tensors antisymmetric in (i,j) and in (a,b):
+//   S <- 1/4 (S - S(ij) - S(ab) + S(ij)(ab)); entries with i = j or a = b become zero.
+// Each orbit {ijab, jiab, ijba, jiba} is written by the thread of its i<j, a<b member.
+template <typename T>
+__global__ void antisym_project_kernel(int o, int v, typename cpx<T>::t *S) {
+  using C = typename cpx<T>::t;
+  const int64_t vv = (int64_t)v * v, n = (int64_t)o * o * vv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = e % vv, ij = e / vv;
+    const int a = (int)(ab / v), b = (int)(ab % v), i = (int)(ij / o), j = (int)(ij % o);
+    if (i == j || a == b) {
+      C z;
+      z.x = 0;
+      z.y = 0;
+      S[e] = z;
+    } else if (i < j && a < b) {
+      const int64_t e_ba = ij * vv + (int64_t)b * v + a;
+      const int64_t e_ji = ((int64_t)j * o + i) * vv + ab;
+      const int64_t e_jiba = ((int64_t)j * o + i) * vv + (int64_t)b * v + a;
+      const C s1 = S[e], s2 = S[e_ji], s3 = S[e_ba], s4 = S[e_jiba];
+      C q;
+      q.x = (T)0.25 * (s1.x - s2.x - s3.x + s4.x);
+      q.y = (T)0.25 * (s1.y - s2.y - s3.y + s4.y);
+      C mq;
+      mq.x = -q.x;
+      mq.y = -q.y;
+      S[e] = q;
+      S[e_ji] = mq;
+      S[e_ba] = mq;
+      S[e_jiba] = q;
+    }
+  }
+}
+
+void antisym_project(int dt, int o, int v, void *S, cudaStream_t st) {
+  const int64_t n = (int64_t)o * o * v * v;
+  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
+  if (dt == C128) antisym_project_kernel<double><<<g, 256, 0, st>>>(o, v, (double2 *)S);
+  else antisym_project_kernel<float><<<g, 256, 0, st>>>(o, v, (float2 *)S);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
 void antisym_apply(int dt, int o, int v, int dir, void *S, void *Rab, void *Rij, void *R4, cudaStream_t st) {
   const int64_t n = (int64_t)o * o * v * v;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));

@@ -39,6 +39,8 @@ void launch_permute(const PermArgs &a, int dt_in, int dt_out, cudaStream_t st);
 // S += P(ab) Rab + P(ij) Rij + P(ij)P(ab) R4 (dir +1) or the transpose into Rab, Rij, R4
 // (dir -1); all [o][o][v][v].
 void antisym_apply(int dt, int o, int v, int dir, void *S, void *Rab, void *Rij, void *R4, cudaStream_t st);
+// In-place projection of S [o][o][v][v] onto tensors antisymmetric in (i,j) and (a,b).
+void antisym_project(int dt, int o, int v, void *S, cudaStream_t st);
 void vec_axpy(int dt, int64_t n, zc a, const void *x, void *y, cudaStream_t st);
 void vec_scal(int dt, int64_t n, zc a, void *y, cudaStream_t st);
 void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 *part,

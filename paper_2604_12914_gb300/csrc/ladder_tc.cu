@@ -99,15 +99,15 @@ __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *
   }
 }
 
-// out[i,j,a,b] += alpha * S[(ab)][(ij)] with the four antisymmetric images (S [Pv][Po]).
-__global__ void unpack_sig(const float2 *S, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
-                           int64_t Pv, float ar, float ai, float2 *out) {
+// out[i,j,a,b] += alpha * S[(ab) * lds + (ij)] with the four antisymmetric images.
+__global__ void unpack_sig(const float2 *S, int64_t lds, int o, int v, const int2 *op, const int2 *vp,
+                           int64_t Po, int64_t Pv, float ar, float ai, float2 *out) {
   const int64_t total = Po * Pv;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = e / Pv, k = e % Pv;  // n = (i<j), k = (a<b)
     const int2 ij = op[n], ab = vp[k];
-    const float2 s = S[k * Po + n];
+    const float2 s = S[k * lds + n];
     const float2 val = make_float2(ar * s.x - ai * s.y, ar * s.y + ai * s.x);
     const int64_t i = ij.x, j = ij.y, a = ab.x, b = ab.y;
     float2 *p;
@@ -118,7 +118,7 @@ __global__ void unpack_sig(const float2 *S, int o, int v, const int2 *op, const 
   }
 }
 
-// out[i,j,e,f] += alpha * Z[(ij)][(ef)] for i<j, e<f only (Z [Po][Pv]).
+// out[i,j,e,f] += alpha * Z[(ij)][(ef)] for i<j, e<f only (Z rows of Pv).
 __global__ void unpack_z(const float2 *Z, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
                          int64_t Pv, float ar, float ai, float2 *out) {
   const int64_t total = Po * Pv;
@@ -169,30 +169,34 @@ void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int s
   CCLR_CUDA(cudaStreamSynchronize(st));
 }
 
-void LadderTC::apply(Engine &E, int dir, zc alpha, const void *in, void *out) {
+void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out) {
   cudaStream_t st = E.st;
   const int o = o_, v = v_, seg = seg_;
   const int64_t Po = Po_, Pv = Pv_;
-  if (Po == 0 || Pv == 0) return;
+  if (Po == 0 || Pv == 0 || nrhs < 1) return;
   const int64_t vv = (int64_t)v * v;
   const int64_t ldL = 2 * tc_kpad(naux_) * seg;
   const int64_t KpPv = tc_kpad(Pv), ldPv = 2 * KpPv * seg;
   const int ga = std::min(ga_, v);
+  const int64_t NR = (int64_t)nrhs;
   // buffers sized for the first (largest) group
   const int64_t maxpairs = pair_start(v, ga);
   if (W.bytes < (size_t)vv * ga * v * 8) W.alloc((size_t)vv * ga * v * 8);
   const int64_t kpg = tc_kpad(maxpairs);
   const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldPv * 4 : (size_t)2 * Pv * (2 * kpg * seg) * 4;
   if (Wp.bytes < wp_bytes) Wp.alloc(wp_bytes);
-  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * ldPv * 4 : (size_t)Po * (2 * kpg * seg) * 4;
+  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * NR * ldPv * 4 : (size_t)Po * NR * (2 * kpg * seg) * 4;
   if (Xp.bytes < xp_bytes) Xp.alloc(xp_bytes);
-  if (sig.bytes < (size_t)Po * Pv * 8) sig.alloc((size_t)Po * Pv * 8);
+  if (sig.bytes < (size_t)Po * Pv * NR * 8) sig.alloc((size_t)Po * Pv * NR * 8);
   const int2 *op = opairs.as<int2>(), *vp = vpairs.as<int2>();
   if (dir > 0) {
-    pack_x_b<<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in, o, v, op, vp, Po, Pv, KpPv, seg, Xp.as<float>(), ldPv);
-    count_launch();
+    for (int64_t r = 0; r < NR; ++r) {
+      pack_x_b<<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
+                                                  Xp.as<float>() + 2 * Po * r * ldPv, ldPv);
+      count_launch();
+    }
   } else {
-    CCLR_CUDA(cudaMemsetAsync(sig.p, 0, (size_t)Po * Pv * 8, st));
+    CCLR_CUDA(cudaMemsetAsync(sig.p, 0, (size_t)Po * Pv * NR * 8, st));
   }
   for (int a0 = 0; a0 < v - 1; a0 += ga) {
     const int a1 = std::min(v, a0 + ga);
@@ -206,31 +210,35 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, const void *in, void *out) {
       pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
                                                 Wp.as<float>(), ldPv);
       count_launch();
-      // sigT[(ab)][(ij)] = sum_{e<f} <ab||ef>~ X[i,j,e,f]  for the group's pairs
-      tc_gemm_seg(Wp.as<float>(), ldPv, Xp.as<float>(), ldPv, np, 2 * Po, ldPv / seg, seg,
-                  sig.as<float>() + 2 * p0 * Po, 2 * Po, zc(1.0), false, st);
+      // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f]  for the group's pairs, all RHS
+      tc_gemm_seg(Wp.as<float>(), ldPv, Xp.as<float>(), ldPv, np, 2 * Po * NR, ldPv / seg, seg,
+                  sig.as<float>() + 2 * p0 * Po * NR, 2 * Po * NR, zc(1.0), false, st);
     } else {
       const int64_t kg = tc_kpad(np), ldg = 2 * kg * seg;
       pack_w<<<grid1d(Pv * kg), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, kg, seg, 1,
                                               Wp.as<float>(), ldg);
       count_launch();
-      pack_y_a<<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in, o, v, op, vp, Po, p0, np, kg, seg,
-                                                 Xp.as<float>(), ldg);
-      count_launch();
-      // Z[(ij)][(ef)] += sum_{(ab) in group} Y'[(ij)][(ab)] <ab||ef>~
-      tc_gemm_seg(Xp.as<float>(), ldg, Wp.as<float>(), ldg, Po, 2 * Pv, ldg / seg, seg, sig.as<float>(),
+      for (int64_t r = 0; r < NR; ++r) {
+        pack_y_a<<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, p0, np, kg, seg,
+                                                   Xp.as<float>() + Po * r * ldg, ldg);
+        count_launch();
+      }
+      // Z[(r, ij)][(ef)] += sum_{(ab) in group} Y'_r[(ij)][(ab)] <ab||ef>~
+      tc_gemm_seg(Xp.as<float>(), ldg, Wp.as<float>(), ldg, Po * NR, 2 * Pv, ldg / seg, seg, sig.as<float>(),
                   2 * Pv, zc(1.0), true, st);
     }
     CCLR_CUDA(cudaGetLastError());
   }
-  if (dir > 0) {
-    unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>(), o, v, op, vp, Po, Pv, (float)alpha.re,
-                                                 (float)alpha.im, (float2 *)out);
-  } else {
-    unpack_z<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>(), o, v, op, vp, Po, Pv, (float)alpha.re,
-                                               (float)alpha.im, (float2 *)out);
+  for (int64_t r = 0; r < NR; ++r) {
+    if (dir > 0) {
+      unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>() + Po * r, Po * NR, o, v, op, vp, Po, Pv,
+                                                   (float)alpha.re, (float)alpha.im, (float2 *)out[r]);
+    } else {
+      unpack_z<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>() + Po * Pv * r, o, v, op, vp, Po, Pv,
+                                                 (float)alpha.re, (float)alpha.im, (float2 *)out[r]);
+    }
+    count_launch();
   }
-  count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 

@@ -15,9 +15,10 @@ class LadderTC {
   // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (TF32) or 3 (3xTF32).
   void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg);
   bool ready(int seg) const { return seg_ == seg && LA.p != nullptr; }
-  // dir +1: out += alpha * ladder(in);  dir -1: out += alpha * ladder^T(in).
-  // in/out: complex64 [o][o][v][v].
-  void apply(Engine &E, int dir, zc alpha, const void *in, void *out);
+  // dir +1: out[r] += alpha * ladder(in[r]);  dir -1: out[r] += alpha * ladder^T(in[r]),
+  // r = 0..nrhs-1, all complex64 [o][o][v][v].  Each <ab||ef>~ group block is formed once
+  // and contracted with every right-hand side.
+  void apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out);
 
  private:
   int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0;

@@ -290,8 +290,10 @@ const Tens &Model::oovv128() {
   return oovv_t;
 }
 
-std::vector<DevBuf> &Model::temps(int dt) {
-  auto &tv = dt == C128 ? tmp128 : tmp64;
+std::vector<DevBuf> &Model::temps(int dt, int r) {
+  auto &all = dt == C128 ? tmp128 : tmp64;
+  if ((int)all.size() <= r) all.resize(r + 1);
+  auto &tv = all[r];
   if (tv.empty()) {
     tv.resize(prog.vars.size());
     for (size_t k = 0; k < prog.vars.size(); ++k) {
@@ -321,17 +323,23 @@ Tens Model::var_tens(int id, int dt, void *p) const {
 // pp-ladder on CUDA cores: out[i,j,a,b] += alpha sum_ef <ab|ef>~ in[i,j,e,f] (dir +1), or the
 // transpose in'[i,j,e,f] += alpha sum_ab <ab|ef>~ in[i,j,a,b] (dir -1), <ab|ef>~ formed in
 // chunks of a from L~_vv and never stored whole.
-void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out) {
+void Model::ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &in,
+                   const std::vector<Tens> &out) {
   const int dt = C.dt;
+  const int nr = (int)in.size();
   if (dt == C64 && E.tc_mode) {
     const int seg = E.tc_mode == 2 ? 3 : 1, k = E.tc_mode == 2 ? 1 : 0;
     if (!ltc[k].ready(seg) || ltc_src[k] != C.t[K_LVV].p) {
       ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg);
       ltc_src[k] = C.t[K_LVV].p;
     }
-    ltc[k].apply(E, dir, alpha, in.p, out.p);
+    std::vector<const void *> ip(nr);
+    std::vector<void *> outp(nr);
+    for (int r = 0; r < nr; ++r) { ip[r] = in[r].p; outp[r] = out[r].p; }
+    ltc[k].apply(E, dir, alpha, nr, ip.data(), outp.data());
     return;
   }
+  // CUDA cores: <ab|ef>~ formed in chunks of a and contracted with every right-hand side
   const Tens &Lvv = C.t[K_LVV];
   const int64_t per_a = (int64_t)v * v * v * dt_size(dt);
   int64_t ac = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_a));
@@ -341,27 +349,38 @@ void Model::ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Ten
     Tens W = make_tens(ladW.p, dt, {a1 - a0, v, v, v});
     E.zero(W);
     E.contract(zc(1), Lvv.slice(1, a0, a1), "Pae", Lvv, "Pbf", W, "aebf");
-    if (dir > 0) E.contract(alpha, W, "aebf", in, "ijef", out.slice(2, a0, a1), "ijab");
-    else E.contract(alpha, W, "aebf", in.slice(2, a0, a1), "ijab", out, "ijef");
+    for (int r = 0; r < nr; ++r) {
+      if (dir > 0) E.contract(alpha, W, "aebf", in[r], "ijef", out[r].slice(2, a0, a1), "ijab");
+      else E.contract(alpha, W, "aebf", in[r].slice(2, a0, a1), "ijab", out[r], "ijef");
+    }
   }
 }
 
 void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2) {
+  apply_batch(dir, C, 1, &x1, &x2, &s1, &s2);
+}
+
+void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
+                        void *const *s1, void *const *s2) {
   const int dt = C.dt;
   // tensor cores for complex64: TF32 (prec 1) or 3xTF32 (prec 2); FP32 CUDA cores for prec 3
   E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : 0) : 0;
-  auto &tv = temps(dt);
   const int nv = (int)prog.vars.size();
-  std::vector<void *> ptr(nv, nullptr);
-  for (int k = 4; k < nv; ++k) ptr[k] = tv[k].p;
-  auto V = [&](int id) { return var_tens(id, dt, ptr[id]); };
+  std::vector<std::vector<void *>> ptr(nr, std::vector<void *>(nv, nullptr));
+  for (int r = 0; r < nr; ++r) {
+    auto &tv = temps(dt, r);
+    for (int k = 4; k < nv; ++k) ptr[r][k] = tv[k].p;
+  }
+  auto V = [&](int r, int id) { return var_tens(id, dt, ptr[r][id]); };
   auto Cst = [&](int id) { return C.t[id]; };
   if (!tm.made) {
     for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
     tm.made = true;
   }
   float lad_ms = 0.f;
-  auto run_ladder = [&](int d, zc a, const Tens &in, const Tens &out) {
+  auto run_ladder = [&](int d, zc a, int in_id, int out_id) {
+    std::vector<Tens> in(nr), out(nr);
+    for (int r = 0; r < nr; ++r) { in[r] = V(r, in_id); out[r] = V(r, out_id); }
     CCLR_CUDA(cudaEventRecord(tm.ev[1], st));
     ladder(d, C, a, in, out);
     CCLR_CUDA(cudaEventRecord(tm.ev[2], st));
@@ -372,45 +391,64 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
   };
   CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
   if (dir > 0) {
-    ptr[0] = (void *)x1; ptr[1] = (void *)x2; ptr[2] = s1; ptr[3] = s2;
-    E.zero(V(2));
-    E.zero(V(3));
+    for (int r = 0; r < nr; ++r) {
+      ptr[r][0] = (void *)x1[r]; ptr[r][1] = (void *)x2[r]; ptr[r][2] = s1[r]; ptr[r][3] = s2[r];
+      E.zero(V(r, 2));
+      E.zero(V(r, 3));
+    }
     for (const Op &op : prog.ops) {
-      switch (op.kind) {
-        case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.in), op.mi, V(op.out), op.mo); break;
-        case OP_PERM: E.permute(op.alpha, V(op.in), op.mi, V(op.out), op.mo, true); break;
-        case OP_ZERO: E.zero(V(op.out)); break;
-        case OP_LADDER: run_ladder(+1, op.alpha, V(op.in), V(op.out)); break;
-        case OP_ANTISYM: antisym_apply(dt, o, v, +1, ptr[op.out], ptr[op.in], ptr[op.in2], ptr[op.in3], st); break;
+      if (op.kind == OP_LADDER) { run_ladder(+1, op.alpha, op.in, op.out); continue; }
+      for (int r = 0; r < nr; ++r) {
+        switch (op.kind) {
+          case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.in), op.mi, V(r, op.out), op.mo); break;
+          case OP_PERM: E.permute(op.alpha, V(r, op.in), op.mi, V(r, op.out), op.mo, true); break;
+          case OP_ZERO: E.zero(V(r, op.out)); break;
+          case OP_ANTISYM:
+            antisym_apply(dt, o, v, +1, ptr[r][op.out], ptr[r][op.in], ptr[r][op.in2], ptr[r][op.in3], st);
+            break;
+          case OP_PROJECT: antisym_project(dt, o, v, ptr[r][op.out], st); break;
+          default: break;
+        }
       }
     }
   } else {
     // bars: s1 <- y1 (x1 argument), s2 <- y2 / 4 (unique-amplitude weight), outputs to
     // x1-bar (s1 argument) and a temporary x2-bar projected onto antisymmetric tensors.
-    ptr[2] = (void *)x1;
-    ptr[3] = tv[3].p;
-    ptr[0] = s1;
-    ptr[1] = tv[1].p;
-    E.permute(zc(0.25), var_tens(3, dt, (void *)x2), "ijab", V(3), "ijab", false);
-    E.zero(V(0));
-    E.zero(V(1));
-    for (int k = 4; k < nv; ++k) E.zero(V(k));
+    for (int r = 0; r < nr; ++r) {
+      auto &tv = temps(dt, r);
+      ptr[r][2] = (void *)x1[r];
+      ptr[r][3] = tv[3].p;
+      ptr[r][0] = s1[r];
+      ptr[r][1] = tv[1].p;
+      E.permute(zc(0.25), var_tens(3, dt, (void *)x2[r]), "ijab", V(r, 3), "ijab", false);
+      E.zero(V(r, 0));
+      E.zero(V(r, 1));
+      for (int k = 4; k < nv; ++k) E.zero(V(r, k));
+    }
     for (auto it = prog.ops.rbegin(); it != prog.ops.rend(); ++it) {
       const Op &op = *it;
-      switch (op.kind) {
-        case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(op.out), op.mo, V(op.in), op.mi); break;
-        case OP_PERM: E.permute(op.alpha, V(op.out), op.mo, V(op.in), op.mi, true); break;
-        case OP_ZERO: E.zero(V(op.out)); break;
-        case OP_LADDER: run_ladder(-1, op.alpha, V(op.out), V(op.in)); break;
-        case OP_ANTISYM: antisym_apply(dt, o, v, -1, ptr[op.out], ptr[op.in], ptr[op.in2], ptr[op.in3], st); break;
+      if (op.kind == OP_LADDER) { run_ladder(-1, op.alpha, op.out, op.in); continue; }
+      for (int r = 0; r < nr; ++r) {
+        switch (op.kind) {
+          case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.out), op.mo, V(r, op.in), op.mi); break;
+          case OP_PERM: E.permute(op.alpha, V(r, op.out), op.mo, V(r, op.in), op.mi, true); break;
+          case OP_ZERO: E.zero(V(r, op.out)); break;
+          case OP_ANTISYM:
+            antisym_apply(dt, o, v, -1, ptr[r][op.out], ptr[r][op.in], ptr[r][op.in2], ptr[r][op.in3], st);
+            break;
+          case OP_PROJECT: antisym_project(dt, o, v, ptr[r][op.out], st); break;
+          default: break;
+        }
       }
     }
-    Tens out2 = var_tens(3, dt, s2);
-    Tens z2 = V(1);
-    E.permute(zc(1), z2, "ijab", out2, "ijab", false);
-    E.permute(zc(-1), z2, "ijab", out2, "jiab", true);
-    E.permute(zc(-1), z2, "ijab", out2, "ijba", true);
-    E.permute(zc(1), z2, "ijab", out2, "jiba", true);
+    for (int r = 0; r < nr; ++r) {
+      Tens out2 = var_tens(3, dt, s2[r]);
+      Tens z2 = V(r, 1);
+      E.permute(zc(1), z2, "ijab", out2, "ijab", false);
+      E.permute(zc(-1), z2, "ijab", out2, "jiab", true);
+      E.permute(zc(-1), z2, "ijab", out2, "ijba", true);
+      E.permute(zc(1), z2, "ijab", out2, "jiba", true);
+    }
   }
   CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
   CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
@@ -533,6 +571,9 @@ Program build_sigma_program(int o, int v, int naux) {
     a.in3 = Rijab;
     p.ops.push_back(a);
   }
+  // exact projection onto antisymmetric doubles: the identity on exact results, it keeps the
+  // rounding of the partial terms from leaving the antisymmetric subspace (self-adjoint)
+  p.ops.push_back(Op{OP_PROJECT, zc(1), -1, "", "", "", -1, S2});
   (void)PM;
   return p;
 }

@@ -26,7 +26,7 @@ struct CstSet {
   bool valid = false;
 };
 
-enum OpKind { OP_CONTRACT, OP_PERM, OP_ZERO, OP_LADDER, OP_ANTISYM };
+enum OpKind { OP_CONTRACT, OP_PERM, OP_ZERO, OP_LADDER, OP_ANTISYM, OP_PROJECT };
 
 struct Op {
   OpKind kind;
@@ -74,7 +74,7 @@ class Model {
   CstSet c128, c64;                 // intermediates at the current T
   DevBuf D1, D2;                    // preconditioner diagonal (real)
   Program prog;
-  std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision
+  std::vector<std::vector<DevBuf>> tmp128, tmp64;  // program temporaries per precision and RHS
   int prec = 0;
   DevBuf ladW;                      // ladder formation scratch (CUDA-core path)
   LadderTC ltc[2];                  // packed tensor-core ladder: [0] TF32, [1] 3xTF32
@@ -94,6 +94,9 @@ class Model {
 
   // sigma (dir = +1) or sigma^T (dir = -1) on device buffers of the given dtype.
   void apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2);
+  // the same for nr right-hand sides at once (the ladder's <ab||ef>~ is formed once for all)
+  void apply_batch(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
+                   void *const *s1, void *const *s2);
   // xi^B (or at other amplitudes), complex128 device buffers.
   void xi(const void *mub, const void *t1d, const void *t2d, void *xi1, void *xi2);
 
@@ -102,8 +105,8 @@ class Model {
   }
 
  private:
-  void ladder(int dir, const CstSet &C, zc alpha, const Tens &in, const Tens &out);
-  std::vector<DevBuf> &temps(int dt);
+  void ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &in, const std::vector<Tens> &out);
+  std::vector<DevBuf> &temps(int dt, int r);
   Tens var_tens(int id, int dt, void *p) const;
 };
 
