@@ -79,6 +79,23 @@ def ladder_peak(prec):
     return "alu", 1.25, "nominal FP64 rate"
 
 
+def reduce_max(x: float) -> float:
+    """Max over ranks (identity without a process group); NCCL needs a device tensor."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, units_per_rank: int, ms_max: float) -> float:
+    """Whole-job units/s for independent replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms_max / 1e3)
+
+
 class Clocks:
     """Sample SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
 
@@ -281,11 +298,8 @@ def run_cclr(args):
         torch.cuda.profiler.stop()
     ms = e0.elapsed_time(e1)
     launches = binding.cc_lr_launch_count() - n0
-    ms_t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = world * args.steps / (ms_max / 1e3)
+    ms_max = reduce_max(ms)
+    value = replica_throughput(world, args.steps, ms_max)
     clk = ck.summary()
 
     # end to end through the public API with host buffers (pinned)
@@ -301,10 +315,7 @@ def run_cclr(args):
         ctx.sigma_into(x1p, x2p, s1p, s2p)
     e1.record(stream)
     barrier()
-    ms_e = torch.tensor([e0.elapsed_time(e1)], device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_e, op=dist.ReduceOp.MAX)
-    e2e = world * args.steps / (float(ms_e.item()) / 1e3)
+    e2e = replica_throughput(world, args.steps, reduce_max(e0.elapsed_time(e1)))
     bytes_io = (x1p.numel() + x2p.numel()) * 16
 
     # batched: several right-hand sides share each formed <ab||ef>~ block
@@ -327,8 +338,8 @@ def run_cclr(args):
             lad_b.append(float(ctx.cc_lr_last_timings()[0]))
         e1.record(stream)
         barrier()
-        msb = e0.elapsed_time(e1) / reps
-        batched = {"nrhs": nb, "sigma_vectors_per_s": world * nb / (msb / 1e3), "ms_per_batch": msb,
+        msb = reduce_max(e0.elapsed_time(e1)) / reps
+        batched = {"nrhs": nb, "sigma_vectors_per_s": replica_throughput(world, nb, msb), "ms_per_batch": msb,
                    "ladder_ms_per_batch": sum(lad_b) / len(lad_b)}
         del xb1, xb2, sb1, sb2
 
