@@ -20,6 +20,12 @@ int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *er
  * GEMM, ms[1] = the corresponding TFLOP/s at 8 real flops per complex multiply-add. */
 int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms);
 
+/* Failure-detection self-test: launches one block that waits on an mbarrier phase that
+ * nothing completes, with a limit of timeout_us microseconds (globaltimer).  The wait gives
+ * up, raises the device error flag and returns; *flag receives the flag (1 expected) and the
+ * call returns CCLR_ETIMEOUT (5).  No fault, trap or hang is involved. */
+int cc_lr_selftest_timeout(int timeout_us, int *flag);
+
 #ifdef __cplusplus
 }
 #endif

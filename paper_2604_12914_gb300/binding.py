@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_launch_count": [],
         "cc_lr_selftest_gemm": [I, I, I, I, ctypes.c_uint, P],
         "cc_lr_bench_gemm": [I, I, I, I, I, P],
+        "cc_lr_selftest_timeout": [I, ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -243,6 +244,13 @@ def cc_lr_bench_gemm(M, N, K, mode, reps=5):
     out = np.zeros(2, dtype=np.float64)
     _check(load().cc_lr_bench_gemm(M, N, K, mode, reps, _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+def cc_lr_selftest_timeout(timeout_us=1000):
+    """(status, device flag) of the bounded-wait give-up self-test."""
+    flag = ctypes.c_int(0)
+    st = load().cc_lr_selftest_timeout(int(timeout_us), ctypes.byref(flag))
+    return st, flag.value
 
 
 def cc_lr_launch_count() -> int:

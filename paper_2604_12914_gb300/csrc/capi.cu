@@ -780,6 +780,18 @@ const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
 
 unsigned long long cc_lr_launch_count(void) { return cclr::launch_count(); }
 
+int cc_lr_selftest_timeout(int timeout_us, int *flag) {
+  if (timeout_us < 1 || timeout_us > 10000000 || !flag) return fail(CCLR_EINVAL, "bad selftest_timeout arguments");
+  int st = guarded([&] {
+    cudaStream_t s;
+    CCLR_CUDA(cudaStreamCreate(&s));
+    *flag = tc_selftest_timeout(timeout_us, s);
+    CCLR_CUDA(cudaStreamDestroy(s));
+  });
+  if (st != CCLR_OK) return st;
+  return *flag ? fail(CCLR_ETIMEOUT, "bounded device wait gave up (self-test)") : CCLR_OK;
+}
+
 int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
   if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || reps < 1 || !ms) return fail(CCLR_EINVAL, "bad bench_gemm arguments");
   return guarded([&] {

@@ -72,6 +72,30 @@ static bool group_view(const Tens &t, const std::string &modes, const std::strin
   return true;
 }
 
+// The same with up to two levels: index = outer * v.sout + inner * v.sin, inner < v.din.
+static bool group_view2(const Tens &t, const std::string &modes, const std::string &group, View2 &v) {
+  v = View2();
+  int64_t expect = -1, size = 1;
+  int levels = 0;
+  for (int g = (int)group.size() - 1; g >= 0; --g) {
+    int pos = mode_pos(modes, group[g]);
+    int64_t d = t.dim[pos], s = t.str[pos];
+    if (d == 1) continue;
+    if (expect < 0) {
+      v.sin = s;
+      levels = 1;
+    } else if (s != expect) {
+      if (levels == 2) return false;
+      v.din = size;
+      v.sout = s;
+      levels = 2;
+    }
+    expect = s * d;
+    size *= d;
+  }
+  return true;
+}
+
 static int64_t prod_dims(const Tens &t, const std::string &modes, const std::string &group) {
   int64_t p = 1;
   for (char c : group) p *= t.dim[mode_pos(modes, c)];
@@ -169,6 +193,15 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
   if (K == 0) return;
   const size_t es = dt_size(dt);
 
+  // complex64 on tensor cores: operands prepared straight from (two-level) strided views and
+  // the result written as interleaved complex pairs into C through its own views; an operand
+  // whose modes need more than two levels is first permuted into a contiguous temporary.
+  if (dt == C64 && tc_mode && nb <= 16 &&
+      (tc_force || ((double)M * N * K >= 3.0e7 && M >= 16 && K >= 8))) {
+    contract_tc(alpha, A, ma, B, mb, C, mc, bat, Mm, Nm, Km, nb, M, N, K);
+    return;
+  }
+
   GemmArgs g;
   g.M = M; g.N = N; g.K = K; g.batch = nb;
   g.alr = alpha.re; g.ali = alpha.im;
@@ -202,33 +235,6 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
       g.B = T.p; g.sBb = K * N; g.sBk = N; g.sBn = 1;
     }
   }
-  // complex64 on tensor cores: operands prepared from the strided views, result written as
-  // interleaved complex pairs straight into C when its N modes are contiguous.
-  if (dt == C64 && tc_mode && nb <= 16 &&
-      (tc_force || ((double)M * N * K >= 3.0e7 && M >= 16 && K >= 8))) {
-    const int seg = tc_mode == 2 ? 3 : 1;
-    const int64_t ld = 2 * tc_kpad(K) * seg;
-    float *Ao = (float *)ws(3, (size_t)M * ld * 4);
-    float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
-    int64_t c0, c1, c2, zz;
-    bool direct = group_view(C, mc, bat, zz, c0) && group_view(C, mc, Mm, zz, c1) &&
-                  group_view(C, mc, Nm, zz, c2) && (N == 1 || c2 == 1);
-    Tens T;
-    if (!direct) {
-      std::string order = bat + Mm + Nm;
-      T = contiguous_like(ws(2, nb * M * N * es), dt, C, mc, order);
-      c0 = M * N; c1 = N; c2 = 1;
-    }
-    for (int64_t b = 0; b < nb; ++b) {
-      tc_prep_a((const char *)g.A + b * g.sAb * es, g.sAm, g.sAk, M, K, seg, Ao, ld, st);
-      tc_prep_b((const char *)g.B + b * g.sBb * es, g.sBk, g.sBn, K, N, seg, Bo, ld, st);
-      float *Cp = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
-      tc_gemm_seg(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, 2 * c1, alpha, direct, st);
-      ++tc_calls;
-    }
-    if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);
-    return;
-  }
   // C as [batch][M][N]
   int64_t s0, s1, s2, z;
   bool ok = group_view(C, mc, bat, z, s0) && group_view(C, mc, Mm, z, s1) &&
@@ -243,6 +249,47 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
     launch_gemm(g, dt, st);
     permute(zc(1.0), T, order, C, mc, true);
   }
+}
+
+void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const Tens &B,
+                         const std::string &mb, const Tens &C, const std::string &mc,
+                         const std::string &bat, const std::string &Mm, const std::string &Nm,
+                         const std::string &Km, int64_t nb, int64_t M, int64_t N, int64_t K) {
+  const size_t es = dt_size(C64);
+  int64_t a0, b0, c0, z;
+  View2 am, ak, bk, bn, cm, cn;
+  const void *Ap = A.p, *Bp = B.p;
+  if (!(group_view(A, ma, bat, z, a0) && group_view2(A, ma, Mm, am) && group_view2(A, ma, Km, ak))) {
+    std::string order = bat + Mm + Km;
+    Tens T = contiguous_like(ws(0, nb * M * K * es), C64, A, ma, order);
+    permute(zc(1.0), A, ma, T, order, false);
+    Ap = T.p; a0 = M * K; am = view1(K); ak = view1(1);
+  }
+  if (!(group_view(B, mb, bat, z, b0) && group_view2(B, mb, Km, bk) && group_view2(B, mb, Nm, bn))) {
+    std::string order = bat + Km + Nm;
+    Tens T = contiguous_like(ws(1, nb * K * N * es), C64, B, mb, order);
+    permute(zc(1.0), B, mb, T, order, false);
+    Bp = T.p; b0 = K * N; bk = view1(N); bn = view1(1);
+  }
+  const bool direct = group_view(C, mc, bat, z, c0) && group_view2(C, mc, Mm, cm) && group_view2(C, mc, Nm, cn);
+  Tens T;
+  if (!direct) {
+    std::string order = bat + Mm + Nm;
+    T = contiguous_like(ws(2, nb * M * N * es), C64, C, mc, order);
+    c0 = M * N; cm = view1(N); cn = view1(1);
+  }
+  const int seg = tc_mode == 2 ? 3 : 1;
+  const int64_t ld = 2 * tc_kpad(K) * seg;
+  float *Ao = (float *)ws(3, (size_t)M * ld * 4);
+  float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
+  for (int64_t b = 0; b < nb; ++b) {
+    tc_prep_a2((const char *)Ap + b * a0 * es, am, ak, M, K, seg, Ao, ld, st);
+    tc_prep_b2((const char *)Bp + b * b0 * es, bk, bn, K, N, seg, Bo, ld, st);
+    float *Cp = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
+    tc_gemm_seg_v(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, cm, cn, alpha, direct, st);
+    ++tc_calls;
+  }
+  if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);
 }
 
 }  // namespace cclr

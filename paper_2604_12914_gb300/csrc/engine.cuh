@@ -43,6 +43,10 @@ class Engine {
   // mode must appear in exactly two operands or in all three).
   void contract(zc alpha, const Tens &A, const std::string &ma, const Tens &B,
                 const std::string &mb, const Tens &C, const std::string &mc);
+  // the complex64 tensor-core branch of contract (modes already classified)
+  void contract_tc(zc alpha, const Tens &A, const std::string &ma, const Tens &B, const std::string &mb,
+                   const Tens &C, const std::string &mc, const std::string &bat, const std::string &Mm,
+                   const std::string &Nm, const std::string &Km, int64_t nb, int64_t M, int64_t N, int64_t K);
   // out[mo] (+)= alpha * in[mi]  (same mode set; dtypes may differ -> conversion).
   void permute(zc alpha, const Tens &in, const std::string &mi, const Tens &out,
                const std::string &mo, bool acc);

@@ -22,7 +22,7 @@ struct TcParams {
   int nMt, nNt, band;   // tile counts; M tiles per raster band (N varies fastest inside a band)
   int kb_per_split;     // K blocks per split (grid.y splits of K, atomically summed)
   float *C;
-  long long ldc;
+  View2 rv, cv;         // C rows and complex columns
   float ar, ai;
   int accumulate;       // add to C (always true when split)
   int atomic;           // split-K: combine partial tiles with atomicAdd
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (ok && nk > 0) {
     const int row = m0 + warp * 32 + lane;
-    float *crow = p.C + (long long)row * p.ldc;
+    float *crow = p.C + 2 * (row < p.M ? v2off(p.rv, row) : 0);
     for (int c0 = 0; c0 < BN; c0 += 16) {
       uint32_t r[16];
       tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
@@ -215,18 +215,19 @@ __global__ void __launch_bounds__(128, 1)
         for (int j = 0; j < 16; j += 2) {
           const int n = n0 + c0 + j;
           if (n < p.N) {
+            float *dst = crow + 2 * v2off(p.cv, n >> 1);
             const float re = __uint_as_float(r[j]), im = __uint_as_float(r[j + 1]);
             float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
             if (p.atomic) {
-              atomicAdd(crow + n, vr);
-              atomicAdd(crow + n + 1, vi);
+              atomicAdd(dst, vr);
+              atomicAdd(dst + 1, vi);
             } else {
               if (p.accumulate) {
-                vr += crow[n];
-                vi += crow[n + 1];
+                vr += dst[0];
+                vi += dst[1];
               }
-              crow[n] = vr;
-              crow[n + 1] = vi;
+              dst[0] = vr;
+              dst[1] = vi;
             }
           }
         }
@@ -245,6 +246,26 @@ __global__ void __launch_bounds__(128, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols) : "memory");
 }
 
+// A wait that nothing completes, bounded by timeout_ns (self-test of the give-up path).
+__global__ void wait_never_kernel(unsigned long long timeout_ns, int *err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = gtime();
+    while (!mbar_try(su32(&bar), 0)) {
+      if (gtime() - t0 > timeout_ns) {
+        atomicExch(err, 1);
+        break;
+      }
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------- operand preparation ----------------
 __device__ __forceinline__ float tf32_hi(float x) {
   uint32_t u = __float_as_uint(x);
@@ -252,15 +273,15 @@ __device__ __forceinline__ float tf32_hi(float x) {
   return __uint_as_float(u);
 }
 
-__global__ void prep_a_kernel(const float2 *A, int64_t sam, int64_t sak, int64_t M, int64_t K,
+__global__ void prep_a_kernel(const float2 *A, View2 mv, View2 kv, int64_t M, int64_t K,
                               int64_t Kp, int seg, float *dst, int64_t ldd) {
   const int64_t total = M * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t m, k;
-    if (sak == 1 || sam != 1) { k = e % Kp; m = e / Kp; } else { m = e % M; k = e / M; }
+    if (kv.sin == 1 || mv.sin != 1) { k = e % Kp; m = e / Kp; } else { m = e % M; k = e / M; }
     float2 v = make_float2(0.f, 0.f);
-    if (k < K) v = A[m * sam + k * sak];
+    if (k < K) v = A[v2off(mv, m) + v2off(kv, k)];
     float *row = dst + m * ldd;
     if (seg == 1) {
       row[2 * k] = v.x;
@@ -277,15 +298,15 @@ __global__ void prep_a_kernel(const float2 *A, int64_t sam, int64_t sak, int64_t
   }
 }
 
-__global__ void prep_b_kernel(const float2 *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N,
+__global__ void prep_b_kernel(const float2 *B, View2 kv, View2 nv, int64_t K, int64_t N,
                               int64_t Kp, int seg, float *dst, int64_t ldd) {
   const int64_t total = N * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     int64_t n, k;
-    if (sbk == 1 || sbn != 1) { k = e % Kp; n = e / Kp; } else { n = e % N; k = e / N; }
+    if (kv.sin == 1 || nv.sin != 1) { k = e % Kp; n = e / Kp; } else { n = e % N; k = e / N; }
     float2 v = make_float2(0.f, 0.f);
-    if (k < K) v = B[k * sbk + n * sbn];
+    if (k < K) v = B[v2off(kv, k) + v2off(nv, n)];
     float *r0 = dst + (2 * n) * ldd, *r1 = dst + (2 * n + 1) * ldd;
     if (seg == 1) {
       r0[2 * k] = v.x;
@@ -305,7 +326,7 @@ __global__ void prep_b_kernel(const float2 *B, int64_t sbk, int64_t sbn, int64_t
 
 // Transposing preparation: the source is contiguous along m (A) or n (B) and strided along
 // k; 32 x 32 tiles through shared memory so that reads and writes are both coalesced.
-__global__ void prep_tiled_kernel(const float2 *src, int64_t s_mn, int64_t s_k, int64_t MN, int64_t K,
+__global__ void prep_tiled_kernel(const float2 *src, View2 mnv, View2 kv, int64_t MN, int64_t K,
                                   int64_t Kp, int seg, int isB, float *dst, int64_t ldd) {
   __shared__ float2 tile[32][33];
   const int64_t tmn = (MN + 31) / 32, tk = (Kp + 31) / 32;
@@ -314,7 +335,7 @@ __global__ void prep_tiled_kernel(const float2 *src, int64_t s_mn, int64_t s_k, 
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
       const int64_t mn = mn0 + threadIdx.x, k = k0 + r;
       float2 v = make_float2(0.f, 0.f);
-      if (mn < MN && k < K) v = src[mn * s_mn + k * s_k];
+      if (mn < MN && k < K) v = src[v2off(mnv, mn) + v2off(kv, k)];
       tile[r][threadIdx.x] = v;
     }
     __syncthreads();
@@ -351,7 +372,9 @@ int *g_err = nullptr;
 std::once_flag g_once;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
-void init_once() {
+std::once_flag g_enc_once;
+
+void fetch_encoder() {
   // the driver entry point is fetched through the runtime, so the library does not link
   // against libcuda itself (it still loads on machines without a driver)
   cudaDriverEntryPointQueryResult q;
@@ -359,6 +382,10 @@ void init_once() {
   CCLR_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
   if (q != cudaDriverEntryPointSuccess || !fn) throw Error(4, "cuTensorMapEncodeTiled not available");
   g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+}
+
+void init_once() {
+  std::call_once(g_enc_once, fetch_encoder);
   CCLR_CUDA(cudaMalloc(&g_err, sizeof(int)));
   CCLR_CUDA(cudaMemset(g_err, 0, sizeof(int)));
   CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
@@ -398,44 +425,49 @@ unsigned grid1d(int64_t n) {
 
 }  // namespace
 
-void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, float *dst,
-               int64_t ldd, cudaStream_t st) {
+void tc_prep_a2(const void *A, View2 mv, View2 kv, int64_t M, int64_t K, int seg, float *dst, int64_t ldd,
+                cudaStream_t st) {
   const int64_t Kp = tc_kpad(K);
   CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_a: row too short");
-  if (sak != 1 && sam == 1 && M >= 8) {
+  if (kv.sin != 1 && mv.sin == 1 && M >= 8) {
     const int64_t nt = ((M + 31) / 32) * ((Kp + 31) / 32);
     prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
-        (const float2 *)A, sam, sak, M, K, Kp, seg, 0, dst, ldd);
-    count_launch();
-    CCLR_CUDA(cudaGetLastError());
-    return;
+        (const float2 *)A, mv, kv, M, K, Kp, seg, 0, dst, ldd);
+  } else {
+    prep_a_kernel<<<grid1d(M * Kp), 256, 0, st>>>((const float2 *)A, mv, kv, M, K, Kp, seg, dst, ldd);
   }
-  prep_a_kernel<<<grid1d(M * Kp), 256, 0, st>>>((const float2 *)A, sam, sak, M, K, Kp, seg, dst, ldd);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
+}
+
+void tc_prep_b2(const void *B, View2 kv, View2 nv, int64_t K, int64_t N, int seg, float *dst, int64_t ldd,
+                cudaStream_t st) {
+  const int64_t Kp = tc_kpad(K);
+  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_b: row too short");
+  if (kv.sin != 1 && nv.sin == 1 && N >= 8) {
+    const int64_t nt = ((N + 31) / 32) * ((Kp + 31) / 32);
+    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
+        (const float2 *)B, nv, kv, N, K, Kp, seg, 1, dst, ldd);
+  } else {
+    prep_b_kernel<<<grid1d(N * Kp), 256, 0, st>>>((const float2 *)B, kv, nv, K, N, Kp, seg, dst, ldd);
+  }
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, float *dst,
+               int64_t ldd, cudaStream_t st) {
+  tc_prep_a2(A, view1(sam), view1(sak), M, K, seg, dst, ldd, st);
 }
 
 void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, float *dst,
                int64_t ldd, cudaStream_t st) {
-  const int64_t Kp = tc_kpad(K);
-  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_b: row too short");
-  if (sbk != 1 && sbn == 1 && N >= 8) {
-    const int64_t nt = ((N + 31) / 32) * ((Kp + 31) / 32);
-    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
-        (const float2 *)B, sbn, sbk, N, K, Kp, seg, 1, dst, ldd);
-    count_launch();
-    CCLR_CUDA(cudaGetLastError());
-    return;
-  }
-  prep_b_kernel<<<grid1d(N * Kp), 256, 0, st>>>((const float2 *)B, sbk, sbn, K, N, Kp, seg, dst, ldd);
-  count_launch();
-  CCLR_CUDA(cudaGetLastError());
+  tc_prep_b2(B, view1(sbk), view1(sbn), K, N, seg, dst, ldd, st);
 }
 
-static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-                         int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
-                         int max_kb_per_split, cudaStream_t st) {
-  std::call_once(g_once, init_once);
+static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+                         int max_kb_per_split, int *err, cudaStream_t st) {
   if (M <= 0 || Nreal <= 0) return;
   CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
   CCLR_REQUIRE(lda % 4 == 0 && ldb % 4 == 0, "tc_gemm: leading dimensions must be multiples of 16 bytes");
@@ -466,14 +498,18 @@ static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ld
   p.kb_per_split = (nk + splits - 1) / splits;
   splits = (nk + p.kb_per_split - 1) / p.kb_per_split;
   p.C = C;
-  p.ldc = ldc_floats;
+  p.rv = rv;
+  p.cv = cv;
   p.ar = (float)alpha.re;
   p.ai = (float)alpha.im;
   p.atomic = splits > 1 ? 1 : 0;
   p.accumulate = (accumulate || splits > 1) ? 1 : 0;
-  p.err = g_err;
-  if (splits > 1 && !accumulate)
-    CCLR_CUDA(cudaMemset2DAsync(C, (size_t)ldc_floats * 4, 0, (size_t)Nreal * 4, (size_t)M, st));
+  p.err = err;
+  if (splits > 1 && !accumulate) {
+    CCLR_REQUIRE(rv.din == TC_ONE_LEVEL && cv.din == TC_ONE_LEVEL && cv.sin == 1,
+                 "tc_gemm: split K without accumulation needs a plain C layout");
+    CCLR_CUDA(cudaMemset2DAsync(C, (size_t)rv.sin * 8, 0, (size_t)Nreal * 4, (size_t)M, st));
+  }
   const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (2 * STAGES + 1) * 8 + 16;
   CCLR_REQUIRE(tiles < (1ll << 31) && splits <= 65535, "tc_gemm: grid too large");
   dim3 grid((unsigned)tiles, (unsigned)splits);
@@ -482,23 +518,44 @@ static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ld
   CCLR_CUDA(cudaGetLastError());
 }
 
+static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+                         int max_kb_per_split, cudaStream_t st) {
+  std::call_once(g_once, init_once);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kreal, C, rv, cv, alpha, accumulate, max_kb_per_split, g_err, st);
+}
+
 void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
              int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
-  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kreal, C, ldc_floats, alpha, accumulate, 0, st);
+  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kreal, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, 0, st);
 }
 
 // The tensor-core accumulation error was measured to grow linearly with the chain length,
 // so the split passes keep every accumulator to at most 64 K blocks (2048 real K) and sum
 // the partial tiles in FP32.
+void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                   int64_t Kseg, int seg, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+                   cudaStream_t st) {
+  if (seg == 1) {
+    tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, accumulate, 0, st);
+    return;
+  }
+  tc_gemm_impl(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, rv, cv, alpha, accumulate, 64, st);
+  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, true, 64, st);
+}
+
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                  int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
                  cudaStream_t st) {
-  if (seg == 1) {
-    tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, accumulate, 0, st);
-    return;
-  }
-  tc_gemm_impl(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, ldc_floats, alpha, accumulate, 64, st);
-  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, ldc_floats, alpha, true, 64, st);
+  tc_gemm_seg_v(A, lda, B, ldb, M, Nreal, Kseg, seg, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, st);
+}
+
+int tc_selftest_timeout(int timeout_us, cudaStream_t st) {
+  std::call_once(g_once, init_once);
+  wait_never_kernel<<<1, 32, 0, st>>>((unsigned long long)timeout_us * 1000ull, g_err);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+  return tc_error(st);
 }
 
 int tc_error(cudaStream_t st) {

@@ -14,6 +14,26 @@
 
 namespace cclr {
 
+// Two-level strided index view: offset(i) = (i / din) * sout + (i % din) * sin (elements).
+// One level: din = TC_ONE_LEVEL, sout = 0.
+constexpr int64_t TC_ONE_LEVEL = (int64_t)1 << 62;
+struct View2 {
+  int64_t din = TC_ONE_LEVEL, sout = 0, sin = 1;
+};
+__host__ __device__ __forceinline__ int64_t v2off(const View2 &v, int64_t i) {
+  if (v.din == TC_ONE_LEVEL) return i * v.sin;
+  if (i < 0x7fffffff && v.din < 0x7fffffff) {  // 32-bit division where it suffices
+    const uint32_t q = (uint32_t)i / (uint32_t)v.din, r = (uint32_t)i - q * (uint32_t)v.din;
+    return (int64_t)q * v.sout + (int64_t)r * v.sin;
+  }
+  return (i / v.din) * v.sout + (i % v.din) * v.sin;
+}
+inline View2 view1(int64_t stride) {
+  View2 v;
+  v.sin = stride;
+  return v;
+}
+
 // Complex K padded so that every operand row is a whole number of 16-byte units.
 inline int64_t tc_kpad(int64_t K) { return (K + 1) / 2 * 2; }
 
@@ -22,6 +42,11 @@ void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, in
                int64_t ldd, cudaStream_t st);
 void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, float *dst,
                int64_t ldd, cudaStream_t st);
+// the same reading A(m, k) at v2off(mv, m) + v2off(kv, k) (B(k, n) likewise)
+void tc_prep_a2(const void *A, View2 mv, View2 kv, int64_t M, int64_t K, int seg, float *dst, int64_t ldd,
+                cudaStream_t st);
+void tc_prep_b2(const void *B, View2 kv, View2 nv, int64_t K, int64_t N, int seg, float *dst, int64_t ldd,
+                cudaStream_t st);
 
 // Real tensor-core GEMM; C is written as complex pairs: C[m][n..n+1] (+)= alpha * D[m][n..n+1]
 // for even n.  Nreal must be even; lda/ldb multiples of 4 floats; A, B 16-byte aligned.
@@ -35,9 +60,17 @@ void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                  int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
                  cudaStream_t st);
+// the same with C addressed through views of its rows and its complex columns
+// (complex element (m, n) at C + 2 * (v2off(rv, m) + v2off(cv, n)) floats)
+void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                   int64_t Kseg, int seg, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+                   cudaStream_t st);
 
 // Reads (and clears) the device-side error flag of the tensor-core kernels: 0 = fine,
 // 1 = a bounded wait gave up.
 int tc_error(cudaStream_t st);
+
+// Runs the bounded-wait give-up path once (a wait nothing completes); returns the flag.
+int tc_selftest_timeout(int timeout_us, cudaStream_t st);
 
 }  // namespace cclr

@@ -241,3 +241,21 @@ def test_autograd_sigma_function():
     # PyTorch reports 2 dL/dz* = conj(dL/dz) for a real L: here conj((W A)_singles)
     assert np.abs(z1.grad.cpu().numpy() - np.conj(ref1)).max() < 1e-9 * np.abs(ref1).max()
     ctx.close()
+
+
+def test_bounded_wait_gives_up_and_context_survives():
+    """A device wait that nothing completes ends after its limit with CCLR_ETIMEOUT; the
+    CUDA context stays usable (a sigma afterwards still matches the oracle)."""
+    from paper_2604_12914_gb300 import binding
+    st, flag = binding.cc_lr_selftest_timeout(2000)
+    assert flag == 1 and st == binding.CCLR_ETIMEOUT
+    assert "gave up" in binding.load().cc_lr_last_error().decode()
+    o, v, naux, seed, scale, t1s = CASES[1]
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx = gpu_context(s, t1=t1, t2=t2, prec="tf32")
+    x1, x2 = random_amplitudes(o, v, seed=3)
+    g1, g2 = ctx.cc_lr_sigma(x1, x2)
+    r1, r2 = oracle_sigma(s, t1, t2, x1, x2)
+    assert rel_err(g1, g2, r1, r2) < 3e-3
+    ctx.close()
