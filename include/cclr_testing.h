@@ -20,6 +20,35 @@ int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *er
  * GEMM, ms[1] = the corresponding TFLOP/s at 8 real flops per complex multiply-add. */
 int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms);
 
+/* Size in bytes of the fixed device array that cc_lr_selftest_gemm_noalloc works in (32 MiB,
+ * one copy per device). */
+#define CCLR_SELFTEST_NOALLOC_SCRATCH_BYTES 33554432ull
+
+/* cc_lr_selftest_gemm without any device allocation.  The paper has no counterpart: this
+ * entry point exists for host programs that cannot let a library call cudaMalloc or cudaFree
+ * -- typically because they hand nearly all device memory to their own caching pool at start-up
+ * and account for every byte through it, so a stray cudaMalloc fails or escapes the pool, and
+ * cudaFree would make the whole device wait.  It computes the same products on the same
+ * seeded data and writes the same err[0] (tcgen05 tensor cores, mode 1 TF32 or 2 3xTF32) and
+ * err[1] (FP32 CUDA cores), both relative to the FP64 result.
+ *   Memory: every buffer (inputs in FP64 and complex64, the three products, the staged
+ *   tensor-core operands and the bounded-wait flag) lives in one file-scope device array of
+ *   CCLR_SELFTEST_NOALLOC_SCRATCH_BYTES; sizes that do not fit return CCLR_EINVAL (1) and a
+ *   message naming the bytes needed (cc_lr_last_error).  About 24(MK + KN) + 32MN +
+ *   8(M + 2N)(K + 1)s bytes are needed, s = 1 for TF32 and 3 for 3xTF32; M = N = K = 384
+ *   fits with 3xTF32.  Nothing is allocated: no cudaMalloc, no cudaFree, no allocating
+ *   library routine; host staging uses fixed stack buffers.
+ *   Set-up: the first call on each device (with that device current) looks the array up with
+ *   cudaGetSymbolAddress and prepares the tensor-core kernel; make that first call before
+ *   any stream capture begins.
+ *   Sharing: all calls on a device use the same array, and each call clears what must start
+ *   at zero (the flag and the products) itself.  Calls that overlap on the GPU -- two host
+ *   threads calling at once on one device -- race on the array and give wrong results;
+ *   callers must serialise them.  The call is synchronous (it runs on the calling thread's
+ *   per-thread default stream and waits for it).
+ * Returns 0 on success, else a cclr_status code. */
+int cc_lr_selftest_gemm_noalloc(int M, int N, int K, int mode, unsigned seed, double *err);
+
 /* Failure-detection self-test: launches one block that waits on an mbarrier phase that
  * nothing completes, with a limit of timeout_us microseconds (globaltimer).  The wait gives
  * up, raises the device error flag and returns; *flag receives the flag (1 expected) and the

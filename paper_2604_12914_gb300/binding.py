@@ -70,6 +70,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_last_error": [],
         "cc_lr_launch_count": [],
         "cc_lr_selftest_gemm": [I, I, I, I, ctypes.c_uint, P],
+        "cc_lr_selftest_gemm_noalloc": [I, I, I, I, ctypes.c_uint, P],
         "cc_lr_bench_gemm": [I, I, I, I, I, P],
         "cc_lr_selftest_timeout": [I, ctypes.POINTER(ctypes.c_int)],
     }
@@ -236,6 +237,13 @@ def cc_lr_selftest_gemm(M, N, K, mode, seed=1):
     """(tensor-core error, FP32 CUDA-core error) of a random complex64 GEMM vs FP64."""
     err = np.zeros(2, dtype=np.float64)
     _check(load().cc_lr_selftest_gemm(M, N, K, mode, seed, _ptr(err)))
+    return float(err[0]), float(err[1])
+
+
+def cc_lr_selftest_gemm_noalloc(M, N, K, mode, seed=1):
+    """cc_lr_selftest_gemm computed in the library's fixed device array (no allocation)."""
+    err = np.zeros(2, dtype=np.float64)
+    _check(load().cc_lr_selftest_gemm_noalloc(M, N, K, mode, seed, _ptr(err)))
     return float(err[0]), float(err[1])
 
 

@@ -503,6 +503,16 @@ template <typename F> int guarded(F &&f) {
   }
 }
 
+}  // namespace
+
+namespace cclr {
+// Records msg as the thread's last error (cc_lr_last_error) and returns status; for entry
+// points defined in other translation units.
+int record_error(int status, const std::string &msg) { return fail(status, msg); }
+}  // namespace cclr
+
+namespace {
+
 // cudaMemcpyDefault: the direction follows from the pointers (unified addressing), so host
 // and device arrays are both accepted whatever device_ptrs said at init.
 void to_dev(cclr_ctx *c, const double *src, void *dst, size_t bytes) {

@@ -550,6 +550,24 @@ void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64
   tc_gemm_seg_v(A, lda, B, ldb, M, Nreal, Kseg, seg, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, st);
 }
 
+void tc_setup_device_flagged() {
+  std::call_once(g_enc_once, fetch_encoder);
+  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+}
+
+void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
+                         int *err, cudaStream_t st) {
+  CCLR_REQUIRE(g_encode != nullptr, "tc_gemm_seg_flagged: tc_setup_device_flagged was not called");
+  const View2 rv = view1(ldc_floats / 2), cv = view1(1);
+  if (seg == 1) {
+    tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, accumulate, 0, err, st);
+    return;
+  }
+  tc_gemm_core(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, rv, cv, alpha, accumulate, 64, err, st);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, true, 64, err, st);
+}
+
 int tc_selftest_timeout(int timeout_us, cudaStream_t st) {
   std::call_once(g_once, init_once);
   wait_never_kernel<<<1, 32, 0, st>>>((unsigned long long)timeout_us * 1000ull, g_err);

@@ -60,6 +60,14 @@ void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                  int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
                  cudaStream_t st);
+// The same GEMM for callers that hold their own device error flag (it must start at zero;
+// a bounded wait that gives up sets it to 1).  Neither function allocates device memory:
+// tc_setup_device_flagged fetches the tensor-map encoder and raises the kernel's dynamic
+// shared-memory limit on the current device, and must be called once per device first.
+void tc_setup_device_flagged();
+void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
+                         int *err, cudaStream_t st);
 // the same with C addressed through views of its rows and its complex columns
 // (complex element (m, n) at C + 2 * (v2off(rv, m) + v2off(cv, n)) floats)
 void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,

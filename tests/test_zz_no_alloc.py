@@ -1,0 +1,45 @@
+"""cc_lr_selftest_gemm_noalloc: the tensor-core GEMM self-test run inside the library's fixed
+device array, with no device allocation, against the allocating cc_lr_selftest_gemm.
+
+Both compute the same products from the same seeded inputs; the FP32 CUDA-core products are
+deterministic and must agree to the last bit, the tensor-core ones (split-K passes add
+partial tiles with atomics) within the tolerance the tensor-core self-test uses.  The
+entry point is called twice in a row, so the second call checks that the shared array is
+cleared where it must be.  The file is named to be collected last: the first call on the
+device does the set-up, and it must work both in a fresh process and after every other test.
+"""
+import pytest
+
+from paper_2604_12914_gb300 import binding
+
+
+def _tol(mode, K):
+    # the tolerances of the tensor-core GEMM self-test in test_gpu_parity.py
+    return 4e-3 if mode == 1 else 1e-8 * K + 2e-6
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("M,N,K,mode", [(200, 136, 300, 1), (200, 136, 300, 2), (384, 384, 384, 2),
+                                        (37, 5, 900, 2)])
+def test_noalloc_matches_allocating_selftest(M, N, K, mode):
+    tol = _tol(mode, K)
+    # the no-allocation call comes first, so that in a fresh process it does its own set-up
+    # before any other tensor-core work has run
+    first = binding.cc_lr_selftest_gemm_noalloc(M, N, K, mode, seed=7)
+    ref_tc, ref_fp32 = binding.cc_lr_selftest_gemm(M, N, K, mode, seed=7)
+    assert 0 <= ref_tc < tol
+    second = binding.cc_lr_selftest_gemm_noalloc(M, N, K, mode, seed=7)
+    for call, (e_tc, e_fp32) in enumerate((first, second)):
+        print(f"call {call}: M={M} N={N} K={K} mode={mode}: tc {e_tc:.3e} (allocating {ref_tc:.3e}) "
+              f"fp32 {e_fp32:.3e} (allocating {ref_fp32:.3e})")
+        assert 0 <= e_tc < tol
+        assert abs(e_tc - ref_tc) <= tol
+        assert e_fp32 == ref_fp32
+
+
+def test_noalloc_rejects_sizes_beyond_the_array():
+    """Checked before any device call, so it runs without a GPU as well."""
+    with pytest.raises(RuntimeError, match="bytes of scratch"):
+        binding.cc_lr_selftest_gemm_noalloc(512, 512, 512, 2)
+    with pytest.raises(RuntimeError, match="bytes of scratch"):
+        binding.cc_lr_selftest_gemm_noalloc(1 << 30, 1 << 30, 1 << 30, 1)
