@@ -127,8 +127,10 @@ cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
  * GMRES with the diagonal preconditioner (default; subspace = restart length),
  * method 0 = DIIS extrapolation of preconditioned Jacobi steps (subspace ignored; the
  * calls' diis_depth applies).  In the mixed modes either method solves the corrections
- * of the FP64-residual iterative refinement. */
-cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace);
+ * of the FP64-residual iterative refinement.  max_iterations bounds the sigma products of
+ * each linear solve (default 300; 0 keeps the current value); a solve that reaches it
+ * returns CCLR_ENOCONV with its best iterate. */
+cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace, int max_iterations);
 
 /* Device-side timing (CUDA events on the context's stream) of the last sigma or
  * sigma^T vector, in milliseconds: [0] particle-particle ladder (formation of <ab|ef>~

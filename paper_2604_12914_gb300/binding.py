@@ -223,9 +223,9 @@ class Context:
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         _check(load().cc_lr_set_precision(self._h, p))
 
-    def cc_lr_set_solver(self, method="gmres", subspace=30):
+    def cc_lr_set_solver(self, method="gmres", subspace=30, max_iterations=0):
         m = {"gmres": 1, "diis": 0}[method] if isinstance(method, str) else int(method)
-        _check(load().cc_lr_set_solver(self._h, m, int(subspace)))
+        _check(load().cc_lr_set_solver(self._h, m, int(subspace), int(max_iterations)))
 
     def cc_lr_last_timings(self):
         out = np.zeros(3, dtype=np.float64)

@@ -182,6 +182,7 @@ struct cclr_ctx {
   // Krylov method of the linear solves: 1 = restarted GMRES (default), 0 = DIIS.
   int method = 1;
   int krylov = 30;
+  int maxit = 300;  // iterations per linear solve, all precisions together
 
   double solve_diis(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
                     int *its, bool warm = false) {
@@ -404,7 +405,7 @@ struct cclr_ctx {
     eta0(b.b.p);
     scal(zd(-1), b.b.p);
     int its = 0;
-    double rel = solve(-1, 0.0, b.b.p, lam.b.p, tol, depth, 200, &its);
+    double rel = solve(-1, 0.0, b.b.p, lam.b.p, tol, depth, maxit, &its);
     if (stats) {
       stats->iterations += its;
       stats->time_lambda_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -636,7 +637,7 @@ cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int d
     c->scal(zd(-1), b.b.p);
     int its = 0;
     int calls0 = c->sigma_calls;
-    rel = c->solve(+1, omega, b.b.p, x.b.p, tol, diis_depth, 300, &its);
+    rel = c->solve(+1, omega, b.b.p, x.b.p, tol, diis_depth, c->maxit, &its);
     from_dev(c, x.p1(), x1, (size_t)c->n1 * 16);
     from_dev(c, x.p2(c->n1), x2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
@@ -691,7 +692,7 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
           AVec &x = X[(size_t)a * 2 + s];
           c->alloc_vec(x);
           int its = 0;
-          double rel = c->solve(+1, s == 0 ? om : -om, b.b.p, x.b.p, tol, diis_depth, 300, &its);
+          double rel = c->solve(+1, s == 0 ? om : -om, b.b.p, x.b.p, tol, diis_depth, c->maxit, &its);
           loc.iterations += its;
           loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
           if (!(rel < tol)) loc.converged = 0;
@@ -750,11 +751,12 @@ cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
   });
 }
 
-cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace) {
-  if (!c || (method != 0 && method != 1) || subspace < 0 || subspace > 100)
+cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace, int max_iterations) {
+  if (!c || (method != 0 && method != 1) || subspace < 0 || subspace > 100 || max_iterations < 0)
     return (cclr_status)fail(CCLR_EINVAL, "bad solver arguments");
   c->method = method;
   if (subspace >= 2) c->krylov = subspace;
+  if (max_iterations > 0) c->maxit = max_iterations;
   return CCLR_OK;
 }
 

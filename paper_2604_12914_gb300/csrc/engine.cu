@@ -2,6 +2,8 @@
 // views each operand as a strided batched matrix when its modes merge, and permutes it
 // into a contiguous scratch layout otherwise.
 #include <atomic>
+#include <cstdio>
+#include <cstdlib>
 
 #include "engine.cuh"
 #include "tc_gemm.cuh"
@@ -117,6 +119,17 @@ static Tens contiguous_like(void *p, int dt, const Tens &src, const std::string 
   return t;
 }
 
+// CCLR_TRACE=1 prints one line per contraction (modes, sizes, path) to stderr.
+static bool trace_on() {
+  static const bool t = std::getenv("CCLR_TRACE") && std::getenv("CCLR_TRACE")[0] == '1';
+  return t;
+}
+
+static std::string vstr(const View2 &v) {
+  if (v.din == TC_ONE_LEVEL) return std::to_string(v.sin);
+  return std::to_string(v.sout) + "/" + std::to_string(v.din) + "x" + std::to_string(v.sin);
+}
+
 void Engine::permute(zc alpha, const Tens &in, const std::string &mi, const Tens &out,
                      const std::string &mo, bool acc) {
   CCLR_REQUIRE((int)mi.size() == in.rank && (int)mo.size() == out.rank && in.rank == out.rank,
@@ -198,7 +211,12 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
   // whose modes need more than two levels is first permuted into a contiguous temporary.
   if (dt == C64 && tc_mode && nb <= 16 &&
       (tc_force || ((double)M * N * K >= 3.0e7 && M >= 16 && K >= 8))) {
-    contract_tc(alpha, A, ma, B, mb, C, mc, bat, Mm, Nm, Km, nb, M, N, K);
+    // the tensor-core tile is 128 rows high and up to 256 columns wide: a short M side
+    // goes to the columns (C^T = B^T A^T)
+    if (M < 128 && N > M)
+      contract_tc(alpha, B, mb, A, ma, C, mc, bat, Nm, Mm, Km, nb, N, M, K);
+    else
+      contract_tc(alpha, A, ma, B, mb, C, mc, bat, Mm, Nm, Km, nb, M, N, K);
     return;
   }
 
@@ -235,6 +253,9 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
       g.B = T.p; g.sBb = K * N; g.sBk = N; g.sBn = 1;
     }
   }
+  if (trace_on())
+    std::fprintf(stderr, "cclr contract simt %s,%s->%s nb=%lld M=%lld N=%lld K=%lld dt=%d\n", ma.c_str(),
+                 mb.c_str(), mc.c_str(), (long long)nb, (long long)M, (long long)N, (long long)K, dt);
   // C as [batch][M][N]
   int64_t s0, s1, s2, z;
   bool ok = group_view(C, mc, bat, z, s0) && group_view(C, mc, Mm, z, s1) &&
@@ -259,19 +280,33 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
   int64_t a0, b0, c0, z;
   View2 am, ak, bk, bn, cm, cn;
   const void *Ap = A.p, *Bp = B.p;
-  if (!(group_view(A, ma, bat, z, a0) && group_view2(A, ma, Mm, am) && group_view2(A, ma, Km, ak))) {
+  // A view is read (or written) in place only if one of its two indices walks memory in
+  // unit-stride runs of at least 8 elements (or the whole index, when shorter); otherwise
+  // the accesses would be scattered and a coalesced permute into a temporary is cheaper.
+  auto runs = [](const View2 &x, int64_t n) {
+    if (x.sin != 1) return false;
+    const int64_t run = x.din == TC_ONE_LEVEL ? n : x.din;
+    return run >= std::min<int64_t>(8, n);
+  };
+  auto coalesced = [&](const View2 &x, int64_t nx, const View2 &y, int64_t ny) {
+    return runs(x, nx) || runs(y, ny);
+  };
+  if (!(group_view(A, ma, bat, z, a0) && group_view2(A, ma, Mm, am) && group_view2(A, ma, Km, ak) &&
+        coalesced(am, M, ak, K))) {
     std::string order = bat + Mm + Km;
     Tens T = contiguous_like(ws(0, nb * M * K * es), C64, A, ma, order);
     permute(zc(1.0), A, ma, T, order, false);
     Ap = T.p; a0 = M * K; am = view1(K); ak = view1(1);
   }
-  if (!(group_view(B, mb, bat, z, b0) && group_view2(B, mb, Km, bk) && group_view2(B, mb, Nm, bn))) {
+  if (!(group_view(B, mb, bat, z, b0) && group_view2(B, mb, Km, bk) && group_view2(B, mb, Nm, bn) &&
+        coalesced(bk, K, bn, N))) {
     std::string order = bat + Km + Nm;
     Tens T = contiguous_like(ws(1, nb * K * N * es), C64, B, mb, order);
     permute(zc(1.0), B, mb, T, order, false);
     Bp = T.p; b0 = K * N; bk = view1(N); bn = view1(1);
   }
-  const bool direct = group_view(C, mc, bat, z, c0) && group_view2(C, mc, Mm, cm) && group_view2(C, mc, Nm, cn);
+  const bool direct = group_view(C, mc, bat, z, c0) && group_view2(C, mc, Mm, cm) &&
+                      group_view2(C, mc, Nm, cn) && coalesced(cm, M, cn, N);
   Tens T;
   if (!direct) {
     std::string order = bat + Mm + Nm;
@@ -280,6 +315,12 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
   }
   const int seg = tc_mode == 2 ? 3 : 1;
   const int64_t ld = 2 * tc_kpad(K) * seg;
+  if (trace_on())
+    std::fprintf(stderr, "cclr contract tc %s,%s->%s nb=%lld M=%lld N=%lld K=%lld A[%s|%s]%s B[%s|%s]%s C[%s|%s]%s\n",
+                 ma.c_str(), mb.c_str(), mc.c_str(), (long long)nb, (long long)M, (long long)N, (long long)K,
+                 vstr(am).c_str(), vstr(ak).c_str(), Ap == A.p ? "" : "(permuted)", vstr(bk).c_str(),
+                 vstr(bn).c_str(), Bp == B.p ? "" : "(permuted)", vstr(cm).c_str(), vstr(cn).c_str(),
+                 direct ? "" : "(temporary)");
   float *Ao = (float *)ws(3, (size_t)M * ld * 4);
   float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
   for (int64_t b = 0; b < nb; ++b) {

@@ -1,7 +1,13 @@
-// tcgen05 TF32 GEMM for sm_103a: TMA (128-byte swizzle) -> 4-stage shared-memory ring ->
-// tcgen05.mma issued by one thread -> FP32 accumulator in TMEM -> tcgen05.ld epilogue.
-// Every mbarrier wait is bounded (globaltimer); on timeout the kernel raises a device
-// flag, drains its own copies with a bounded wait, frees its TMEM and returns.
+// tcgen05 TF32 GEMM for sm_103a, persistent and warp-specialised: one CTA per SM walks a
+// static list of (tile, K split) work units.  Warp 0 streams A/B K blocks with TMA (128-byte
+// swizzle) into a 4-stage shared-memory ring, warp 1 issues tcgen05.mma into one of two TMEM
+// accumulators, and warps 2-5 drain the other accumulator (tcgen05.ld -> registers ->
+// shared-memory staging -> coalesced global stores), so the epilogue of one tile overlaps
+// the main loop of the next.  Every mbarrier wait is bounded (globaltimer); on timeout the
+// kernel raises a device flag, stops every role, drains its own copies and MMAs with bounded
+// waits, frees its TMEM and returns.
+#include <cstdio>
+#include <cstdlib>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -20,7 +26,9 @@ constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 struct TcParams {
   int M, N, K, BN;
   int nMt, nNt, band;   // tile counts; M tiles per raster band (N varies fastest inside a band)
-  int kb_per_split;     // K blocks per split (grid.y splits of K, atomically summed)
+  int kb_per_split;     // K blocks per split (splits of K are atomically summed)
+  int splits;           // work units = tiles x splits, walked with stride gridDim.x
+  int transposed;       // epilogue: 1 = lanes along columns (C columns contiguous), 0 = lane per row
   float *C;
   View2 rv, cv;         // C rows and complex columns
   float ar, ai;
@@ -114,7 +122,57 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(128, 1)
+// Bounded wait that also gives up when another role of the CTA has aborted.
+__device__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtime();
+  while (true) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort_flag) return false;
+    if (gtime() - t0 > TIMEOUT_NS) {
+      atomicExch(err, 1);
+      *abort_flag = 1;
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// work unit -> (m tile, n tile, split); banded rasterisation: consecutive units share one B
+// tile column across a band of M tiles, so the band's A tiles and the current B tiles stay in L2
+__device__ __forceinline__ void unit_coords(const TcParams &p, int u, int &m_tile, int &n_tile, int &split) {
+  const int tiles = p.nMt * p.nNt;
+  split = u / tiles;
+  const int id = u - split * tiles;
+  const int per_band = p.band * p.nNt;
+  const int b = id / per_band;
+  const int local = id - b * per_band;
+  const int mb = min(p.band, p.nMt - b * p.band);
+  m_tile = b * p.band + local % mb;
+  n_tile = local / mb;
+}
+
+constexpr int EPI_PITCH = 18;  // floats per staged row (16 + 2): conflict-free float2 traffic
+
+__device__ __forceinline__ void store_c(const TcParams &p, float *dst, float re, float im) {
+  float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
+  if (p.atomic) {
+    atomicAdd(dst, vr);
+    atomicAdd(dst + 1, vi);
+  } else {
+    if (p.accumulate) {
+      const float2 old = *reinterpret_cast<const float2 *>(dst);
+      vr += old.x;
+      vi += old.y;
+    }
+    *reinterpret_cast<float2 *>(dst) = make_float2(vr, vi);
+  }
+}
+
+__global__ void __launch_bounds__(192, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -122,36 +180,38 @@ __global__ void __launch_bounds__(128, 1)
   const int BN = p.BN;
   float *sA = (float *)smem;
   float *sB = (float *)(smem + STAGES * BM * BK * 4);
-  uint64_t *bars = (uint64_t *)(smem + STAGES * (BM + BN) * BK * 4);  // full[S], empty[S], acc
-  uint32_t *tslot = (uint32_t *)(bars + 2 * STAGES + 1);
-  int *progress = (int *)(tslot + 1);  // [0] loads issued, [1] stages consumed
+  float *stage = (float *)(smem + STAGES * (BM + BN) * BK * 4);  // 4 warps x 32 rows x EPI_PITCH
+  // barriers: full[S], empty[S], tfull[2], tempty[2], drain
+  uint64_t *bars = (uint64_t *)(stage + 4 * 32 * EPI_PITCH);
+  uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = tfull + 2,
+           *drain = tempty + 2;
+  uint32_t *tslot = (uint32_t *)(drain + 1);
+  int *issued = (int *)(tslot + 1);  // K blocks loaded (producer)
+  int *consumed = issued + 1;        // K blocks whose full barrier the MMA warp passed
+  volatile int *abort_flag = issued + 2;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // banded rasterisation: consecutive CTAs share one B tile column across a band of M tiles,
-  // so the band's A tiles and the current B tiles stay in L2
-  int m_tile, n_tile;
-  {
-    const int id = blockIdx.x;
-    const int per_band = p.band * p.nNt;
-    const int b = id / per_band;
-    const int local = id - b * per_band;
-    const int mb = min(p.band, p.nMt - b * p.band);
-    m_tile = b * p.band + local % mb;
-    n_tile = local / mb;
-  }
-  const int m0 = m_tile * BM, n0 = n_tile * BN;
+  const int units = p.nMt * p.nNt * p.splits;
   const int nk_all = (p.K + BK - 1) / BK;
-  const int kb0 = blockIdx.y * p.kb_per_split;
-  const int nk = max(0, min(nk_all - kb0, p.kb_per_split));
-  const uint32_t tcols = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+  // accumulator columns: one buffer per power of two >= BN, two buffers
+  const uint32_t half = BN <= 32 ? 32u : BN <= 64 ? 64u : BN <= 128 ? 128u : 256u;
+  const uint32_t tcols = 2 * half;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < 2 * STAGES + 1; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(bars + s)) : "memory");
+    for (int s = 0; s < STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(full + s)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(empty + s)) : "memory");
+    }
+    for (int b = 0; b < 2; ++b) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(tfull + b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(su32(tempty + b)) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(drain)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmB)) : "memory");
-    progress[0] = 0;
-    progress[1] = 0;
+    issued[0] = 0;
+    consumed[0] = 0;
+    *abort_flag = 0;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tslot)),
@@ -164,71 +224,113 @@ __global__ void __launch_bounds__(128, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    const uint32_t bytes = (uint32_t)(BM + BN) * BK * 4;
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (kb >= STAGES && !mbar_wait(su32(bars + STAGES + s), ph ^ 1u, p.err)) break;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(bars + s)), "r"(bytes)
-                   : "memory");
-      tma_load_2d(sA + s * BM * BK, &tmA, (kb0 + kb) * BK, m0, su32(bars + s));
-      tma_load_2d(sB + s * BN * BK, &tmB, (kb0 + kb) * BK, n0, su32(bars + s));
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer: K blocks of every unit of this CTA, through the ring
+      const uint32_t bytes = (uint32_t)(BM + BN) * BK * 4;
+      int g = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
+        int mt, nt, sp;
+        unit_coords(p, u, mt, nt, sp);
+        const int kb0 = sp * p.kb_per_split;
+        const int nk = max(0, min(nk_all - kb0, p.kb_per_split));
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait_ab(su32(empty + s), ph ^ 1u, p.err, abort_flag)) { ok = false; break; }
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(full + s)), "r"(bytes)
+                       : "memory");
+          tma_load_2d(sA + s * BM * BK, &tmA, (kb0 + kb) * BK, mt * BM, su32(full + s));
+          tma_load_2d(sB + s * BN * BK, &tmB, (kb0 + kb) * BK, nt * BN, su32(full + s));
+          issued[0] = g + 1;
+        }
+      }
     }
-    progress[0] = kb;
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = idesc_tf32(BM, BN);
-    int kb = 0;
-    for (; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (uint32_t)(kb / STAGES) & 1u;
-      if (!mbar_wait(su32(bars + s), ph, p.err)) break;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer: accumulator buffer it & 1 for the it-th unit of this CTA
+      const uint32_t idesc = idesc_tf32(BM, BN);
+      int g = 0, it = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++it) {
+        int mt, nt, sp;
+        unit_coords(p, u, mt, nt, sp);
+        const int kb0 = sp * p.kb_per_split;
+        const int nk = max(0, min(nk_all - kb0, p.kb_per_split));
+        const int buf = it & 1;
+        if (!mbar_wait_ab(su32(tempty + buf), ((uint32_t)(it >> 1) & 1u) ^ 1u, p.err, abort_flag)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + (uint32_t)buf * half;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (uint32_t)(g / STAGES) & 1u;
+          if (!mbar_wait_ab(su32(full + s), ph, p.err, abort_flag)) { ok = false; break; }
+          consumed[0] = g + 1;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint64_t da = sw128_desc(su32(sA + s * BM * BK));
+          const uint64_t db = sw128_desc(su32(sB + s * BN * BK));
+#pragma unroll
+          for (int kk = 0; kk < BK / 8; ++kk)  // 8 tf32 = 32 bytes per instruction
+            mma_tf32(dacc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
+          mma_commit(su32(empty + s));
+        }
+        if (ok) mma_commit(su32(tfull + buf));  // arrives once this unit's MMAs have completed
+      }
+      // every MMA issued above has completed once this arrives
+      mma_commit(su32(drain));
+      mbar_wait(su32(drain), 0, p.err);
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31
+    const int q = warp & 3;
+    float *stg = stage + (warp - 2) * 32 * EPI_PITCH;
+    int it = 0;
+    for (int u = blockIdx.x; u < units; u += gridDim.x, ++it) {
+      int mt, nt, sp;
+      unit_coords(p, u, mt, nt, sp);
+      const int buf = it & 1;
+      bool ok = mbar_wait_ab(su32(tfull + buf), (uint32_t)(it >> 1) & 1u, p.err, abort_flag);
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t da = sw128_desc(su32(sA + s * BM * BK));
-      const uint64_t db = sw128_desc(su32(sB + s * BN * BK));
+      const int m0 = mt * BM, n0 = nt * BN;
+      const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * half;
+      const int row = m0 + q * 32 + lane;
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t r[16];
+        tmem_ld16(tbase + (uint32_t)c0, r);
+        if (c0 + 16 >= BN) {
+          // the accumulator buffer is free for the next unit once every lane has read it
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(su32(tempty + buf));
+        }
+        if (p.transposed) {
+          // stage rows, then write 4 rows x 8 complex per instruction (64 contiguous bytes per row)
+          float2 *srow = reinterpret_cast<float2 *>(stg + lane * EPI_PITCH);
 #pragma unroll
-      for (int kk = 0; kk < BK / 8; ++kk)  // 8 tf32 = 32 bytes per instruction
-        mma_tf32(tmem, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
-      mma_commit(su32(bars + STAGES + s));
-    }
-    progress[1] = kb;
-    mma_commit(su32(bars + 2 * STAGES));  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-
-  // epilogue: TMEM lanes 32w..32w+31 hold rows m0 + 32w + lane
-  bool ok = mbar_wait(su32(bars + 2 * STAGES), 0, p.err);
-  ok = __all_sync(0xffffffffu, ok) && (*(volatile int *)p.err == 0);
-  ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (ok && nk > 0) {
-    const int row = m0 + warp * 32 + lane;
-    float *crow = p.C + 2 * (row < p.M ? v2off(p.rv, row) : 0);
-    for (int c0 = 0; c0 < BN; c0 += 16) {
-      uint32_t r[16];
-      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, r);
-      if (row < p.M) {
-#pragma unroll
-        for (int j = 0; j < 16; j += 2) {
-          const int n = n0 + c0 + j;
-          if (n < p.N) {
-            float *dst = crow + 2 * v2off(p.cv, n >> 1);
-            const float re = __uint_as_float(r[j]), im = __uint_as_float(r[j + 1]);
-            float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
-            if (p.atomic) {
-              atomicAdd(dst, vr);
-              atomicAdd(dst + 1, vi);
-            } else {
-              if (p.accumulate) {
-                vr += dst[0];
-                vi += dst[1];
-              }
-              dst[0] = vr;
-              dst[1] = vi;
+          for (int j = 0; j < 8; ++j) srow[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
+          __syncwarp();
+          const int jj = lane & 7, rs = lane >> 3;
+          const int n = n0 + c0 + 2 * jj;
+#pragma unroll 2
+          for (int rr = 0; rr < 32; rr += 4) {
+            const int rl = rr + rs, grow = m0 + q * 32 + rl;
+            if (grow < p.M && n < p.N) {
+              const float2 v = reinterpret_cast<const float2 *>(stg + rl * EPI_PITCH)[jj];
+              store_c(p, p.C + 2 * (v2off(p.rv, grow) + v2off(p.cv, n >> 1)), v.x, v.y);
             }
+          }
+          __syncwarp();
+        } else if (row < p.M) {
+          float *crow = p.C + 2 * v2off(p.rv, row);
+#pragma unroll
+          for (int j = 0; j < 16; j += 2) {
+            const int n = n0 + c0 + j;
+            if (n < p.N) store_c(p, crow + 2 * v2off(p.cv, n >> 1), __uint_as_float(r[j]), __uint_as_float(r[j + 1]));
           }
         }
       }
@@ -236,10 +338,10 @@ __global__ void __launch_bounds__(128, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (threadIdx.x == 0 && progress[1] < progress[0]) {
+  if (threadIdx.x == 0 && consumed[0] < issued[0]) {
     // error path: drain TMA copies issued but never consumed (bounded)
-    for (int kb = progress[1]; kb < progress[0]; ++kb)
-      mbar_wait(su32(bars + kb % STAGES), (uint32_t)(kb / STAGES) & 1u, p.err);
+    for (int g = consumed[0]; g < issued[0]; ++g)
+      mbar_wait(su32(full + g % STAGES), (uint32_t)(g / STAGES) & 1u, p.err);
   }
   __syncthreads();
   if (warp == 1)
@@ -419,6 +521,16 @@ int pick_bn(int64_t N) {
   return best;
 }
 
+int num_sms() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      n <= 0) {
+    (void)cudaGetLastError();
+    return 152;
+  }
+  return n;
+}
+
 unsigned grid1d(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
 }
@@ -487,19 +599,23 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
   p.band = (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * 4 + 1)));
   const int nk = (int)((Kreal + BK - 1) / BK);
   const int64_t tiles = (int64_t)p.nMt * p.nNt;
-  // split K when the tile grid cannot fill the GPU (two CTAs' worth per SM), at least
-  // 16 K blocks per split
+  const int nsm = num_sms();
+  // split K when the tile list cannot fill the GPU (two units per SM), at least 16 K blocks
+  // per split
   int splits = 1;
-  if (tiles < 2 * 152 && nk >= 32)
-    splits = (int)std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, nk / 16));
+  if (tiles < 2 * nsm && nk >= 32)
+    splits = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + tiles - 1) / tiles, nk / 16));
   // bound the length of each accumulation chain (accuracy of the split-precision passes)
   if (max_kb_per_split > 0) splits = std::max(splits, (nk + max_kb_per_split - 1) / max_kb_per_split);
   splits = std::min(splits, 65535);
   p.kb_per_split = (nk + splits - 1) / splits;
-  splits = (nk + p.kb_per_split - 1) / p.kb_per_split;
+  splits = (nk + p.kb_per_split - 1) / p.kb_per_split;  // every split has at least one K block
+  p.splits = splits;
   p.C = C;
   p.rv = rv;
   p.cv = cv;
+  // lanes along columns when C's columns run contiguously, one lane per row otherwise
+  p.transposed = (cv.sin == 1 && (cv.din == TC_ONE_LEVEL || cv.din >= 8)) ? 1 : 0;
   p.ar = (float)alpha.re;
   p.ai = (float)alpha.im;
   p.atomic = splits > 1 ? 1 : 0;
@@ -510,10 +626,17 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
                  "tc_gemm: split K without accumulation needs a plain C layout");
     CCLR_CUDA(cudaMemset2DAsync(C, (size_t)rv.sin * 8, 0, (size_t)Nreal * 4, (size_t)M, st));
   }
-  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (2 * STAGES + 1) * 8 + 16;
-  CCLR_REQUIRE(tiles < (1ll << 31) && splits <= 65535, "tc_gemm: grid too large");
-  dim3 grid((unsigned)tiles, (unsigned)splits);
-  tc_gemm_kernel<<<grid, 128, smem, st>>>(ma, mb, p);
+  const int64_t units = tiles * splits;
+  CCLR_REQUIRE(units < (1ll << 31), "tc_gemm: too many work units");
+  static const bool trace = std::getenv("CCLR_TRACE") && std::getenv("CCLR_TRACE")[0] == '1';
+  if (trace)
+    std::fprintf(stderr, "cclr tc_gemm M=%lld N=%lld K=%lld BN=%d tiles=%lld splits=%d band=%d atomic=%d transposed=%d\n",
+                 (long long)M, (long long)Nreal, (long long)Kreal, BN, (long long)tiles, splits, p.band, p.atomic,
+                 p.transposed);
+  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (size_t)4 * 32 * EPI_PITCH * 4 +
+                      (2 * STAGES + 5) * 8 + 16;
+  const unsigned grid = (unsigned)std::min<int64_t>(units, nsm);
+  tc_gemm_kernel<<<grid, 192, smem, st>>>(ma, mb, p);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
