@@ -46,14 +46,16 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
 
   const bool a_kfast = (g.sAk == 1);
   const bool b_nfast = (g.sBn == 1);
-  for (int64_t k0 = 0; k0 < g.K; k0 += BK) {
+  const int64_t kbeg = g.kchunk > 0 ? (int64_t)blockIdx.y * g.kchunk : 0;
+  const int64_t kend = g.kchunk > 0 ? min(g.K, kbeg + g.kchunk) : g.K;
+  for (int64_t k0 = kbeg; k0 < kend; k0 += BK) {
 #pragma unroll
     for (int e = tid; e < BM * BK; e += NT) {
       int mm, kk;
       if (a_kfast) { kk = e % BK; mm = e / BK; } else { mm = e % BM; kk = e / BM; }
       int64_t m = m0 + mm, k = k0 + kk;
       C val = C{T(0), T(0)};
-      if (m < g.M && k < g.K) val = A[m * g.sAm + k * g.sAk];
+      if (m < g.M && k < kend) val = A[m * g.sAm + k * g.sAk];
       As[kk][mm] = val;
     }
 #pragma unroll
@@ -62,7 +64,7 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       if (b_nfast) { nn = e % BN; kk = e / BN; } else { kk = e % BK; nn = e / BK; }
       int64_t n = n0 + nn, k = k0 + kk;
       C val = C{T(0), T(0)};
-      if (n < g.N && k < g.K) val = B[k * g.sBk + n * g.sBn];
+      if (n < g.N && k < kend) val = B[k * g.sBk + n * g.sBn];
       Bs[kk][nn] = val;
     }
     __syncthreads();
@@ -99,6 +101,11 @@ __global__ void __launch_bounds__((BM / TM) * (BN / TN))
       C r;
       r.x = ar * v.x - ai * v.y;
       r.y = ar * v.y + ai * v.x;
+      if (g.kchunk > 0) {  // partial sum over this block's K range
+        atomicAdd(&dst->x, r.x);
+        atomicAdd(&dst->y, r.y);
+        continue;
+      }
       if (!g.overwrite) {
         C o = *dst;
         r.x += o.x;
@@ -115,19 +122,30 @@ void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st) {
     CCLR_REQUIRE(!g.overwrite, "gemm with K=0 and overwrite is not supported");
     return;
   }
+  const int64_t tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  // split K over blocks (partial sums added atomically) when the tile grid cannot fill the
+  // GPU and K is long: the skinny and matrix-vector shapes
+  int64_t splits = 1;
+  const int64_t bk = dt == C128 ? 8 : 16;
+  const bool plain_c = g.sCn == 1 && g.sCm == g.N && (g.batch == 1 || g.sCb == g.M * g.N);
+  if (tiles * g.batch < 2 * 152 && g.K >= 1024 && (!g.overwrite || plain_c) && g.batch <= 65535)
+    splits = std::min<int64_t>((2 * 152 + tiles * g.batch - 1) / (tiles * g.batch), g.K / 256);
+  GemmArgs ga = g;
+  if (splits > 1) {
+    ga.kchunk = ((g.K + splits - 1) / splits + bk - 1) / bk * bk;
+    splits = (g.K + ga.kchunk - 1) / ga.kchunk;
+    if (g.overwrite) {
+      CCLR_CUDA(cudaMemsetAsync(g.C, 0, (size_t)g.batch * g.M * g.N * (dt == C128 ? 16 : 8), st));
+      ga.overwrite = 0;
+    }
+  }
   for (int64_t b0 = 0; b0 < g.batch; b0 += 65535) {
     int64_t nb = std::min<int64_t>(65535, g.batch - b0);
-    if (dt == C128) {
-      constexpr int BM = 64, BN = 64, BK = 8;
-      int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-      dim3 grid((unsigned)tiles, 1, (unsigned)nb);
-      zgemm_simt<double, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g, b0);
-    } else {
-      constexpr int BM = 64, BN = 64, BK = 16;
-      int64_t tiles = ((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-      dim3 grid((unsigned)tiles, 1, (unsigned)nb);
-      zgemm_simt<float, BM, BN, BK, 4, 4><<<grid, 256, 0, st>>>(g, b0);
-    }
+    dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)nb);
+    if (dt == C128)
+      zgemm_simt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
+    else
+      zgemm_simt<float, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
     count_launch();
     CCLR_CUDA(cudaGetLastError());
   }

@@ -16,6 +16,7 @@ struct GemmArgs {
   int64_t sCb = 0, sCm = 0, sCn = 0;
   double alr = 1.0, ali = 0.0;
   int overwrite = 0;  // 1: C = alpha A B ; 0: C += alpha A B
+  int64_t kchunk = 0;  // set by launch_gemm: K range per block when K is split (atomic sums)
 };
 
 struct PermArgs {

@@ -1,7 +1,7 @@
 // tcgen05 TF32 GEMM for sm_103a, persistent and warp-specialised: one CTA per SM walks a
 // static list of (tile, K split) work units.  Warp 0 streams A/B K blocks with TMA (128-byte
 // swizzle) into a 4-stage shared-memory ring, warp 1 issues tcgen05.mma into one of two TMEM
-// accumulators, and warps 2-5 drain the other accumulator (tcgen05.ld -> registers ->
+// accumulators, and warps 2-9 drain the other accumulator (tcgen05.ld -> registers ->
 // shared-memory staging -> coalesced global stores), so the epilogue of one tile overlaps
 // the main loop of the next.  Every mbarrier wait is bounded (globaltimer); on timeout the
 // kernel raises a device flag, stops every role, drains its own copies and MMAs with bounded
@@ -157,22 +157,7 @@ __device__ __forceinline__ void unit_coords(const TcParams &p, int u, int &m_til
 
 constexpr int EPI_PITCH = 18;  // floats per staged row (16 + 2): conflict-free float2 traffic
 
-__device__ __forceinline__ void store_c(const TcParams &p, float *dst, float re, float im) {
-  float vr = p.ar * re - p.ai * im, vi = p.ar * im + p.ai * re;
-  if (p.atomic) {
-    atomicAdd(dst, vr);
-    atomicAdd(dst + 1, vi);
-  } else {
-    if (p.accumulate) {
-      const float2 old = *reinterpret_cast<const float2 *>(dst);
-      vr += old.x;
-      vi += old.y;
-    }
-    *reinterpret_cast<float2 *>(dst) = make_float2(vr, vi);
-  }
-}
-
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcParams p) {
   extern __shared__ uint8_t smem_raw[];
@@ -180,9 +165,9 @@ __global__ void __launch_bounds__(192, 1)
   const int BN = p.BN;
   float *sA = (float *)smem;
   float *sB = (float *)(smem + STAGES * BM * BK * 4);
-  float *stage = (float *)(smem + STAGES * (BM + BN) * BK * 4);  // 4 warps x 32 rows x EPI_PITCH
+  float *stage = (float *)(smem + STAGES * (BM + BN) * BK * 4);  // 8 warps x 32 rows x EPI_PITCH
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
-  uint64_t *bars = (uint64_t *)(stage + 4 * 32 * EPI_PITCH);
+  uint64_t *bars = (uint64_t *)(stage + 8 * 32 * EPI_PITCH);
   uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = tfull + 2,
            *drain = tempty + 2;
   uint32_t *tslot = (uint32_t *)(drain + 1);
@@ -203,7 +188,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(tfull + b)) : "memory");
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 4;" ::"r"(su32(tempty + b)) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;" ::"r"(su32(tempty + b)) : "memory");
     }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(su32(drain)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -284,8 +269,9 @@ __global__ void __launch_bounds__(192, 1)
     }
     __syncwarp();
   } else {
-    // epilogue warps 2..5: TMEM lane quarter (warp % 4) holds rows 32 (warp % 4) .. + 31
-    const int q = warp & 3;
+    // epilogue warps 2..9: warps w and w + 4 share TMEM lane quarter w % 4 (rows 32 (w % 4)
+    // .. + 31 of the tile) and take alternate 16-column chunks
+    const int q = warp & 3, h = (warp - 2) >> 2;
     float *stg = stage + (warp - 2) * 32 * EPI_PITCH;
     int it = 0;
     for (int u = blockIdx.x; u < units; u += gridDim.x, ++it) {
@@ -299,39 +285,71 @@ __global__ void __launch_bounds__(192, 1)
       const int m0 = mt * BM, n0 = nt * BN;
       const uint32_t tbase = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)buf * half;
       const int row = m0 + q * 32 + lane;
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      if (16 * h >= BN) {  // no chunk for this warp: release the buffer at once
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(su32(tempty + buf));
+        continue;
+      }
+      for (int c0 = 16 * h; c0 < BN; c0 += 32) {
         uint32_t r[16];
         tmem_ld16(tbase + (uint32_t)c0, r);
-        if (c0 + 16 >= BN) {
-          // the accumulator buffer is free for the next unit once every lane has read it
+        if (c0 + 32 >= BN) {
+          // the accumulator buffer is free for the next unit once every warp has read its part
           asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
           __syncwarp();
           if (lane == 0) mbar_arrive(su32(tempty + buf));
         }
+        // eight complex values per lane: destinations first, then all loads, then all stores
+        // (independent accesses in flight instead of one read-modify-write at a time)
+        float *dst[8];
+        float2 val[8];
         if (p.transposed) {
-          // stage rows, then write 4 rows x 8 complex per instruction (64 contiguous bytes per row)
+          // stage rows, then 4 rows x 8 complex per instruction (64 contiguous bytes per row)
           float2 *srow = reinterpret_cast<float2 *>(stg + lane * EPI_PITCH);
 #pragma unroll
           for (int j = 0; j < 8; ++j) srow[j] = make_float2(__uint_as_float(r[2 * j]), __uint_as_float(r[2 * j + 1]));
           __syncwarp();
           const int jj = lane & 7, rs = lane >> 3;
           const int n = n0 + c0 + 2 * jj;
-#pragma unroll 2
-          for (int rr = 0; rr < 32; rr += 4) {
-            const int rl = rr + rs, grow = m0 + q * 32 + rl;
-            if (grow < p.M && n < p.N) {
-              const float2 v = reinterpret_cast<const float2 *>(stg + rl * EPI_PITCH)[jj];
-              store_c(p, p.C + 2 * (v2off(p.rv, grow) + v2off(p.cv, n >> 1)), v.x, v.y);
-            }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int rl = 4 * k + rs, grow = m0 + q * 32 + rl;
+            val[k] = reinterpret_cast<const float2 *>(stg + rl * EPI_PITCH)[jj];
+            dst[k] = (grow < p.M && n < p.N) ? p.C + 2 * (v2off(p.rv, grow) + v2off(p.cv, n >> 1)) : nullptr;
           }
           __syncwarp();
-        } else if (row < p.M) {
-          float *crow = p.C + 2 * v2off(p.rv, row);
+        } else {
+          const float *crow = p.C + 2 * v2off(p.rv, row < p.M ? row : 0);
 #pragma unroll
-          for (int j = 0; j < 16; j += 2) {
-            const int n = n0 + c0 + j;
-            if (n < p.N) store_c(p, crow + 2 * v2off(p.cv, n >> 1), __uint_as_float(r[j]), __uint_as_float(r[j + 1]));
+          for (int k = 0; k < 8; ++k) {
+            const int n = n0 + c0 + 2 * k;
+            val[k] = make_float2(__uint_as_float(r[2 * k]), __uint_as_float(r[2 * k + 1]));
+            dst[k] = (row < p.M && n < p.N) ? const_cast<float *>(crow) + 2 * v2off(p.cv, n >> 1) : nullptr;
           }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+          val[k] = make_float2(p.ar * val[k].x - p.ai * val[k].y, p.ar * val[k].y + p.ai * val[k].x);
+        if (p.atomic) {
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (dst[k]) {
+              atomicAdd(dst[k], val[k].x);
+              atomicAdd(dst[k] + 1, val[k].y);
+            }
+        } else {
+          if (p.accumulate) {
+            float2 old[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              old[k] = dst[k] ? *reinterpret_cast<const float2 *>(dst[k]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) val[k] = make_float2(val[k].x + old[k].x, val[k].y + old[k].y);
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (dst[k]) *reinterpret_cast<float2 *>(dst[k]) = val[k];
         }
       }
     }
@@ -633,10 +651,10 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
     std::fprintf(stderr, "cclr tc_gemm M=%lld N=%lld K=%lld BN=%d tiles=%lld splits=%d band=%d atomic=%d transposed=%d\n",
                  (long long)M, (long long)Nreal, (long long)Kreal, BN, (long long)tiles, splits, p.band, p.atomic,
                  p.transposed);
-  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (size_t)4 * 32 * EPI_PITCH * 4 +
+  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (size_t)8 * 32 * EPI_PITCH * 4 +
                       (2 * STAGES + 5) * 8 + 16;
   const unsigned grid = (unsigned)std::min<int64_t>(units, nsm);
-  tc_gemm_kernel<<<grid, 192, smem, st>>>(ma, mb, p);
+  tc_gemm_kernel<<<grid, 320, smem, st>>>(ma, mb, p);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
