@@ -123,6 +123,14 @@ cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
 /* Switch the arithmetic of subsequent sigma / sigma^T / solves. */
 cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
 
+/* Arithmetic of the mixed modes' accurate sigma products: the residual of every refinement
+ * step, the polish that finishes a refinement which stalls, and the sigma^T products of the
+ * F X stencil.  CCLR_FP64 (default): FP64 on CUDA cores; CCLR_C64_3XTF32: complex64 with
+ * 3xTF32 on the tensor cores (about FP32 accuracy; the residual norms, vector updates, Krylov
+ * subspace and alpha contractions stay FP64 either way).  The FP64 sigma is slow on GPUs with
+ * a reduced FP64 rate, so large systems use CCLR_C64_3XTF32 with CCLR_C64_TF32 corrections. */
+cclr_status cc_lr_set_refinement(cclr_ctx *ctx, int prec);
+
 /* Linear solver of cc_lr_solve / cc_lr_solve_x / cc_lr_lambda: method 1 = restarted
  * GMRES with the diagonal preconditioner (default; subspace = restart length),
  * method 0 = DIIS extrapolation of preconditioned Jacobi steps (subspace ignored; the

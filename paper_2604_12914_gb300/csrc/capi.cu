@@ -45,6 +45,10 @@ struct cclr_ctx {
   AVec lam;
   std::vector<AVec> stage_in, stage_out;  // host <-> device staging (complex128), per RHS
   CstSet shift;                   // intermediates at shifted amplitudes (F X stencils)
+  CstSet shift64;                 // their complex64 rounding (tensor-core F X stencils)
+  // arithmetic of the mixed modes' accurate sigma products: the refinement residuals, the
+  // final polish and the F X stencils (CCLR_FP64, or CCLR_C64_3XTF32 on the tensor cores)
+  int hi_prec = CCLR_FP64;
   int sigma_calls = 0;
 
   int64_t ntot() const { return n1 + n2; }
@@ -137,7 +141,7 @@ struct cclr_ctx {
     bool stalled = false;
     for (int outer = 0; outer < 40 && used < maxit; ++outer) {
       if (outer > 0) {
-        M->prec = CCLR_FP64;
+        M->prec = hi_prec;
         op(dir, x, s.b.p);
         M->prec = lo;
         ++refinements;
@@ -168,13 +172,13 @@ struct cclr_ctx {
       axpy(zd(1), d.b.p, x);
     }
     if ((stalled || rel >= tol) && used < maxit) {
-      // finish in FP64, warm-started from the refined solution
-      M->prec = CCLR_FP64;
+      // finish in the accurate arithmetic, warm-started from the refined solution
+      M->prec = hi_prec;
       int rest = 0;
       rel = solve_diis(dir, omega, b, x, tol, depth, maxit - used, &rest, true);
       M->prec = lo;
       if (its) *its += rest;
-      if (verbose()) std::fprintf(stderr, "cclr fp64 finish dir=%d iterations=%d rel=%.3e\n", dir, rest, rel);
+      if (verbose()) std::fprintf(stderr, "cclr finish prec=%d dir=%d iterations=%d rel=%.3e\n", hi_prec, dir, rest, rel);
     }
     return rel;
   }
@@ -480,8 +484,14 @@ struct cclr_ctx {
       shifted(x, ks[s] * h, ts);
       M->build_set(ts.p1(), ts.p2(n1), shift, C128);
       const int saved = M->prec;
-      M->prec = CCLR_FP64;
-      op(-1, lam.b.p, sv.b.p, &shift);
+      const int use = M->prec == CCLR_FP64 ? CCLR_FP64 : hi_prec;
+      M->prec = use;
+      if (use == CCLR_FP64) {
+        op(-1, lam.b.p, sv.b.p, &shift);
+      } else {
+        M->round_set(shift, shift64);
+        op(-1, lam.b.p, sv.b.p, &shift64);
+      }
       M->prec = saved;
       axpy(zd(cs[s] / (12.0 * h)), sv.b.p, out);
     }
@@ -747,6 +757,15 @@ cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
   if (!c || prec < 0 || prec > 3) return (cclr_status)fail(CCLR_EINVAL, "bad precision");
   return (cclr_status)guarded([&] {
     c->M->prec = prec;
+    if (prec != CCLR_FP64) c->M->cst_for(prec);
+  });
+}
+
+cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
+  if (!c || (prec != CCLR_FP64 && prec != CCLR_C64_3XTF32))
+    return (cclr_status)fail(CCLR_EINVAL, "refinement precision must be CCLR_FP64 or CCLR_C64_3XTF32");
+  return (cclr_status)guarded([&] {
+    c->hi_prec = prec;
     if (prec != CCLR_FP64) c->M->cst_for(prec);
   });
 }

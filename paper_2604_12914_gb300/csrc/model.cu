@@ -234,6 +234,8 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
   E.tc_mode = tc_saved;
+  for (int k = 0; k < 2; ++k)  // a ladder prepared from this buffer is stale
+    if (ltc_src[k] == out.t[K_LVV].p) ltc_src[k] = nullptr;
   out.valid = true;
 }
 
@@ -249,26 +251,33 @@ void Model::build_diagonal() {
   CCLR_CUDA(cudaStreamSynchronize(st));
 }
 
+// complex64 rounding of a complex128 set (same shapes, contiguous)
+void Model::round_set(const CstSet &src, CstSet &dst) {
+  CCLR_REQUIRE(src.valid && src.dt == C128, "round_set: source must be a valid complex128 set");
+  dst.dt = C64;
+  for (int k = 0; k < K_NCST; ++k) {
+    const Tens &s = src.t[k];
+    const size_t bytes = (size_t)s.numel() * 8;
+    if (dst.buf[k].bytes != bytes) dst.buf[k].alloc(bytes);
+    Tens d = s;
+    d.p = dst.buf[k].p;
+    d.dt = C64;
+    const std::string m = std::string("abcdefgh").substr(0, s.rank);
+    E.permute(zc(1), s, m, d, m, false);
+    dst.t[k] = d;
+  }
+  // a tensor-core ladder prepared from this set's L~_vv (same buffer) is now stale
+  for (int k = 0; k < 2; ++k)
+    if (ltc_src[k] == dst.t[K_LVV].p) ltc_src[k] = nullptr;
+  CCLR_CUDA(cudaStreamSynchronize(st));
+  dst.valid = true;
+}
+
 // The working intermediates are built in FP64; the complex64 modes read a rounded copy.
 const CstSet &Model::cst_for(int p) {
   if (!c128.valid) build_set(t1.p, t2.p, c128, C128);
   if (p == 0) return c128;
-  if (!c64.valid) {
-    c64.dt = C64;
-    for (int k = 0; k < K_NCST; ++k) {
-      const Tens &s = c128.t[k];
-      const size_t bytes = (size_t)s.numel() * 8;
-      if (c64.buf[k].bytes != bytes) c64.buf[k].alloc(bytes);
-      Tens d = s;
-      d.p = c64.buf[k].p;
-      d.dt = C64;
-      const std::string m = std::string("abcdefgh").substr(0, s.rank);
-      E.permute(zc(1), s, m, d, m, false);
-      c64.t[k] = d;
-    }
-    CCLR_CUDA(cudaStreamSynchronize(st));
-    c64.valid = true;
-  }
+  if (!c64.valid) round_set(c128, c64);
   return c64;
 }
 

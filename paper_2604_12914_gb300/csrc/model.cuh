@@ -91,6 +91,7 @@ class Model {
   const Tens &oovv128();
   void build_diagonal();
   const CstSet &cst_for(int prec_) ;
+  void round_set(const CstSet &src, CstSet &dst);
 
   // sigma (dir = +1) or sigma^T (dir = -1) on device buffers of the given dtype.
   void apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2);

@@ -188,6 +188,23 @@ def test_alpha_mixed_precision_within_1e4(prec):
     ctx.close()
 
 
+def test_alpha_tensor_core_refinement_within_1e4():
+    """TF32 corrections refined with 3xTF32 residuals (no FP64 sigma anywhere: residuals,
+    polish and the F X stencil on the tensor cores; norms, updates, subspace and alpha in FP64)
+    against the FP64 oracle: |delta alpha| < 1e-4 a.u. for every entry."""
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy(), prec="tf32")
+    ctx.cc_lr_set_refinement("3xtf32")
+    for omega in (0.0, 0.0428):
+        al, st = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-6)
+        ref = R.alpha(P, [as_t(m) for m in s.mu], omega).numpy()
+        err = np.abs(al[0] - ref).max()
+        print(f"omega={omega}: |delta alpha| = {err:.2e}, max|alpha| = {np.abs(ref).max():.3f}, {st}")
+        assert err < 1e-4, (omega, err)
+        assert st["refinements"] > 0
+    ctx.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("tf32", 3e-3), ("3xtf32", 5e-5)])
 def test_batched_sigma_matches_single(prec, tol):
     """Several right-hand sides share each formed <ab||ef>~ block; results equal the oracle."""
