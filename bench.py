@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--alpha-config", default="C1")
     ap.add_argument("--alpha-scale", type=float, default=0.2)
     ap.add_argument("--batch-rhs", type=int, default=9)
+    ap.add_argument("--no-alpha-large", action="store_true")
+    ap.add_argument("--alpha-large-config", default="C2")
+    ap.add_argument("--alpha-large-scale", type=float, default=0.05)
     return ap.parse_args()
 
 
@@ -54,7 +57,7 @@ def algorithmic(o, v, naux):
     form = naux * Pv * v * v          # <ab|ef>~ for a<b, all (e, f)
     contr = Po * Pv * Pv              # sum_{e<f} <ab||ef>~ X_ij^ef
     ring = o ** 3 * v ** 3
-    return {"ladder_cmac": form + contr, "ring_cmac": ring,
+    return {"ladder_cmac": form + contr, "form_cmac": form, "ring_cmac": ring,
             "n_unique": o * v + Po * Pv}
 
 
@@ -249,6 +252,33 @@ def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428),
     return out
 
 
+def time_to_alpha_large(cfg, scale, comps=(2,), omegas=(0.0,), tol=1e-6):
+    """Wall time of cc_lr_solve on the large workload with tensor-core arithmetic throughout
+    the solve: TF32 corrections, 3xTF32 refinement residuals and F X stencils, FP64 vectors,
+    Krylov subspace and alpha contractions.  (One FP64 sigma at this size takes about a minute on
+    this GPU, so the FP64 path is not run here.)"""
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import make_config
+    s = make_config(cfg, scale=scale)
+    t0 = time.perf_counter()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec="tf32")
+    ctx.cc_lr_set_refinement("3xtf32")
+    t_init = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    al, st = ctx.cc_lr_solve(list(omegas), comps, tol=tol, allow_noconv=True)
+    el = time.perf_counter() - t0
+    ctx.close()
+    return {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
+            "components": list(comps), "omegas": list(omegas), "tol": tol,
+            "precision_mode": "tf32 corrections, 3xtf32 refinement, fp64 vectors",
+            "seconds": el, "init_seconds": t_init, "iterations": st["iterations"],
+            "sigma_calls": st["sigma_calls"], "refinements": st["refinements"],
+            "converged": st["converged"], "max_rel_residual": st["max_rel_residual"],
+            "seconds_solve_lambda_alpha": [st["time_solve_ms"] / 1e3, st["time_lambda_ms"] / 1e3,
+                                           st["time_alpha_ms"] / 1e3],
+            "alpha": [[float(al[w, a, a].real) for a in range(len(comps))] for w in range(len(omegas))]}
+
+
 def run_cclr(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -285,14 +315,16 @@ def run_cclr(args):
         ctx.sigma_into(x1, x2, s1, s2)
     barrier()
     n0 = binding.cc_lr_launch_count()
-    lad = []
+    lad, form = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local) as ck:
         torch.cuda.profiler.start()       # profiler range = the timed region (ncu --profile-from-start off)
         e0.record(stream)
         for _ in range(args.steps):
             ctx.sigma_into(x1, x2, s1, s2)
-            lad.append(float(ctx.cc_lr_last_timings()[0]))
+            tm = ctx.cc_lr_last_timings()
+            lad.append(float(tm[0]))
+            form.append(float(tm[3]))
         e1.record(stream)
         barrier()
         torch.cuda.profiler.stop()
@@ -345,12 +377,23 @@ def run_cclr(args):
 
     alg = algorithmic(o, v, naux)
     lad_ms = sum(lad) / len(lad)
+    form_ms = sum(form) / len(form)
     bound, peak, how = ladder_peak(args.prec)
-    achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
+    lad_achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
+    # the dominant kernel: the tensor-core GEMMs that form <ab|ef>~ (CUDA events around each)
+    if form_ms > 0:
+        kernel = "tc_gemm_kernel: pp-ladder formation <ab|ef>~ = sum_P L~_ae L~_bf (all groups of one sigma)"
+        achieved = alg["form_cmac"] * 8 / (form_ms * 1e-3) / 1e12
+    else:
+        kernel = "pp-ladder (formation + contraction)"
+        achieved = lad_achieved
     ctx.close()
     tta = None
+    tta_large = None
     if rank == 0 and not args.no_alpha:
         tta = time_to_alpha(args.alpha_config, args.alpha_scale, "tf32" if args.prec in ("tf32", "fp64") else args.prec)
+        if not args.no_alpha_large:
+            tta_large = time_to_alpha_large(args.alpha_large_config, args.alpha_large_scale)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,
@@ -361,10 +404,12 @@ def run_cclr(args):
             "config": {"workload": f"{args.config} o={o} v={v} naux={naux} single-RHS sigma",
                        "precision_mode": args.prec, "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (X2 c128 %.2f GB, L~vv %.2f GB)" % (x2.numel() * 16 / 1e9, naux * v * v * 16 / 1e9)},
-            "roofline": {"kernel": "pp-ladder (formation + contraction)", "bound": bound,
+            "roofline": {"kernel": kernel, "bound": bound,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": how, "traffic": None,
-                         "ladder_ms": lad_ms, "ladder_share": lad_ms / (ms_max / args.steps)},
+                         "kernel_ms": form_ms if form_ms > 0 else lad_ms,
+                         "ladder_ms": lad_ms, "ladder_share": lad_ms / (ms_max / args.steps),
+                         "ladder_achieved": lad_achieved, "ladder_frac": lad_achieved / peak},
             "clocks": clk,
             "e2e": {"value": e2e, "unit": "sigma-vectors/s", "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
@@ -372,6 +417,8 @@ def run_cclr(args):
         }
         if tta is not None:
             out["time_to_alpha"] = tta
+        if tta_large is not None:
+            out["time_to_alpha_large"] = tta_large
         if batched is not None:
             out["batched"] = batched
         if cpu is not None:

@@ -141,9 +141,10 @@ cclr_status cc_lr_set_refinement(cclr_ctx *ctx, int prec);
 cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace, int max_iterations);
 
 /* Device-side timing (CUDA events on the context's stream) of the last sigma or
- * sigma^T vector, in milliseconds: [0] particle-particle ladder (formation of <ab|ef>~
- * from L~_vv and its contraction with X), [1] every other kernel, [2] total. */
-cclr_status cc_lr_last_timings(cclr_ctx *ctx, double *ms3);
+ * sigma^T product, in milliseconds; writes the first min(n, 4) of: [0] particle-particle
+ * ladder (formation of <ab|ef>~ from L~_vv and its contraction with X), [1] every other
+ * kernel, [2] total, [3] the ladder's formation GEMMs alone (tensor-core modes; 0 otherwise). */
+cclr_status cc_lr_last_timings(cclr_ctx *ctx, double *ms, int n);
 
 void cc_lr_free(cclr_ctx *ctx);
 const char *cc_lr_strerror(cclr_status status);

@@ -65,7 +65,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_get_t": [P, P, P],
         "cc_lr_set_precision": [P, I],
         "cc_lr_set_solver": [P, I, I],
-        "cc_lr_last_timings": [P, P],
+        "cc_lr_last_timings": [P, P, I],
         "cc_lr_free": [P],
         "cc_lr_strerror": [I],
         "cc_lr_last_error": [],
@@ -233,8 +233,9 @@ class Context:
         _check(load().cc_lr_set_solver(self._h, m, int(subspace), int(max_iterations)))
 
     def cc_lr_last_timings(self):
-        out = np.zeros(3, dtype=np.float64)
-        _check(load().cc_lr_last_timings(self._h, _ptr(out)))
+        """[ladder, everything else, total, ladder formation GEMMs] of the last product (ms)."""
+        out = np.zeros(4, dtype=np.float64)
+        _check(load().cc_lr_last_timings(self._h, _ptr(out), 4))
         return out
 
 

@@ -779,9 +779,9 @@ cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace, int max_iter
   return CCLR_OK;
 }
 
-cclr_status cc_lr_last_timings(cclr_ctx *c, double *ms3) {
-  if (!c || !ms3) return (cclr_status)fail(CCLR_EINVAL, "bad timings arguments");
-  for (int k = 0; k < 3; ++k) ms3[k] = c->M->ms_last[k];
+cclr_status cc_lr_last_timings(cclr_ctx *c, double *ms, int n) {
+  if (!c || !ms || n < 0) return (cclr_status)fail(CCLR_EINVAL, "bad timings arguments");
+  for (int k = 0; k < n && k < 4; ++k) ms[k] = c->M->ms_last[k];
   return CCLR_OK;
 }
 

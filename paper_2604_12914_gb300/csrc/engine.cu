@@ -213,7 +213,9 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
       (tc_force || ((double)M * N * K >= 3.0e7 && M >= 16 && K >= 8))) {
     // the tensor-core tile is 128 rows high and up to 256 columns wide: a short M side
     // goes to the columns (C^T = B^T A^T)
-    if (M < 128 && N > M)
+    // and, when the contraction is short in K (memory-bound), the larger operand goes to the
+    // row side, which is read as is (the column side is stored twice as large, embedded)
+    if ((M < 128 && N > M) || (N > M && K <= 2048))
       contract_tc(alpha, B, mb, A, ma, C, mc, bat, Nm, Mm, Km, nb, N, M, K);
     else
       contract_tc(alpha, A, ma, B, mb, C, mc, bat, Mm, Nm, Km, nb, M, N, K);
@@ -323,11 +325,19 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
                  direct ? "" : "(temporary)");
   float *Ao = (float *)ws(3, (size_t)M * ld * 4);
   float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
+  // TF32 reads A in place when its K index is contiguous and its rows are one strided level
+  const bool a_direct = seg == 1 && ak.sin == 1 && ak.din == TC_ONE_LEVEL && am.din == TC_ONE_LEVEL &&
+                        (M == 1 || tc_a_inplace_ok(Ap, am.sin, K)) && (nb == 1 || (a0 * es) % 16 == 0);
   for (int64_t b = 0; b < nb; ++b) {
-    tc_prep_a2((const char *)Ap + b * a0 * es, am, ak, M, K, seg, Ao, ld, st);
+    const void *Ab = (const char *)Ap + b * a0 * es;
+    const bool ad = a_direct && tc_a_inplace_ok(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K);
+    if (!ad) tc_prep_a2(Ab, am, ak, M, K, seg, Ao, ld, st);
     tc_prep_b2((const char *)Bp + b * b0 * es, bk, bn, K, N, seg, Bo, ld, st);
     float *Cp = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
-    tc_gemm_seg_v(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, cm, cn, alpha, direct, st);
+    if (ad)
+      tc_gemm_a_inplace(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K, Bo, ld, M, 2 * N, Cp, cm, cn, alpha, direct, st);
+    else
+      tc_gemm_seg_v(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, cm, cn, alpha, direct, st);
     ++tc_calls;
   }
   if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);

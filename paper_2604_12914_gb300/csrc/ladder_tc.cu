@@ -189,6 +189,7 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   if (Xp.bytes < xp_bytes) Xp.alloc(xp_bytes);
   if (sig.bytes < (size_t)Po * Pv * NR * 8) sig.alloc((size_t)Po * Pv * NR * 8);
   const int2 *op = opairs.as<int2>(), *vp = vpairs.as<int2>();
+  nform_ = 0;
   if (dir > 0) {
     for (int64_t r = 0; r < NR; ++r) {
       pack_x_b<<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
@@ -204,8 +205,16 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
     if (np == 0) continue;
     // formation: W[(b - a0, f)][(a - a0, e)] = sum_P L[P,b,f] L[P,a,e], b >= a0
     const int64_t rows = (int64_t)(v - a0) * v, cols = (int64_t)(a1 - a0) * v;
+    if ((int)fev.size() < 2 * (nform_ + 1)) {
+      fev.resize(2 * (nform_ + 1), nullptr);
+      for (auto &e : fev)
+        if (!e) CCLR_CUDA(cudaEventCreate(&e));
+    }
+    CCLR_CUDA(cudaEventRecord(fev[2 * nform_], st));
     tc_gemm_seg(LA.as<float>() + (int64_t)a0 * v * ldL, ldL, LB.as<float>() + 2 * (int64_t)a0 * v * ldL, ldL,
                 rows, 2 * cols, ldL / seg, seg, W.as<float>(), 2 * cols, zc(1.0), false, st);
+    CCLR_CUDA(cudaEventRecord(fev[2 * nform_ + 1], st));
+    ++nform_;
     if (dir > 0) {
       pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
                                                 Wp.as<float>(), ldPv);
@@ -240,6 +249,16 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
     count_launch();
   }
   CCLR_CUDA(cudaGetLastError());
+}
+
+float LadderTC::formation_ms() {
+  float tot = 0.f;
+  for (int g = 0; g < nform_; ++g) {
+    float ms = 0.f;
+    CCLR_CUDA(cudaEventElapsedTime(&ms, fev[2 * g], fev[2 * g + 1]));
+    tot += ms;
+  }
+  return tot;
 }
 
 }  // namespace cclr

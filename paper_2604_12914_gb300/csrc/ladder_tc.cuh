@@ -6,6 +6,8 @@
 // antisymmetrise/pack to <ab||ef>~ over (a<b) x (e<f), contraction GEMM with packed X.
 // The transpose product (dir -1) contracts the same packed block over (a<b) instead.
 #pragma once
+#include <vector>
+
 #include "engine.cuh"
 
 namespace cclr {
@@ -19,6 +21,8 @@ class LadderTC {
   // r = 0..nrhs-1, all complex64 [o][o][v][v].  Each <ab||ef>~ group block is formed once
   // and contracted with every right-hand side.
   void apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out);
+  // device time (ms) of the formation GEMMs of the last apply(); call once its work has completed
+  float formation_ms();
 
  private:
   int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0;
@@ -27,6 +31,8 @@ class LadderTC {
   DevBuf opairs, vpairs;    // pair tables (p, q), p < q, row-major pair order
   DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result
   int ga_ = 32;             // a values per group
+  std::vector<cudaEvent_t> fev;  // formation start/stop events, two per group
+  int nform_ = 0;                // groups timed in the last apply()
 };
 
 }  // namespace cclr

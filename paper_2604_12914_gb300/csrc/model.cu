@@ -386,7 +386,7 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
     for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
     tm.made = true;
   }
-  float lad_ms = 0.f;
+  float lad_ms = 0.f, form_ms = 0.f;
   auto run_ladder = [&](int d, zc a, int in_id, int out_id) {
     std::vector<Tens> in(nr), out(nr);
     for (int r = 0; r < nr; ++r) { in[r] = V(r, in_id); out[r] = V(r, out_id); }
@@ -397,6 +397,7 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
     float ms = 0.f;
     CCLR_CUDA(cudaEventElapsedTime(&ms, tm.ev[1], tm.ev[2]));
     lad_ms += ms;
+    if (dt == C64 && E.tc_mode) form_ms += ltc[E.tc_mode == 2 ? 1 : 0].formation_ms();
   };
   CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
   if (dir > 0) {
@@ -466,6 +467,7 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
   ms_last[0] = lad_ms;
   ms_last[1] = tot - lad_ms;
   ms_last[2] = tot;
+  ms_last[3] = form_ms;
   if (E.tc_mode && tc_error(st)) throw Error(5, "a tensor-core kernel gave up on a bounded wait");
 }
 

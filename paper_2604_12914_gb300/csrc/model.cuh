@@ -79,7 +79,7 @@ class Model {
   DevBuf ladW;                      // ladder formation scratch (CUDA-core path)
   LadderTC ltc[2];                  // packed tensor-core ladder: [0] TF32, [1] 3xTF32
   const void *ltc_src[2] = {nullptr, nullptr};
-  float ms_last[3] = {0, 0, 0};   // last apply(): ladder, everything else, total (ms)
+  float ms_last[4] = {0, 0, 0, 0};  // last apply(): ladder, everything else, total, ladder formation (ms)
   Timers tm;
 
   void upload_inputs(const double *eps_h, const double *L, const double *mu_h,

@@ -595,16 +595,17 @@ void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, in
   tc_prep_b2(B, view1(sbk), view1(sbn), K, N, seg, dst, ldd, st);
 }
 
+// a_cols: real columns A actually holds per row (<= Kreal; the rest reads as zero)
 static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                          int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
-                         int max_kb_per_split, int *err, cudaStream_t st) {
+                         int max_kb_per_split, int *err, cudaStream_t st, int64_t a_cols = -1) {
   if (M <= 0 || Nreal <= 0) return;
   CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
   CCLR_REQUIRE(lda % 4 == 0 && ldb % 4 == 0, "tc_gemm: leading dimensions must be multiples of 16 bytes");
   CCLR_REQUIRE(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, "tc_gemm: operands must be 16-byte aligned");
   CCLR_REQUIRE(M < (1ll << 31) && Nreal < (1ll << 31) && Kreal < (1ll << 31), "tc_gemm: dimension too large");
   const int BN = pick_bn(Nreal);
-  const CUtensorMap ma = make_map(A, M, Kreal, lda, BM);
+  const CUtensorMap ma = make_map(A, M, a_cols < 0 ? Kreal : a_cols, lda, BM);
   const CUtensorMap mb = make_map(B, Nreal, Kreal, ldb, BN);
   TcParams p;
   p.M = (int)M;
@@ -683,6 +684,17 @@ void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int
   }
   tc_gemm_impl(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, rv, cv, alpha, accumulate, 64, st);
   tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, true, 64, st);
+}
+
+void tc_gemm_a_inplace(const void *A, int64_t lda_cpx, int64_t K, const float *B, int64_t ldb, int64_t M,
+                       int64_t Nreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st) {
+  std::call_once(g_once, init_once);
+  tc_gemm_core((const float *)A, 2 * lda_cpx, B, ldb, M, Nreal, 2 * tc_kpad(K), C, rv, cv, alpha, accumulate, 0,
+               g_err, st, 2 * K);
+}
+
+bool tc_a_inplace_ok(const void *A, int64_t lda_cpx, int64_t K) {
+  return ((uintptr_t)A % 16) == 0 && lda_cpx % 2 == 0 && lda_cpx >= K && 8 * lda_cpx < (1ll << 40);
 }
 
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,

@@ -60,6 +60,13 @@ void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M
 void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                  int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
                  cudaStream_t st);
+// TF32 GEMM whose A is read in place: complex64 rows of K contiguous elements, lda_cpx complex
+// elements apart (no prepared copy; TF32 needs no split of A).  tc_a_inplace_ok tells whether
+// the TMA rules allow it (16-byte aligned base, row pitch a multiple of 16 bytes).
+bool tc_a_inplace_ok(const void *A, int64_t lda_cpx, int64_t K);
+void tc_gemm_a_inplace(const void *A, int64_t lda_cpx, int64_t K, const float *B, int64_t ldb, int64_t M,
+                       int64_t Nreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st);
+
 // The same GEMM for callers that hold their own device error flag (it must start at zero;
 // a bounded wait that gives up sets it to 1).  Neither function allocates device memory:
 // tc_setup_device_flagged fetches the tensor-map encoder and raises the kernel's dynamic
