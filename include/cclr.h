@@ -123,6 +123,22 @@ cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
 /* Switch the arithmetic of subsequent sigma / sigma^T / solves. */
 cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
 
+/* CUDA graphs for the sigma / sigma^T programs (off by default).  On: a product whose
+ * arguments (direction, precision, constant set, buffer addresses) repeat those of the
+ * previous product, with no device memory freed and no constants rebuilt in between, is
+ * captured once into a CUDA graph (thread-local capture on the context's stream) and later
+ * products with those arguments replay it with one cudaGraphLaunch; the solvers' products
+ * qualify after their first iterations.  Freeing memory or rebuilding constants invalidates
+ * the captured graphs.  While a graph is replayed, cc_lr_last_timings reports the total only
+ * (the other entries are -1).  If a capture fails the context turns graphs off and stays
+ * eager.  Off: every product is issued kernel by kernel (and cached graphs are destroyed).
+ * Needs a context created with its own stream (not the default stream): CCLR_EUNSUPPORTED
+ * otherwise. */
+cclr_status cc_lr_set_graphs(cclr_ctx *ctx, int on);
+
+/* Number of graph captures and graph launches made by the context so far. */
+cclr_status cc_lr_graph_stats(cclr_ctx *ctx, int *captures, int *launches);
+
 /* Arithmetic of the mixed modes' accurate sigma products: the residual of every refinement
  * step, the polish that finishes a refinement which stalls, and the sigma^T products of the
  * F X stencil.  CCLR_FP64 (default): FP64 on CUDA cores; CCLR_C64_3XTF32: complex64 with

@@ -21,7 +21,8 @@ CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32 = range(4)
 PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32}
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
-           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_solver",
+           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
+           "cc_lr_graph_stats", "cc_lr_set_solver",
            "cc_lr_last_timings",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
@@ -223,6 +224,16 @@ class Context:
     def cc_lr_set_precision(self, prec):
         p = PREC[prec] if isinstance(prec, str) else int(prec)
         _check(load().cc_lr_set_precision(self._h, p))
+
+    def cc_lr_set_graphs(self, on=True):
+        """Capture repeated sigma products in CUDA graphs and replay them."""
+        _check(load().cc_lr_set_graphs(self._h, 1 if on else 0))
+
+    def cc_lr_graph_stats(self):
+        """(graph captures, graph launches) so far."""
+        c, l = ctypes.c_int(0), ctypes.c_int(0)
+        _check(load().cc_lr_graph_stats(self._h, ctypes.byref(c), ctypes.byref(l)))
+        return c.value, l.value
 
     def cc_lr_set_refinement(self, prec="fp64"):
         """Arithmetic of the refinement residuals and F X stencils: "fp64" or "3xtf32"."""

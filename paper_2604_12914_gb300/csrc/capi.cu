@@ -85,6 +85,7 @@ struct cclr_ctx {
 
   // the same for nr vectors at once (the ladder's integral blocks are formed once for all)
   std::vector<DevBuf> x64, s64;   // complex64 copies for the mixed-precision sigma
+  std::vector<DevBuf> x128, s128; // fixed staging of FP64 sigma arguments when graphs are on
   void op_batch(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set = nullptr) {
     sigma_calls += nr;
     if (set == nullptr) set = &M->cst_for(M->prec);
@@ -95,6 +96,13 @@ struct cclr_ctx {
       x64.resize(nr);
       s64.resize(nr);
     }
+    // with CUDA graphs on, FP64 arguments go through fixed buffers too, so that repeated
+    // products present the same addresses and replay one captured program
+    const bool stage128 = set->dt == C128 && M->graphs;
+    if (stage128 && (int)x128.size() < nr) {
+      x128.resize(nr);
+      s128.resize(nr);
+    }
     for (int r = 0; r < nr; ++r) {
       const void *x = xs[r];
       void *s = ss[r];
@@ -103,6 +111,11 @@ struct cclr_ctx {
         M->E.permute(zc(1), make_tens((void *)x, C128, {ntot()}), "a", make_tens(x64[r].p, C64, {ntot()}), "a", false);
         x = x64[r].p;
         s = s64[r].p;
+      } else if (stage128) {
+        if (!x128[r].p) { x128[r].alloc((size_t)ntot() * 16); s128[r].alloc((size_t)ntot() * 16); }
+        CCLR_CUDA(cudaMemcpyAsync(x128[r].p, x, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st));
+        x = x128[r].p;
+        s = s128[r].p;
       }
       a1[r] = x;
       a2[r] = (const char *)x + n1 * es;
@@ -113,6 +126,9 @@ struct cclr_ctx {
     if (set->dt == C64)
       for (int r = 0; r < nr; ++r)
         M->E.permute(zc(1), make_tens(s64[r].p, C64, {ntot()}), "a", make_tens(ss[r], C128, {ntot()}), "a", false);
+    else if (stage128)
+      for (int r = 0; r < nr; ++r)
+        CCLR_CUDA(cudaMemcpyAsync(ss[r], s128[r].p, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st));
   }
 
   // Solve (Op - omega) x = b.  FP64 mode: preconditioned DIIS.  Mixed modes: iterative
@@ -762,6 +778,24 @@ cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
     c->M->prec = prec;
     if (prec != CCLR_FP64) c->M->cst_for(prec);
   });
+}
+
+cclr_status cc_lr_set_graphs(cclr_ctx *c, int on) {
+  if (!c || (on != 0 && on != 1)) return (cclr_status)fail(CCLR_EINVAL, "graphs must be 0 or 1");
+  if (on && (c->st == nullptr || c->st == cudaStreamLegacy || c->st == cudaStreamPerThread))
+    return (cclr_status)fail(CCLR_EUNSUPPORTED, "CUDA graphs need a context created with its own (non-default) stream");
+  return (cclr_status)guarded([&] {
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+    c->M->graphs = on != 0;
+    if (!on) c->M->clear_graphs();
+  });
+}
+
+cclr_status cc_lr_graph_stats(cclr_ctx *c, int *captures, int *launches) {
+  if (!c || !captures || !launches) return (cclr_status)fail(CCLR_EINVAL, "bad graph_stats arguments");
+  *captures = c->M->graph_captures;
+  *launches = c->M->graph_launches;
+  return CCLR_OK;
 }
 
 cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {

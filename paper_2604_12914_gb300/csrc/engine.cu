@@ -14,6 +14,10 @@ static std::atomic<size_t> g_bytes_in_use{0};
 
 size_t device_bytes_in_use() { return g_bytes_in_use.load(); }
 
+static std::atomic<unsigned long long> g_epoch{1};
+unsigned long long state_epoch() { return g_epoch.load(); }
+void bump_state_epoch() { ++g_epoch; }
+
 void DevBuf::alloc(size_t b) {
   release();
   if (b == 0) return;
@@ -29,6 +33,7 @@ void DevBuf::alloc(size_t b) {
 
 void DevBuf::release() {
   if (p) {
+    ++g_epoch;
     cudaFree(p);
     g_bytes_in_use -= bytes;
   }

@@ -28,6 +28,10 @@ struct DevBuf {
 };
 
 size_t device_bytes_in_use();
+// Counter bumped whenever device memory is freed (and by callers that rewrite state a captured
+// CUDA graph depends on): a graph captured at one value is valid while the counter keeps it.
+unsigned long long state_epoch();
+void bump_state_epoch();
 
 class Engine {
  public:

@@ -21,7 +21,7 @@ Model::Model(int o_, int v_, int naux_, cudaStream_t st_)
   prog = build_sigma_program(o, v, naux);
 }
 
-Model::~Model() {}
+Model::~Model() { clear_graphs(); }
 
 static void h2d_or_d2d(void *dst, const void *src, size_t bytes, int device_ptrs, cudaStream_t st) {
   (void)device_ptrs;  // unified addressing: the copy direction follows from the pointers
@@ -236,6 +236,7 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
   E.tc_mode = tc_saved;
   for (int k = 0; k < 2; ++k)  // a ladder prepared from this buffer is stale
     if (ltc_src[k] == out.t[K_LVV].p) ltc_src[k] = nullptr;
+  bump_state_epoch();  // and so is any captured program that read the set
   out.valid = true;
 }
 
@@ -266,9 +267,11 @@ void Model::round_set(const CstSet &src, CstSet &dst) {
     E.permute(zc(1), s, m, d, m, false);
     dst.t[k] = d;
   }
-  // a tensor-core ladder prepared from this set's L~_vv (same buffer) is now stale
+  // a tensor-core ladder prepared from this set's L~_vv (same buffer) is now stale, and so is
+  // any captured program that read it
   for (int k = 0; k < 2; ++k)
     if (ltc_src[k] == dst.t[K_LVV].p) ltc_src[k] = nullptr;
+  bump_state_epoch();
   CCLR_CUDA(cudaStreamSynchronize(st));
   dst.valid = true;
 }
@@ -369,11 +372,9 @@ void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void
   apply_batch(dir, C, 1, &x1, &x2, &s1, &s2);
 }
 
-void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
-                        void *const *s1, void *const *s2) {
+void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
+                       void *const *s1, void *const *s2, bool timed, float &lad_ms, float &form_ms) {
   const int dt = C.dt;
-  // tensor cores for complex64: TF32 (prec 1) or 3xTF32 (prec 2); FP32 CUDA cores for prec 3
-  E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : 0) : 0;
   const int nv = (int)prog.vars.size();
   std::vector<std::vector<void *>> ptr(nr, std::vector<void *>(nv, nullptr));
   for (int r = 0; r < nr; ++r) {
@@ -382,14 +383,13 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
   }
   auto V = [&](int r, int id) { return var_tens(id, dt, ptr[r][id]); };
   auto Cst = [&](int id) { return C.t[id]; };
-  if (!tm.made) {
-    for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
-    tm.made = true;
-  }
-  float lad_ms = 0.f, form_ms = 0.f;
   auto run_ladder = [&](int d, zc a, int in_id, int out_id) {
     std::vector<Tens> in(nr), out(nr);
     for (int r = 0; r < nr; ++r) { in[r] = V(r, in_id); out[r] = V(r, out_id); }
+    if (!timed) {
+      ladder(d, C, a, in, out);
+      return;
+    }
     CCLR_CUDA(cudaEventRecord(tm.ev[1], st));
     ladder(d, C, a, in, out);
     CCLR_CUDA(cudaEventRecord(tm.ev[2], st));
@@ -399,7 +399,6 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
     lad_ms += ms;
     if (dt == C64 && E.tc_mode) form_ms += ltc[E.tc_mode == 2 ? 1 : 0].formation_ms();
   };
-  CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
   if (dir > 0) {
     for (int r = 0; r < nr; ++r) {
       ptr[r][0] = (void *)x1[r]; ptr[r][1] = (void *)x2[r]; ptr[r][2] = s1[r]; ptr[r][3] = s2[r];
@@ -460,6 +459,99 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
       E.permute(zc(1), z2, "ijab", out2, "jiba", true);
     }
   }
+}
+
+void Model::clear_graphs() {
+  for (auto &g : gcache)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  gcache.clear();
+  warm.clear();
+}
+
+void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
+                        void *const *s1, void *const *s2) {
+  const int dt = C.dt;
+  // tensor cores for complex64: TF32 (prec 1) or 3xTF32 (prec 2); FP32 CUDA cores for prec 3
+  E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : 0) : 0;
+  if (!tm.made) {
+    for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
+    tm.made = true;
+  }
+  GraphKey key;
+  if (graphs) {
+    key.dir = dir; key.dt = dt; key.tc = E.tc_mode; key.nr = nr; key.set = &C;
+    for (int r = 0; r < nr; ++r) {
+      key.ptrs.push_back(x1[r]); key.ptrs.push_back(x2[r]);
+      key.ptrs.push_back(s1[r]); key.ptrs.push_back(s2[r]);
+    }
+    const unsigned long long ep = state_epoch();
+    GraphEntry *hit = nullptr;
+    for (size_t g = 0; g < gcache.size(); ++g) {
+      if (!(gcache[g].key == key)) continue;
+      if (gcache[g].epoch == ep) {
+        hit = &gcache[g];
+      } else {  // memory it refers to was freed or constants rebuilt since the capture
+        cudaGraphExecDestroy(gcache[g].exec);
+        gcache.erase(gcache.begin() + g);
+      }
+      break;
+    }
+    bool was_warm = false;
+    for (const auto &w : warm)
+      if (w.key == key && w.epoch == ep) was_warm = true;
+    if (!hit && was_warm) {
+      // an eager call with these arguments ran since the last free or rebuild, so every buffer
+      // the program touches is allocated and prepared: capture
+      cudaGraph_t gr = nullptr;
+      float l = 0.f, f = 0.f;
+      CCLR_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+      bool body_ok = true;
+      try {
+        apply_body(dir, C, nr, x1, x2, s1, s2, false, l, f);
+      } catch (...) {
+        body_ok = false;  // nothing of a capture executes: the eager path below redoes it all
+      }
+      const cudaError_t ec = cudaStreamEndCapture(st, &gr);
+      cudaGraphExec_t ex = nullptr;
+      if (body_ok && ec == cudaSuccess && gr && state_epoch() == ep &&
+          cudaGraphInstantiate(&ex, gr, 0) == cudaSuccess) {
+        if (gcache.size() >= 8) {
+          cudaGraphExecDestroy(gcache.front().exec);
+          gcache.erase(gcache.begin());
+        }
+        GraphEntry e;
+        e.key = key;
+        e.exec = ex;
+        e.epoch = ep;
+        gcache.push_back(std::move(e));
+        hit = &gcache.back();
+        ++graph_captures;
+      } else {
+        (void)cudaGetLastError();
+        graphs = false;  // this program cannot be captured here: stay eager from now on
+        warm.clear();
+      }
+      if (gr) cudaGraphDestroy(gr);
+    }
+    if (hit) {
+      CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
+      CCLR_CUDA(cudaGraphLaunch(hit->exec, st));
+      CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
+      CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
+      float tot = 0.f;
+      CCLR_CUDA(cudaEventElapsedTime(&tot, tm.ev[0], tm.ev[3]));
+      ms_last[0] = -1.f;  // the split is not measured inside a graph
+      ms_last[1] = -1.f;
+      ms_last[2] = tot;
+      ms_last[3] = -1.f;
+      ++graph_launches;
+      if (E.tc_mode && tc_error(st)) throw Error(5, "a tensor-core kernel gave up on a bounded wait");
+      return;
+    }
+  }
+  float lad_ms = 0.f, form_ms = 0.f;
+  CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
+  apply_body(dir, C, nr, x1, x2, s1, s2, true, lad_ms, form_ms);
   CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
   CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
   float tot = 0.f;
@@ -469,6 +561,18 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
   ms_last[2] = tot;
   ms_last[3] = form_ms;
   if (E.tc_mode && tc_error(st)) throw Error(5, "a tensor-core kernel gave up on a bounded wait");
+  if (graphs) {
+    for (size_t w = 0; w < warm.size(); ++w)
+      if (warm[w].key == key) {
+        warm.erase(warm.begin() + w);
+        break;
+      }
+    if (warm.size() >= 8) warm.erase(warm.begin());
+    GraphEntry e;
+    e.key = key;
+    e.epoch = state_epoch();
+    warm.push_back(std::move(e));
+  }
 }
 
 // xi^B_ia = mu~_ai + sum_me mu~_me t_im^ae ;

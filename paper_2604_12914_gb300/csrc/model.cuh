@@ -53,6 +53,21 @@ struct Timers {
   bool made = false;
 };
 
+// A captured sigma / sigma^T program for one argument set (see Model::graphs).
+struct GraphKey {
+  int dir = 0, dt = 0, tc = 0, nr = 0;
+  const void *set = nullptr;
+  std::vector<const void *> ptrs;
+  bool operator==(const GraphKey &k) const {
+    return dir == k.dir && dt == k.dt && tc == k.tc && nr == k.nr && set == k.set && ptrs == k.ptrs;
+  }
+};
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long epoch = 0;
+};
+
 class Model {
  public:
   Model(int o, int v, int naux, cudaStream_t st);
@@ -81,6 +96,14 @@ class Model {
   const void *ltc_src[2] = {nullptr, nullptr};
   float ms_last[4] = {0, 0, 0, 0};  // last apply(): ladder, everything else, total, ladder formation (ms)
   Timers tm;
+  // CUDA graphs: with graphs on, a sigma program whose arguments (direction, constant set,
+  // precision, buffer addresses) repeat those of an earlier eager call, with no memory freed
+  // or constants rebuilt since, is captured once and then replayed by cudaGraphLaunch.
+  bool graphs = false;
+  std::vector<GraphEntry> gcache;
+  std::vector<GraphEntry> warm;  // recent eager calls (key, epoch after the call); no exec
+  int graph_launches = 0, graph_captures = 0;
+  void clear_graphs();
 
   void upload_inputs(const double *eps_h, const double *L, const double *mu_h,
                      const double *t1_h, const double *t2_h, int device_ptrs);
@@ -107,6 +130,9 @@ class Model {
 
  private:
   void ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &in, const std::vector<Tens> &out);
+  // the program itself; timed = event timing of the ladder (not while capturing)
+  void apply_body(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
+                  void *const *s1, void *const *s2, bool timed, float &lad_ms, float &form_ms);
   std::vector<DevBuf> &temps(int dt, int r);
   Tens var_tens(int id, int dt, void *p) const;
 };

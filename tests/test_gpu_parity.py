@@ -276,3 +276,54 @@ def test_bounded_wait_gives_up_and_context_survives():
     r1, r2 = oracle_sigma(s, t1, t2, x1, x2)
     assert rel_err(g1, g2, r1, r2) < 3e-3
     ctx.close()
+
+
+def _graph_context(s, prec, **kw):
+    from paper_2604_12914_gb300 import binding
+    stream = torch.cuda.Stream()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec, stream=stream.cuda_stream, **kw)
+    return ctx, stream
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32", 1e-5)])
+def test_graph_replay_matches_eager_sigma(prec, tol):
+    """CUDA-graph replay of the sigma and sigma^T programs gives the eager results (the second
+    identical product is captured, later ones replay it)."""
+    o, v, naux, seed, scale, t1s = CASES[2]
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx, stream = _graph_context(s, prec, t1=t1, t2=t2)
+    x1, x2 = random_amplitudes(o, v, seed=3)
+    e1, e2 = ctx.cc_lr_sigma(x1, x2)
+    f1, f2 = ctx.cc_lr_sigma_T(x1, x2)
+    ctx.cc_lr_set_graphs(True)
+    for _ in range(4):
+        g1, g2 = ctx.cc_lr_sigma(x1, x2)
+        assert rel_err(g1, g2, e1, e2) < tol
+        h1, h2 = ctx.cc_lr_sigma_T(x1, x2)
+        assert rel_err(h1, h2, f1, f2) < tol
+    caps, launches = ctx.cc_lr_graph_stats()
+    assert caps == 2 and launches >= 4, (caps, launches)
+    # a different input through the same buffers replays the same graph
+    y1, y2 = random_amplitudes(o, v, seed=4)
+    g1, g2 = ctx.cc_lr_sigma(y1, y2)
+    ctx.cc_lr_set_graphs(False)
+    r1, r2 = ctx.cc_lr_sigma(y1, y2)
+    assert rel_err(g1, g2, r1, r2) < tol
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32"])
+def test_graph_replay_solve_alpha(prec):
+    """alpha with every solver product replayed from CUDA graphs matches the oracle."""
+    s, P = _converged_small()
+    ctx, stream = _graph_context(s, prec, t1=P.t1.numpy(), t2=P.t2.numpy())
+    ctx.cc_lr_set_graphs(True)
+    al, st = ctx.cc_lr_solve([0.0428], (0, 1, 2), tol=1e-8)
+    ref = R.alpha(P, [as_t(m) for m in s.mu], 0.0428).numpy()
+    err = np.abs(al[0] - ref).max()
+    caps, launches = ctx.cc_lr_graph_stats()
+    print(f"{prec}: |delta alpha| {err:.2e}, graph captures {caps}, launches {launches}, {st}")
+    assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
+    assert launches > caps > 0
+    ctx.close()
