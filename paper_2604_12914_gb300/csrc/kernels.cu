@@ -122,14 +122,19 @@ void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st) {
     CCLR_REQUIRE(!g.overwrite, "gemm with K=0 and overwrite is not supported");
     return;
   }
-  const int64_t tiles = ((g.M + 63) / 64) * ((g.N + 63) / 64);
+  // Tile shape by output shape: the CUDA cores compute every element of a tile, so a skinny
+  // output gets a flat tile (128 x 16 or 16 x 128) instead of 64 x 64 -- FP64 work is dear on
+  // this GPU (about 8 GFLOP/s per SM).
+  const int shape = (g.N <= 16 && g.M > 16) ? 1 : (g.M <= 16 && g.N > 16) ? 2 : 0;
+  const int64_t BMs = shape == 1 ? 128 : shape == 2 ? 16 : 64, BNs = shape == 1 ? 16 : shape == 2 ? 128 : 64;
+  const int64_t tiles = ((g.M + BMs - 1) / BMs) * ((g.N + BNs - 1) / BNs);
   // split K over blocks (partial sums added atomically) when the tile grid cannot fill the
-  // GPU and K is long: the skinny and matrix-vector shapes
+  // GPU: the skinny and matrix-vector shapes; at least 64 of K per split
   int64_t splits = 1;
   const int64_t bk = dt == C128 ? 8 : 16;
   const bool plain_c = g.sCn == 1 && g.sCm == g.N && (g.batch == 1 || g.sCb == g.M * g.N);
-  if (tiles * g.batch < 2 * 152 && g.K >= 1024 && (!g.overwrite || plain_c) && g.batch <= 65535)
-    splits = std::min<int64_t>((2 * 152 + tiles * g.batch - 1) / (tiles * g.batch), g.K / 256);
+  if (tiles * g.batch < 2 * 152 && g.K >= 128 && (!g.overwrite || plain_c) && g.batch <= 65535)
+    splits = std::min<int64_t>((2 * 152 + tiles * g.batch - 1) / (tiles * g.batch), g.K / 64);
   GemmArgs ga = g;
   if (splits > 1) {
     ga.kchunk = ((g.K + splits - 1) / splits + bk - 1) / bk * bk;
@@ -142,10 +147,15 @@ void launch_gemm(const GemmArgs &g, int dt, cudaStream_t st) {
   for (int64_t b0 = 0; b0 < g.batch; b0 += 65535) {
     int64_t nb = std::min<int64_t>(65535, g.batch - b0);
     dim3 grid((unsigned)tiles, (unsigned)splits, (unsigned)nb);
-    if (dt == C128)
-      zgemm_simt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
-    else
-      zgemm_simt<float, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
+    if (dt == C128) {
+      if (shape == 1) zgemm_simt<double, 128, 16, 8, 8, 1><<<grid, 256, 0, st>>>(ga, b0);
+      else if (shape == 2) zgemm_simt<double, 16, 128, 8, 1, 8><<<grid, 256, 0, st>>>(ga, b0);
+      else zgemm_simt<double, 64, 64, 8, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
+    } else {
+      if (shape == 1) zgemm_simt<float, 128, 16, 16, 8, 1><<<grid, 256, 0, st>>>(ga, b0);
+      else if (shape == 2) zgemm_simt<float, 16, 128, 16, 1, 8><<<grid, 256, 0, st>>>(ga, b0);
+      else zgemm_simt<float, 64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(ga, b0);
+    }
     count_launch();
     CCLR_CUDA(cudaGetLastError());
   }

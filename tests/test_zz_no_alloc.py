@@ -1,9 +1,10 @@
 """cc_lr_selftest_gemm_noalloc: the tensor-core GEMM self-test run inside the library's fixed
 device array, with no device allocation, against the allocating cc_lr_selftest_gemm.
 
-Both compute the same products from the same seeded inputs; the FP32 CUDA-core products are
-deterministic and must agree to the last bit, the tensor-core ones (split-K passes add
-partial tiles with atomics) within the tolerance the tensor-core self-test uses.  The
+Both compute the same products from the same seeded inputs.  Short products split K over
+blocks whose partial sums are added with atomics, in an order that varies from run to run, so
+the two agree within the tolerances of the GEMM self-test (tensor cores: 4e-3 for TF32,
+1e-8 K + 2e-6 for 3xTF32; FP32 CUDA cores: 2e-5), not to the last bit.  The
 entry point is called twice in a row, so the second call checks that the shared array is
 cleared where it must be.  The file is named to be collected last: the first call on the
 device does the set-up, and it must work both in a fresh process and after every other test.
@@ -34,7 +35,8 @@ def test_noalloc_matches_allocating_selftest(M, N, K, mode):
               f"fp32 {e_fp32:.3e} (allocating {ref_fp32:.3e})")
         assert 0 <= e_tc < tol
         assert abs(e_tc - ref_tc) <= tol
-        assert e_fp32 == ref_fp32
+        assert 0 <= e_fp32 < 2e-5
+        assert abs(e_fp32 - ref_fp32) <= 2e-5
 
 
 def test_noalloc_rejects_sizes_beyond_the_array():
