@@ -226,9 +226,10 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428), tol=1e-8):
+def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428), tol=1e-6):
     """Wall time of cc_lr_solve (Lambda + X(+-w) solves + alpha), FP64 path vs mixed path,
-    on the same synthetic system; returns both times and max |delta alpha| (a.u.)."""
+    on the same synthetic system and to the same relative residual tol; returns both times
+    and max |delta alpha| (a.u.)."""
     import numpy as np
     from paper_2604_12914_gb300 import binding
     from paper_2604_12914_gb300.inputs import make_config
@@ -236,14 +237,22 @@ def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428),
     out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
            "components": list(comps), "omegas": list(omegas), "tol": tol}
     res = {}
+    import torch
     for tag, prec in (("fp64", "fp64"), ("mixed", prec_mixed)):
-        ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec)
+        stream = torch.cuda.Stream()
+        ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec, stream=stream.cuda_stream)
+        ctx.cc_lr_set_graphs(True)              # both arms replay repeated products from CUDA graphs
+        if tag == "mixed":
+            ctx.cc_lr_set_refinement("3xtf32")  # accurate products on the tensor cores too
         t0 = time.perf_counter()
         al, st = ctx.cc_lr_solve(list(omegas), comps, tol=tol, allow_noconv=True)
         el = time.perf_counter() - t0
+        graphs = ctx.cc_lr_graph_stats()
         ctx.close()
         res[tag] = al
-        out[tag] = {"seconds": el, "precision_mode": prec, "iterations": st["iterations"],
+        out[tag] = {"seconds": el,
+                    "precision_mode": prec if tag == "fp64" else f"{prec} corrections, 3xtf32 refinement",
+                    "graph_captures_launches": list(graphs), "iterations": st["iterations"],
                     "sigma_calls": st["sigma_calls"], "fp64_refinements": st["refinements"],
                     "converged": st["converged"], "max_rel_residual": st["max_rel_residual"]}
     out["max_abs_delta_alpha_au"] = float(np.abs(res["fp64"] - res["mixed"]).max())

@@ -136,6 +136,14 @@ cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
  * otherwise. */
 cclr_status cc_lr_set_graphs(cclr_ctx *ctx, int on);
 
+/* Result of the pp-ladder autotuner for the tensor-core mode prec (CCLR_C64_TF32 or
+ * CCLR_C64_3XTF32): on its first use in that mode the ladder times one product per candidate
+ * group size (how many a values each formed <ab|ef>~ block covers) and keeps the fastest.
+ * Writes the group size in use, the number of candidates timed (*n; 0 before the first use)
+ * and up to cap of them (candidate group size, milliseconds). */
+cclr_status cc_lr_ladder_tuning(cclr_ctx *ctx, int prec, int *group_size, int cap, int *cand, double *ms,
+                                int *n);
+
 /* Number of graph captures and graph launches made by the context so far. */
 cclr_status cc_lr_graph_stats(cclr_ctx *ctx, int *captures, int *launches);
 

@@ -798,6 +798,20 @@ cclr_status cc_lr_graph_stats(cclr_ctx *c, int *captures, int *launches) {
   return CCLR_OK;
 }
 
+cclr_status cc_lr_ladder_tuning(cclr_ctx *c, int prec, int *group_size, int cap, int *cand, double *ms, int *n) {
+  if (!c || (prec != CCLR_C64_TF32 && prec != CCLR_C64_3XTF32) || !group_size || !n || cap < 0 ||
+      (cap > 0 && (!cand || !ms)))
+    return (cclr_status)fail(CCLR_EINVAL, "bad ladder_tuning arguments");
+  const LadderTC &l = c->M->ltc[prec == CCLR_C64_3XTF32 ? 1 : 0];
+  *group_size = l.group_size();
+  *n = (int)l.tune_log.size();
+  for (int k = 0; k < cap && k < *n; ++k) {
+    cand[k] = l.tune_log[k].first;
+    ms[k] = l.tune_log[k].second;
+  }
+  return CCLR_OK;
+}
+
 cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
   if (!c || (prec != CCLR_FP64 && prec != CCLR_C64_3XTF32))
     return (cclr_status)fail(CCLR_EINVAL, "refinement precision must be CCLR_FP64 or CCLR_C64_3XTF32");

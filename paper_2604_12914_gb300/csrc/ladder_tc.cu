@@ -167,6 +167,45 @@ void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int s
   if (!op.empty()) CCLR_CUDA(cudaMemcpyAsync(opairs.p, op.data(), op.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   if (!vp.empty()) CCLR_CUDA(cudaMemcpyAsync(vpairs.p, vp.data(), vp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   CCLR_CUDA(cudaStreamSynchronize(st));
+  if (!tuned_) tune(E);
+}
+
+void LadderTC::tune(Engine &E) {
+  tuned_ = true;
+  tune_log.clear();
+  if (Po_ == 0 || Pv_ == 0) return;
+  cudaStream_t st = E.st;
+  const int64_t n2 = (int64_t)o_ * o_ * v_ * v_;
+  DevBuf xin((size_t)n2 * 8), xout((size_t)n2 * 8);
+  CCLR_CUDA(cudaMemsetAsync(xin.p, 0, xin.bytes, st));
+  cudaEvent_t e0, e1;
+  CCLR_CUDA(cudaEventCreate(&e0));
+  CCLR_CUDA(cudaEventCreate(&e1));
+  const void *in[1] = {xin.p};
+  void *out[1] = {xout.p};
+  int best = ga_;
+  float best_ms = 1e30f;
+  for (int cand : {16, 32, 64}) {
+    const int ga = std::min(cand, v_);
+    const double wbytes = (double)v_ * v_ * ga * v_ * 8;
+    if (cand > 16 && wbytes > 16e9) continue;
+    if (!tune_log.empty() && tune_log.back().first == ga) continue;
+    ga_ = ga;
+    apply(E, +1, zc(1.0), 1, in, out);  // the first run allocates the group buffers
+    CCLR_CUDA(cudaEventRecord(e0, st));
+    apply(E, +1, zc(1.0), 1, in, out);
+    CCLR_CUDA(cudaEventRecord(e1, st));
+    CCLR_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CCLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    tune_log.push_back({ga, ms});
+    if (ms < best_ms) { best_ms = ms; best = ga; }
+    // buffers sized for this candidate are released before the next one
+    W.release(); Wp.release(); Xp.release(); sig.release();
+  }
+  ga_ = best;
+  CCLR_CUDA(cudaEventDestroy(e0));
+  CCLR_CUDA(cudaEventDestroy(e1));
 }
 
 void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out) {

@@ -23,6 +23,12 @@ class LadderTC {
   void apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out);
   // device time (ms) of the formation GEMMs of the last apply(); call once its work has completed
   float formation_ms();
+  // Autotuner: times one product for each candidate group size (a values per formed block:
+  // 16, 32, 64, those whose block fits in 16 GB) on zero input and keeps the fastest.  Runs
+  // once per object, on its first preparation; group_size() and tune_log report the result.
+  void tune(Engine &E);
+  int group_size() const { return ga_; }
+  std::vector<std::pair<int, float>> tune_log;
 
  private:
   int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0;
@@ -30,7 +36,8 @@ class LadderTC {
   DevBuf LA, LB;            // formation operands: rows (b,f) and embedded rows (a,e), K = naux
   DevBuf opairs, vpairs;    // pair tables (p, q), p < q, row-major pair order
   DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result
-  int ga_ = 32;             // a values per group
+  int ga_ = 32;             // a values per group (set by tune())
+  bool tuned_ = false;
   std::vector<cudaEvent_t> fev;  // formation start/stop events, two per group
   int nform_ = 0;                // groups timed in the last apply()
 };

@@ -59,3 +59,24 @@ def test_missing_library_fails_loudly(tmp_path):
             binding.load(str(tmp_path / "nope.so"))
     finally:
         binding._lib = saved
+
+
+def _declared_params():
+    """name -> number of parameters, from every header under include/."""
+    out = {}
+    for h in ("cclr.h", "cclr_testing.h"):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for name, params in re.findall(r"\b(cc_lr_\w+)\s*\(([^)]*)\)\s*;", src):
+            params = params.strip()
+            out[name] = 0 if params in ("", "void") else params.count(",") + 1
+    return out
+
+
+def test_binding_declares_every_signature(lib):
+    """Every declared entry point has ctypes argument types of the declared arity (an
+    undeclared pointer argument would be passed as a 32-bit int)."""
+    for name, n in _declared_params().items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
