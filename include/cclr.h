@@ -158,8 +158,12 @@ cclr_status cc_lr_set_refinement(cclr_ctx *ctx, int prec);
 /* Linear solver of cc_lr_solve / cc_lr_solve_x / cc_lr_lambda: method 1 = restarted
  * GMRES with the diagonal preconditioner (default; subspace = restart length),
  * method 0 = DIIS extrapolation of preconditioned Jacobi steps (subspace ignored; the
- * calls' diis_depth applies).  In the mixed modes either method solves the corrections
- * of the FP64-residual iterative refinement.  max_iterations bounds the sigma products of
+ * calls' diis_depth applies), method 2 = block GMRES: cc_lr_solve advances the X systems of
+ * all its components and frequency signs in lockstep, so every iteration applies the operator
+ * to all unconverged systems in one batched product (the ladder's integral blocks formed once
+ * for all); each system keeps its own GMRES, the restart length shrinks when the bases would not
+ * fit in half of the free device memory, and single-system solves use method 1.  In the mixed
+ * modes every method solves the corrections of the iterative refinement.  max_iterations bounds the sigma products of
  * each linear solve (default 300; 0 keeps the current value); a solve that reaches it
  * returns CCLR_ENOCONV with its best iterate. */
 cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace, int max_iterations);

@@ -253,7 +253,7 @@ class Context:
         _check(load().cc_lr_set_refinement(self._h, PREC[prec] if isinstance(prec, str) else int(prec)))
 
     def cc_lr_set_solver(self, method="gmres", subspace=30, max_iterations=0):
-        m = {"gmres": 1, "diis": 0}[method] if isinstance(method, str) else int(method)
+        m = {"gmres": 1, "diis": 0, "block": 2}[method] if isinstance(method, str) else int(method)
         _check(load().cc_lr_set_solver(self._h, m, int(subspace), int(max_iterations)))
 
     def cc_lr_last_timings(self):

@@ -200,13 +200,13 @@ struct cclr_ctx {
   }
 
   // Krylov method of the linear solves: 1 = restarted GMRES (default), 0 = DIIS.
-  int method = 1;
+  int method = 1;  // 1 GMRES, 0 DIIS, 2 block GMRES over the right-hand sides of cc_lr_solve
   int krylov = 30;
   int maxit = 300;  // iterations per linear solve, all precisions together
 
   double solve_diis(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
                     int *its, bool warm = false) {
-    if (method == 1) return solve_gmres(dir, omega, b, x, tol, krylov, maxit, its, warm);
+    if (method >= 1) return solve_gmres(dir, omega, b, x, tol, krylov, maxit, its, warm);
     return solve_pulay(dir, omega, b, x, tol, depth, maxit, its, warm);
   }
 
@@ -305,6 +305,284 @@ struct cclr_ctx {
     }
     CCLR_CUDA(cudaStreamSynchronize(st));
     return rel;
+  }
+
+  struct BlockSys {
+    std::vector<AVec> V;  // Krylov basis
+    AVec z, w;
+    std::vector<zd> H, cs, sn, g;
+    double bn = 1.0;
+    int j = 0;
+    bool done = false, cyc = false;
+  };
+  std::vector<BlockSys> blk;
+
+  // Block solve: nr independent systems (Op - omega_r) x_r = b_r advanced in lockstep, so that
+  // each iteration applies the operator to every unconverged system in one batched product
+  // (the ladder's <ab||ef>~ blocks are formed once per iteration for all of them).  Each system
+  // keeps its own restarted, right-preconditioned GMRES (the method of solve_gmres); rel[r]
+  // receives its final relative residual, its[r] its iteration count.
+  void gmres_block(int dir, const std::vector<double> &om, const std::vector<const void *> &b,
+                   const std::vector<void *> &x, const std::vector<double> &tol, int m, int maxit,
+                   std::vector<int> &its, std::vector<double> &rel, bool warm) {
+    const int nr = (int)b.size();
+    its.assign(nr, 0);
+    rel.assign(nr, 1.0);
+    if (nr == 0) return;
+    m = std::max(2, std::min(m, 100));
+    if ((int)blk.size() < nr) blk.resize(nr);  // kept between calls (no reallocation per solve)
+    auto &S = blk;
+    for (int r = 0; r < nr; ++r) {
+      BlockSys &q = S[r];
+      if ((int)q.V.size() < m + 1) q.V.resize(m + 1);
+      for (int k = 0; k <= m; ++k) alloc_vec(q.V[k]);
+      q.done = false;
+      q.cyc = false;
+      q.j = 0;
+      alloc_vec(q.z);
+      alloc_vec(q.w);
+      q.H.assign((size_t)(m + 1) * m, zd(0));
+      q.cs.assign(m, zd(0));
+      q.sn.assign(m, zd(0));
+      q.g.assign(m + 1, zd(0));
+      q.bn = std::max(norm(b[r]), 1e-300);
+      if (!warm) CCLR_CUDA(cudaMemsetAsync(x[r], 0, (size_t)ntot() * 16, st));
+    }
+    int used = 0;
+    std::vector<int> act;
+    std::vector<const void *> in;
+    std::vector<void *> out;
+    auto batch = [&](const std::vector<int> &ids, bool from_x) {
+      in.clear();
+      out.clear();
+      for (int r : ids) {
+        in.push_back(from_x ? (const void *)x[r] : (const void *)S[r].z.b.p);
+        out.push_back(S[r].w.b.p);
+      }
+      if (!ids.empty()) op_batch(dir, (int)ids.size(), in.data(), out.data());
+    };
+    while (used < maxit) {
+      // true residuals of the systems still running
+      act.clear();
+      for (int r = 0; r < nr; ++r)
+        if (!S[r].done) act.push_back(r);
+      if (act.empty()) break;
+      for (int r : act) copy(b[r], S[r].V[0].b.p);
+      if (warm || used > 0) {
+        batch(act, true);
+        for (int r : act) {
+          axpy(zd(-1), S[r].w.b.p, S[r].V[0].b.p);
+          axpy(zd(om[r]), x[r], S[r].V[0].b.p);
+        }
+      }
+      warm = true;
+      std::vector<int> cyc;
+      for (int r : act) {
+        BlockSys &q = S[r];
+        const double beta = norm(q.V[0].b.p);
+        rel[r] = beta / q.bn;
+        if (!(rel[r] == rel[r])) throw Error(3, "solver produced NaN residual");
+        if (verbose()) std::fprintf(stderr, "cclr block gmres r=%d dir=%d omega=%g it=%d rel=%.3e prec=%d\n", r, dir, om[r], its[r], rel[r], M->prec);
+        if (rel[r] < tol[r] || beta == 0.0) {
+          q.done = true;
+          continue;
+        }
+        scal(zd(1.0 / beta), q.V[0].b.p);
+        std::fill(q.g.begin(), q.g.end(), zd(0));
+        q.g[0] = beta;
+        q.j = 0;
+        q.cyc = true;
+        cyc.push_back(r);
+      }
+      if (cyc.empty()) break;
+      for (int j = 0; j < m && used < maxit; ++j) {
+        std::vector<int> step;
+        for (int r : cyc)
+          if (S[r].cyc) step.push_back(r);
+        if (step.empty()) break;
+        for (int r : step) precond(om[r], S[r].V[j].b.p, S[r].z.b.p);
+        batch(step, false);
+        ++used;
+        for (int r : step) {
+          BlockSys &q = S[r];
+          ++its[r];
+          axpy(zd(-om[r]), q.z.b.p, q.w.b.p);
+          for (int i = 0; i <= j; ++i) {
+            const zd hij = dot(q.V[i].b.p, q.w.b.p, 1);
+            q.H[(size_t)i * m + j] = hij;
+            axpy(-hij, q.V[i].b.p, q.w.b.p);
+          }
+          const double hn = norm(q.w.b.p);
+          q.H[(size_t)(j + 1) * m + j] = hn;
+          if (hn > 0) {
+            copy(q.w.b.p, q.V[j + 1].b.p);
+            scal(zd(1.0 / hn), q.V[j + 1].b.p);
+          }
+          for (int i = 0; i < j; ++i) {
+            const zd a = q.H[(size_t)i * m + j], c_ = q.H[(size_t)(i + 1) * m + j];
+            q.H[(size_t)i * m + j] = std::conj(q.cs[i]) * a + std::conj(q.sn[i]) * c_;
+            q.H[(size_t)(i + 1) * m + j] = -q.sn[i] * a + q.cs[i] * c_;
+          }
+          const zd a = q.H[(size_t)j * m + j], c_ = q.H[(size_t)(j + 1) * m + j];
+          const double den = std::sqrt(std::norm(a) + std::norm(c_));
+          q.cs[j] = den > 0 ? a / den : zd(1);
+          q.sn[j] = den > 0 ? c_ / den : zd(0);
+          q.H[(size_t)j * m + j] = std::conj(q.cs[j]) * a + std::conj(q.sn[j]) * c_;
+          q.H[(size_t)(j + 1) * m + j] = 0;
+          q.g[j + 1] = -q.sn[j] * q.g[j];
+          q.g[j] = std::conj(q.cs[j]) * q.g[j];
+          q.j = j + 1;
+          const double est = std::abs(q.g[j + 1]) / q.bn;
+          if (est < tol[r] || hn == 0.0 || its[r] >= maxit) q.cyc = false;
+        }
+      }
+      // x_r += P (sum_i y_i v_i) with y from each system's own triangular system
+      for (int r : cyc) {
+        BlockSys &q = S[r];
+        const int jr = q.j;
+        std::vector<zd> y(jr);
+        for (int i = jr - 1; i >= 0; --i) {
+          zd t = q.g[i];
+          for (int k = i + 1; k < jr; ++k) t -= q.H[(size_t)i * m + k] * y[k];
+          const zd d = q.H[(size_t)i * m + i];
+          y[i] = std::abs(d) > 0 ? t / d : zd(0);
+        }
+        CCLR_CUDA(cudaMemsetAsync(q.w.b.p, 0, (size_t)ntot() * 16, st));
+        for (int i = 0; i < jr; ++i) axpy(y[i], q.V[i].b.p, q.w.b.p);
+        precond(om[r], q.w.b.p, q.z.b.p);
+        axpy(zd(1), q.z.b.p, x[r]);
+        if (its[r] >= maxit) q.done = true;
+      }
+    }
+    // final true residuals of the systems that stopped on an estimate or the iteration limit
+    act.clear();
+    for (int r = 0; r < nr; ++r) act.push_back(r);
+    for (int r : act) copy(b[r], S[r].V[0].b.p);
+    batch(act, true);
+    for (int r : act) {
+      axpy(zd(-1), S[r].w.b.p, S[r].V[0].b.p);
+      axpy(zd(om[r]), x[r], S[r].V[0].b.p);
+      rel[r] = norm(S[r].V[0].b.p) / S[r].bn;
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+
+  // The block form of solve(): in FP64 one block GMRES; in the mixed modes a refinement whose
+  // residuals (accurate precision) and corrections (working precision) are both batched.
+  void solve_block(int dir, const std::vector<double> &om, const std::vector<const void *> &b,
+                   const std::vector<void *> &x, double tol, int maxit, std::vector<int> &its,
+                   std::vector<double> &rel) {
+    const int nr = (int)b.size();
+    const int m = block_restart(nr);
+    if (M->prec == CCLR_FP64) {
+      gmres_block(dir, om, b, x, std::vector<double>(nr, tol), m, maxit, its, rel, false);
+      return;
+    }
+    const int lo = M->prec;
+    const double inner_tol = lo == CCLR_C64_TF32 ? 1e-2 : 1e-5;
+    const int inner_cap = lo == CCLR_C64_TF32 ? 30 : 40;
+    std::vector<AVec> sv(nr), rv(nr), dv(nr), xb(nr);
+    std::vector<double> bn(nr), prev(nr, 1e300);
+    std::vector<int> state(nr, 0);  // 0 refining, 1 converged, 2 stalled or out of iterations
+    its.assign(nr, 0);
+    rel.assign(nr, 1.0);
+    for (int r = 0; r < nr; ++r) {
+      alloc_vec(sv[r]); alloc_vec(rv[r]); alloc_vec(dv[r]); alloc_vec(xb[r]);
+      bn[r] = std::max(norm(b[r]), 1e-300);
+      CCLR_CUDA(cudaMemsetAsync(x[r], 0, (size_t)ntot() * 16, st));
+      copy(b[r], rv[r].b.p);
+    }
+    for (int outer = 0; outer < 40; ++outer) {
+      std::vector<int> act;
+      for (int r = 0; r < nr; ++r)
+        if (state[r] == 0) act.push_back(r);
+      if (act.empty()) break;
+      if (outer > 0) {
+        std::vector<const void *> in;
+        std::vector<void *> out;
+        for (int r : act) { in.push_back(x[r]); out.push_back(sv[r].b.p); }
+        M->prec = hi_prec;
+        op_batch(dir, (int)act.size(), in.data(), out.data());
+        M->prec = lo;
+        ++refinements;
+        for (int r : act) {
+          copy(b[r], rv[r].b.p);
+          axpy(zd(-1), sv[r].b.p, rv[r].b.p);
+          axpy(zd(om[r]), x[r], rv[r].b.p);
+        }
+      }
+      std::vector<int> go;
+      std::vector<double> gom, gtol;
+      std::vector<const void *> gb;
+      std::vector<void *> gx;
+      for (int r : act) {
+        rel[r] = norm(rv[r].b.p) / bn[r];
+        if (!(rel[r] == rel[r])) throw Error(3, "solver produced NaN residual");
+        if (verbose()) std::fprintf(stderr, "cclr block refine r=%d dir=%d omega=%g outer=%d rel=%.3e\n", r, dir, om[r], outer, rel[r]);
+        if (rel[r] > 0.5 * prev[r]) {  // the last correction did not help
+          if (rel[r] > prev[r]) {
+            copy(xb[r].b.p, x[r]);
+            rel[r] = prev[r];
+          }
+          state[r] = 2;
+          continue;
+        }
+        if (rel[r] < tol) { state[r] = 1; continue; }
+        if (its[r] >= maxit) { state[r] = 2; continue; }
+        copy(x[r], xb[r].b.p);
+        prev[r] = rel[r];
+        go.push_back(r);
+        gom.push_back(om[r]);
+        gtol.push_back(std::max(inner_tol, 0.3 * tol / rel[r]));
+        gb.push_back(rv[r].b.p);
+        gx.push_back(dv[r].b.p);
+      }
+      if (go.empty()) continue;
+      int cap = inner_cap;
+      for (int r : go) cap = std::min(cap, maxit - its[r]);
+      std::vector<int> inner_its;
+      std::vector<double> inner_rel;
+      gmres_block(dir, gom, gb, gx, gtol, std::min(m, cap), std::max(1, cap), inner_its, inner_rel, false);
+      for (size_t k = 0; k < go.size(); ++k) {
+        its[go[k]] += inner_its[k];
+        axpy(zd(1), dv[go[k]].b.p, x[go[k]]);
+      }
+    }
+    // systems that stalled or ran out: finish in the accurate arithmetic, warm-started
+    std::vector<int> fin;
+    std::vector<double> fom;
+    std::vector<const void *> fb;
+    std::vector<void *> fx_;
+    int rest_cap = maxit;
+    for (int r = 0; r < nr; ++r)
+      if (rel[r] >= tol && its[r] < maxit) {
+        fin.push_back(r); fom.push_back(om[r]); fb.push_back(b[r]); fx_.push_back(x[r]);
+        rest_cap = std::min(rest_cap, maxit - its[r]);
+      }
+    if (!fin.empty()) {
+      std::vector<int> fits;
+      std::vector<double> frel;
+      M->prec = hi_prec;
+      gmres_block(dir, fom, fb, fx_, std::vector<double>(fin.size(), tol), m, rest_cap, fits, frel, true);
+      M->prec = lo;
+      for (size_t k = 0; k < fin.size(); ++k) {
+        its[fin[k]] += fits[k];
+        rel[fin[k]] = frel[k];
+      }
+    }
+  }
+
+  // restart length of the block solver: the Krylov bases of all systems must fit in half of
+  // the free device memory
+  int block_restart(int nr) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return krylov;
+    }
+    const double vec = (double)ntot() * 16;
+    const int fit = (int)(0.5 * (double)free_b / (vec * std::max(1, nr))) - 4;
+    return std::max(2, std::min(krylov, fit));
   }
 
   // Preconditioned DIIS (Pulay extrapolation over Jacobi steps) on (Op - omega) x = b.
@@ -712,7 +990,34 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
       // X^C(s*omega) for every component and sign
       std::vector<AVec> X((size_t)ncomp * 2);
       auto t0 = std::chrono::steady_clock::now();
-      for (int a = 0; a < ncomp; ++a) {
+      if (c->method == 2) {
+        // every component and sign in one block: the operator is applied to all of them at once
+        std::vector<AVec> B(ncomp);
+        std::vector<double> oms;
+        std::vector<const void *> bs;
+        std::vector<void *> xs;
+        for (int a = 0; a < ncomp; ++a) {
+          c->alloc_vec(B[a]);
+          c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, B[a].b.p);
+          c->scal(zd(-1), B[a].b.p);
+          for (int s = 0; s < nsign; ++s) {
+            AVec &x = X[(size_t)a * 2 + s];
+            c->alloc_vec(x);
+            oms.push_back(s == 0 ? om : -om);
+            bs.push_back(B[a].b.p);
+            xs.push_back(x.b.p);
+          }
+        }
+        std::vector<int> its;
+        std::vector<double> rels;
+        c->solve_block(+1, oms, bs, xs, tol, c->maxit, its, rels);
+        for (size_t k = 0; k < its.size(); ++k) {
+          loc.iterations += its[k];
+          loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
+          if (!(rels[k] < tol)) loc.converged = 0;
+        }
+      }
+      for (int a = 0; a < ncomp && c->method != 2; ++a) {
         AVec b;
         c->alloc_vec(b);
         c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, b.b.p);
@@ -822,7 +1127,7 @@ cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
 }
 
 cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace, int max_iterations) {
-  if (!c || (method != 0 && method != 1) || subspace < 0 || subspace > 100 || max_iterations < 0)
+  if (!c || method < 0 || method > 2 || subspace < 0 || subspace > 100 || max_iterations < 0)
     return (cclr_status)fail(CCLR_EINVAL, "bad solver arguments");
   c->method = method;
   if (subspace >= 2) c->krylov = subspace;

@@ -327,3 +327,22 @@ def test_graph_replay_solve_alpha(prec):
     assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
     assert launches > caps > 0
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,refine", [("fp64", "fp64"), ("tf32", "fp64"), ("tf32", "3xtf32")])
+def test_block_solver_alpha_matches_oracle(prec, refine):
+    """Block GMRES (all components and both frequency signs advanced together, one batched
+    operator product per iteration) gives the oracle's alpha."""
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy(), prec=prec)
+    ctx.cc_lr_set_solver("block")
+    if prec != "fp64":
+        ctx.cc_lr_set_refinement(refine)
+    tol = 1e-10 if prec == "fp64" else (1e-8 if refine == "fp64" else 1e-6)
+    al, st = ctx.cc_lr_solve([0.0428], (0, 1, 2), tol=tol)
+    ref = R.alpha(P, [as_t(m) for m in s.mu], 0.0428).numpy()
+    err = np.abs(al[0] - ref).max()
+    print(f"{prec}/{refine}: |delta alpha| {err:.2e}, {st}")
+    assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
+    assert st["converged"] == 1
+    ctx.close()
