@@ -61,6 +61,24 @@ def algorithmic(o, v, naux):
             "n_unique": o * v + Po * Pv}
 
 
+# DRAM bytes (read + write) per executed FLOP of the formation GEMM, from the ncu capture in
+# profiles/tc_gemm_ladder_formation_C2.md (one launch of 28800 x 7680 x 1200 complex:
+# 1.793388 GB read + 1.740861 GB written for 8 M N K = 2.1234e12 FLOP).  With K = naux fixed,
+# both the output writes and the per-band operand reads scale with M N, so the ratio carries
+# over to every group of the same workload.
+FORMATION_BYTES_PER_FLOP = (1.793388e9 + 1.740861e9) / (8 * 28800 * 7680 * 1200)
+
+
+def formation_flops_executed(v, naux, ga):
+    """Real FLOP the formation GEMMs execute per sigma with group size ga (rows (b,f) with
+    b >= a0 for each group of ga a values)."""
+    tot = 0
+    for a0 in range(0, v - 1, ga):
+        a1 = min(v, a0 + ga)
+        tot += 8 * (v - a0) * v * (a1 - a0) * v * naux
+    return tot
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -390,9 +408,12 @@ def run_cclr(args):
     bound, peak, how = ladder_peak(args.prec)
     lad_achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
     # the dominant kernel: the tensor-core GEMMs that form <ab|ef>~ (CUDA events around each)
+    traffic = None
     if form_ms > 0:
         kernel = "tc_gemm_kernel: pp-ladder formation <ab|ef>~ = sum_P L~_ae L~_bf (all groups of one sigma)"
         achieved = alg["form_cmac"] * 8 / (form_ms * 1e-3) / 1e12
+        ga = ctx.cc_lr_ladder_tuning(args.prec)[0]
+        traffic = FORMATION_BYTES_PER_FLOP * formation_flops_executed(v, naux, ga)
     else:
         kernel = "pp-ladder (formation + contraction)"
         achieved = lad_achieved
@@ -415,7 +436,9 @@ def run_cclr(args):
                        "l2": "inputs larger than L2 (X2 c128 %.2f GB, L~vv %.2f GB)" % (x2.numel() * 16 / 1e9, naux * v * v * 16 / 1e9)},
             "roofline": {"kernel": kernel, "bound": bound,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "peak_source": how, "traffic": None,
+                         "frac": achieved / peak, "peak_source": how, "traffic": traffic,
+                         "traffic_source": "ncu dram bytes per FLOP of one formation launch, scaled to the "
+                                           "FLOP of one sigma's formation launches" if traffic else None,
                          "kernel_ms": form_ms if form_ms > 0 else lad_ms,
                          "ladder_ms": lad_ms, "ladder_share": lad_ms / (ms_max / args.steps),
                          "ladder_achieved": lad_achieved, "ladder_frac": lad_achieved / peak},
