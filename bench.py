@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--alpha-scale", type=float, default=0.2)
     ap.add_argument("--batch-rhs", type=int, default=9)
     ap.add_argument("--no-alpha-large", action="store_true")
+    ap.add_argument("--no-ablation", action="store_true")
     ap.add_argument("--alpha-large-config", default="C2")
     ap.add_argument("--alpha-large-scale", type=float, default=0.05)
     return ap.parse_args()
@@ -402,6 +403,28 @@ def run_cclr(args):
                    "ladder_ms_per_batch": sum(lad_b) / len(lad_b)}
         del xb1, xb2, sb1, sb2
 
+    ablation = None
+    if args.prec in ("tf32", "3xtf32") and not args.no_ablation:
+        # ablation: the packed <ab||ef>~ kept in HBM after the first product (no re-formation)
+        ctx.cc_lr_set_ladder_storage(True)
+        for _ in range(2):
+            ctx.sigma_into(x1, x2, s1, s2)
+        barrier()
+        lad_s = []
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.sigma_into(x1, x2, s1, s2)
+            lad_s.append(float(ctx.cc_lr_last_timings()[0]))
+        e1.record(stream)
+        barrier()
+        ms_s = reduce_max(e0.elapsed_time(e1)) / args.steps
+        Pv = v * (v - 1) // 2
+        ablation = {"what": "stored packed <ab||ef>~ (P_v x P_v kept in HBM; deviates from on-the-fly formation)",
+                    "sigma_vectors_per_s": replica_throughput(world, args.steps, ms_s * args.steps),
+                    "ms_per_step": ms_s, "ladder_ms": sum(lad_s) / len(lad_s),
+                    "stored_gb": Pv * Pv * 8 * (3 if args.prec == "3xtf32" else 1) / 1e9}
+        ctx.cc_lr_set_ladder_storage(False)
+
     alg = algorithmic(o, v, naux)
     lad_ms = sum(lad) / len(lad)
     form_ms = sum(form) / len(form)
@@ -453,6 +476,8 @@ def run_cclr(args):
             out["time_to_alpha_large"] = tta_large
         if batched is not None:
             out["batched"] = batched
+        if ablation is not None:
+            out["ablation_stored_ladder"] = ablation
         if cpu is not None:
             out["cpu_baseline"] = cpu
         print(json.dumps(out), flush=True)

@@ -144,6 +144,14 @@ cclr_status cc_lr_set_graphs(cclr_ctx *ctx, int on);
 cclr_status cc_lr_ladder_tuning(cclr_ctx *ctx, int prec, int *group_size, int cap, int *cand, double *ms,
                                 int *n);
 
+/* Ablation of the on-the-fly ladder (off by default): with store = 1 the tensor-core modes keep
+ * the whole antisymmetrised, packed <ab||ef>~ (P_v x P_v, P_v = v(v-1)/2; 8 bytes per entry in
+ * TF32 mode, 24 in 3xTF32: 6.6 GB and 19.7 GB at v = 240) once the first sigma product has
+ * formed it, and later sigma products contract it in one GEMM instead of forming it again.
+ * The transpose product and the FP64 mode still form the blocks on the fly.  A rebuilt
+ * constant set (new amplitudes) re-forms it on the next product. */
+cclr_status cc_lr_set_ladder_storage(cclr_ctx *ctx, int store);
+
 /* Number of graph captures and graph launches made by the context so far. */
 cclr_status cc_lr_graph_stats(cclr_ctx *ctx, int *captures, int *launches);
 

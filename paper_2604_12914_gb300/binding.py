@@ -22,7 +22,7 @@ PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
            "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
-           "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_solver",
+           "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_ladder_storage", "cc_lr_set_solver",
            "cc_lr_last_timings",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_set_solver": [P, I, I, I],
         "cc_lr_set_refinement": [P, I],
         "cc_lr_set_graphs": [P, I],
+        "cc_lr_set_ladder_storage": [P, I],
         "cc_lr_graph_stats": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "cc_lr_ladder_tuning": [P, I, ctypes.POINTER(ctypes.c_int), I, P, P, ctypes.POINTER(ctypes.c_int)],
         "cc_lr_last_timings": [P, P, I],
@@ -238,6 +239,10 @@ class Context:
         c, l = ctypes.c_int(0), ctypes.c_int(0)
         _check(load().cc_lr_graph_stats(self._h, ctypes.byref(c), ctypes.byref(l)))
         return c.value, l.value
+
+    def cc_lr_set_ladder_storage(self, store=True):
+        """Ablation: keep the packed <ab||ef>~ once formed (see include/cclr.h)."""
+        _check(load().cc_lr_set_ladder_storage(self._h, 1 if store else 0))
 
     def cc_lr_ladder_tuning(self, prec="tf32"):
         """(group size in use, [(candidate, ms), ...]) of the pp-ladder autotuner."""

@@ -1117,6 +1117,14 @@ cclr_status cc_lr_ladder_tuning(cclr_ctx *c, int prec, int *group_size, int cap,
   return CCLR_OK;
 }
 
+cclr_status cc_lr_set_ladder_storage(cclr_ctx *c, int store) {
+  if (!c || (store != 0 && store != 1)) return (cclr_status)fail(CCLR_EINVAL, "ladder storage must be 0 or 1");
+  return (cclr_status)guarded([&] {
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+    for (auto &l : c->M->ltc) l.set_store(store != 0);
+  });
+}
+
 cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
   if (!c || (prec != CCLR_FP64 && prec != CCLR_C64_3XTF32))
     return (cclr_status)fail(CCLR_EINVAL, "refinement precision must be CCLR_FP64 or CCLR_C64_3XTF32");

@@ -151,6 +151,7 @@ int64_t pair_start(int v, int a) { return (int64_t)a * v - (int64_t)a * (a + 1) 
 
 void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg) {
   cudaStream_t st = E.st;
+  wall_ready_ = false;  // a stored block belongs to the previous L~_vv
   o_ = o; v_ = v; naux_ = naux; seg_ = seg;
   Po_ = (int64_t)o * (o - 1) / 2;
   Pv_ = (int64_t)v * (v - 1) / 2;
@@ -185,6 +186,8 @@ void LadderTC::tune(Engine &E) {
   void *out[1] = {xout.p};
   int best = ga_;
   float best_ms = 1e30f;
+  const bool store_saved = store_;
+  store_ = false;  // the tuner times the on-the-fly formation
   for (int cand : {16, 32, 64}) {
     const int ga = std::min(cand, v_);
     const double wbytes = (double)v_ * v_ * ga * v_ * 8;
@@ -204,6 +207,7 @@ void LadderTC::tune(Engine &E) {
     W.release(); Wp.release(); Xp.release(); sig.release();
   }
   ga_ = best;
+  store_ = store_saved;
   CCLR_CUDA(cudaEventDestroy(e0));
   CCLR_CUDA(cudaEventDestroy(e1));
 }
@@ -238,7 +242,12 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   } else {
     CCLR_CUDA(cudaMemsetAsync(sig.p, 0, (size_t)Po * Pv * NR * 8, st));
   }
-  for (int a0 = 0; a0 < v - 1; a0 += ga) {
+  const bool use_wall = store_ && dir > 0;
+  if (use_wall && !wall_ready_) {
+    const size_t wall_bytes = (size_t)Pv * ldPv * 4;
+    if (Wall.bytes != wall_bytes) Wall.alloc(wall_bytes);
+  }
+  for (int a0 = 0; a0 < v - 1 && !(use_wall && wall_ready_); a0 += ga) {
     const int a1 = std::min(v, a0 + ga);
     const int64_t p0 = pair_start(v, a0), np = pair_start(v, a1) - p0;
     if (np == 0) continue;
@@ -254,7 +263,11 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
                 rows, 2 * cols, ldL / seg, seg, W.as<float>(), 2 * cols, zc(1.0), false, st);
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_ + 1], st));
     ++nform_;
-    if (dir > 0) {
+    if (use_wall) {  // pack the group's rows into the stored block; contract once afterwards
+      pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
+                                                Wall.as<float>() + p0 * ldPv, ldPv);
+      count_launch();
+    } else if (dir > 0) {
       pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
                                                 Wp.as<float>(), ldPv);
       count_launch();
@@ -275,6 +288,13 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
       tc_gemm_seg(Xp.as<float>(), ldg, Wp.as<float>(), ldg, Po * NR, 2 * Pv, ldg / seg, seg, sig.as<float>(),
                   2 * Pv, zc(1.0), true, st);
     }
+    CCLR_CUDA(cudaGetLastError());
+  }
+  if (use_wall) {
+    wall_ready_ = true;
+    // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f] for every pair at once
+    tc_gemm_seg(Wall.as<float>(), ldPv, Xp.as<float>(), ldPv, Pv, 2 * Po * NR, ldPv / seg, seg, sig.as<float>(),
+                2 * Po * NR, zc(1.0), false, st);
     CCLR_CUDA(cudaGetLastError());
   }
   for (int64_t r = 0; r < NR; ++r) {

@@ -28,6 +28,15 @@ class LadderTC {
   // once per object, on its first preparation; group_size() and tune_log report the result.
   void tune(Engine &E);
   int group_size() const { return ga_; }
+  // Ablation: keep the whole packed <ab||ef>~ (P_v x P_v, TF32 rows) once formed, so that later
+  // sigma products (dir +1) skip the formation and run one contraction GEMM.  The transpose
+  // product still forms the blocks on the fly.  Costs P_v^2 x 8 bytes (x 3 for 3xTF32).
+  void set_store(bool on) {
+    store_ = on;
+    if (!on) { Wall.release(); wall_ready_ = false; }
+  }
+  bool stored() const { return store_; }
+  size_t stored_bytes() const { return Wall.bytes; }
   std::vector<std::pair<int, float>> tune_log;
 
  private:
@@ -38,6 +47,8 @@ class LadderTC {
   DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result
   int ga_ = 32;             // a values per group (set by tune())
   bool tuned_ = false;
+  bool store_ = false, wall_ready_ = false;
+  DevBuf Wall;              // stored packed <ab||ef>~ (ablation)
   std::vector<cudaEvent_t> fev;  // formation start/stop events, two per group
   int nform_ = 0;                // groups timed in the last apply()
 };

@@ -346,3 +346,26 @@ def test_block_solver_alpha_matches_oracle(prec, refine):
     assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
     assert st["converged"] == 1
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("tf32", 1e-5), ("3xtf32", 1e-6)])
+def test_stored_ladder_ablation_matches_on_the_fly(prec, tol):
+    """The stored packed <ab||ef>~ (ablation) gives the on-the-fly sigma: first product forms and
+    keeps it, later ones reuse it; the transpose product is unchanged."""
+    o, v, naux, seed, scale, t1s = CASES[2]
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx = gpu_context(s, t1=t1, t2=t2, prec=prec)
+    x1, x2 = random_amplitudes(o, v, seed=3, nvec=2)
+    e1, e2 = ctx.cc_lr_sigma(x1, x2)
+    f1, f2 = ctx.cc_lr_sigma_T(x1[0], x2[0])
+    ctx.cc_lr_set_ladder_storage(True)
+    for _ in range(2):
+        g1, g2 = ctx.cc_lr_sigma(x1, x2)
+        for r in range(2):
+            assert rel_err(g1[r], g2[r], e1[r], e2[r]) < tol
+    h1, h2 = ctx.cc_lr_sigma_T(x1[0], x2[0])
+    assert rel_err(h1, h2, f1, f2) < tol
+    r1, r2 = oracle_sigma(s, t1, t2, x1[0], x2[0])
+    assert rel_err(g1[0], g2[0], r1, r2) < (3e-3 if prec == "tf32" else 5e-5)
+    ctx.close()
