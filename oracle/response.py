@@ -15,6 +15,10 @@ Sec. 2.2 definitions, with the Lagrangian L(T) = E(T) + lambda . Omega(T):
 * g(A,B;w) = eta^A . X^B(w) + eta^B . X^A(-w) + (F X^A(-w)) . X^B(w);
   <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)] (P(A,B) swaps A and B and conjugates);
   alpha_AB(w) = -<<A;B>>_w.
+* Damped response (complex frequency z = w + i gamma, the same sigma with a complex shift):
+  <<A;B>>_z = 1/2 [g(A,B;z) + conj g(A,B;-z*)], which is the real-frequency formula at
+  gamma = 0 and, for exact states, equals the sum over states continued to complex z
+  (the conjugate term of the exact function at -z* is the function at z).
 Dot products are bilinear over unique amplitudes (singles, i<j a<b doubles).
 """
 from __future__ import annotations
@@ -174,27 +178,29 @@ def solve_x(A, xi_vec, omega):
     return torch.linalg.solve(A - omega * torch.eye(N, dtype=C128), -xi_vec)
 
 
-def alpha(P: Problem, ops, omega: float, lam=None, A=None):
-    """Complex 3x3 (or k x k) polarisability alpha_AB(omega) = -<<A;B>>_omega."""
+def alpha(P: Problem, ops, omega: float, lam=None, A=None, gamma: float = 0.0):
+    """Complex 3x3 (or k x k) polarisability alpha_AB(z) = -<<A;B>>_z, z = omega + i gamma
+    (gamma = 0: the undamped response)."""
     if A is None:
         A = P.jacobian_matrix()
     if lam is None:
         lam = torch.linalg.solve(A.transpose(0, 1), -P.eta0())
     k = len(ops)
+    z = complex(omega, gamma)
     xi = [P.pack(*P.xi(op)) for op in ops]
-    Xp = [P.unpack(solve_x(A, xi[b], omega)) for b in range(k)]
-    Xm = [P.unpack(solve_x(A, xi[b], -omega)) for b in range(k)]
+    X = {}
+    for shift in {z, -z, z.conjugate(), -z.conjugate()}:
+        X[shift] = [P.unpack(solve_x(A, xi[b], shift)) for b in range(k)]
 
-    def g(a, b, Xw, Xmw):
-        return (P.eta_dot(ops[a], lam, *Xw[b]) + P.eta_dot(ops[b], lam, *Xmw[a])
-                + P.fxx(lam, Xmw[a], Xw[b]))
+    def g(a, b, w):
+        # g(A,B;w) = eta^A . X^B(w) + eta^B . X^A(-w) + (F X^A(-w)) . X^B(w)
+        return (P.eta_dot(ops[a], lam, *X[w][b]) + P.eta_dot(ops[b], lam, *X[-w][a])
+                + P.fxx(lam, X[-w][a], X[w][b]))
 
     out = torch.zeros(k, k, dtype=C128)
     for a in range(k):
         for b in range(k):
-            gp = g(a, b, Xp, Xm)
-            gm = g(a, b, Xm, Xp)
-            out[a, b] = -0.5 * (gp + torch.conj(gm))
+            out[a, b] = -0.5 * (g(a, b, z) + torch.conj(g(a, b, -z.conjugate())))
     return out
 
 

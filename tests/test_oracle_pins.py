@@ -163,6 +163,34 @@ def test_eta0_vs_energy_fd():
     assert abs(fd - e0 @ P.pack(d1, d2)) < 1e-10 * abs(fd)
 
 
+@pytest.mark.parametrize("omega,gamma", [(0.0, 0.05), (0.0428, 0.01), (0.7, 0.02)])
+def test_damped_alpha_vs_sum_over_states(omega, gamma):
+    """Two electrons, complex frequency z = omega + i gamma: the damped CC response equals
+    Eq. sos continued to complex z (no symmetry in z is assumed by the sum; 0.7 lies near
+    an excitation, where the damping matters)."""
+    o, v = 2, 4
+    s = _system(o, v, 6, seed=2, scale=0.3)
+    P = oracle_problem(s, converge=True)
+    bf = secondq.BruteForce(P.f.numpy(), P.g.numpy(), o)
+    w, U = bf.fci()
+    st, ov = secondq.cc_state_overlap(U, P.t1.numpy(), P.t2.numpy(), bf)
+    assert ov > 1 - 1e-10
+    mu = [as_t(m) for m in s.mu]
+    ops = [bf.one_body_op(m.numpy()) for m in mu]
+    z = complex(omega, gamma)
+    al = R.alpha(P, mu, omega, gamma=gamma).numpy()
+    sos = np.array([[-secondq.sos_response(w, U, ops[a], ops[b], z, st) for b in range(3)]
+                    for a in range(3)])
+    assert np.abs(al - sos).max() < 1e-10 * np.abs(sos).max()
+    d = np.diag(al)
+    if omega == 0.0:
+        # imaginary frequency: Hermitian operators give a real diagonal
+        assert np.abs(d.imag).max() < 1e-12 * np.abs(d).max()
+    else:
+        # absorption: damping gives the diagonal a nonzero imaginary part of one sign
+        assert np.all(d.imag > 0) or np.all(d.imag < 0)
+
+
 @pytest.mark.parametrize("omega", [0.0, 0.0428])
 def test_alpha_vs_sum_over_states(omega):
     """Two electrons: CCSD is exact, so CC linear response equals Eq. sos."""
