@@ -114,6 +114,16 @@ cclr_status cc_lr_solve(cclr_ctx *ctx, int nomega, const double *omegas, int nco
                         const int *comps, double tol, int diis_depth, double *alpha,
                         cclr_stats *stats);
 
+/* Damped response (complex frequency z = omega + i gamma, gamma >= 0; the pole widths and
+ * absorption of Sec. 2.2's response function continued off the real axis): the same as
+ * cc_lr_solve with X^C solved at the complex shifts z, -z, z*, -z* ((A - s) X = -xi^C, complex
+ * shift in the solver and the diagonal preconditioner) and
+ * <<A;B>>_z = 1/2 [g(A,B;z) + conj g(A,B;-z*)], alpha = -<<A;B>>_z.  gamma = 0 gives
+ * cc_lr_solve. */
+cclr_status cc_lr_solve_damped(cclr_ctx *ctx, int nomega, const double *omegas, double gamma, int ncomp,
+                               const int *comps, double tol, int diis_depth, double *alpha,
+                               cclr_stats *stats);
+
 /* Ground-state Lambda (solved if needed) copied out: lam1 [o][v], lam2 [o][o][v][v]. */
 cclr_status cc_lr_lambda(cclr_ctx *ctx, double tol, double *lam1, double *lam2);
 

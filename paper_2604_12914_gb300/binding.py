@@ -21,6 +21,7 @@ CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32 = range(4)
 PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32}
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
+           "cc_lr_solve_damped",
            "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
            "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_ladder_storage", "cc_lr_set_solver",
            "cc_lr_last_timings",
@@ -62,6 +63,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_xi": [P, I, P, P],
         "cc_lr_solve_x": [P, D, I, D, I, P, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
+        "cc_lr_solve_damped": [P, I, P, D, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_lambda": [P, D, P, P],
         "cc_lr_get_t": [P, P, P],
         "cc_lr_set_precision": [P, I],
@@ -200,14 +202,19 @@ class Context:
                allow=(CCLR_ENOCONV,) if allow_noconv else ())
         return x1, x2, st.as_dict()
 
-    def cc_lr_solve(self, omegas, comps=(0, 1, 2), tol=1e-10, diis_depth=8, allow_noconv=False):
+    def cc_lr_solve(self, omegas, comps=(0, 1, 2), tol=1e-10, diis_depth=8, allow_noconv=False, gamma=0.0):
+        """alpha[w][a][b] at omega_w (+ i gamma when gamma > 0: damped response)."""
         om = np.ascontiguousarray(omegas, dtype=np.float64)
         cp = np.ascontiguousarray(comps, dtype=np.int32)
         out = np.zeros((len(om), len(cp), len(cp)), dtype=np.complex128)
         st = cclr_stats()
-        status = _check(load().cc_lr_solve(self._h, len(om), _ptr(om), len(cp), _ptr(cp), float(tol),
-                                           diis_depth, _ptr(out), ctypes.byref(st)),
-                        allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        if gamma:
+            call = load().cc_lr_solve_damped(self._h, len(om), _ptr(om), float(gamma), len(cp), _ptr(cp),
+                                             float(tol), diis_depth, _ptr(out), ctypes.byref(st))
+        else:
+            call = load().cc_lr_solve(self._h, len(om), _ptr(om), len(cp), _ptr(cp), float(tol),
+                                      diis_depth, _ptr(out), ctypes.byref(st))
+        status = _check(call, allow=(CCLR_ENOCONV,) if allow_noconv else ())
         d = st.as_dict()
         d["status"] = status
         return out, d

@@ -75,9 +75,10 @@ struct cclr_ctx {
   void axpy(zd a, const void *x, void *y) { vec_axpy(C128, ntot(), zc(a.real(), a.imag()), x, y, st); }
   void copy(const void *x, void *y) { CCLR_CUDA(cudaMemcpyAsync(y, x, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st)); }
   void scal(zd a, void *y) { vec_scal(C128, ntot(), zc(a.real(), a.imag()), y, st); }
-  void precond(double omega, const void *r, void *out) {
-    vec_precond(C128, n1, M->D1.as<double>(), omega, r, out, st);
-    vec_precond(C128, n2, M->D2.as<double>(), omega, (const char *)r + n1 * 16, (char *)out + n1 * 16, st);
+  void precond(zd omega, const void *r, void *out) {
+    vec_precond(C128, n1, M->D1.as<double>(), omega.real(), omega.imag(), r, out, st);
+    vec_precond(C128, n2, M->D2.as<double>(), omega.real(), omega.imag(), (const char *)r + n1 * 16,
+                (char *)out + n1 * 16, st);
   }
 
   // s = A x (dir +1) or x A (dir -1) in the current precision; x, s complex128 amplitude vectors
@@ -136,7 +137,7 @@ struct cclr_ctx {
   // normed and applied in FP64; each correction (Op - omega) d = r is solved by DIIS with
   // the tensor-core sigma (TF32: two digits per correction, 3xTF32: five).
   int refinements = 0;
-  double solve(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+  double solve(int dir, zd omega, const void *b, void *x, double tol, int depth, int maxit,
                int *its) {
     if (M->prec == CCLR_FP64) return solve_diis(dir, omega, b, x, tol, depth, maxit, its);
     const int lo = M->prec;
@@ -166,7 +167,7 @@ struct cclr_ctx {
         axpy(zd(omega), x, r.b.p);
       }
       rel = norm(r.b.p) / bn;
-      if (verbose()) std::fprintf(stderr, "cclr refine dir=%d omega=%g outer=%d rel=%.3e\n", dir, omega, outer, rel);
+      if (verbose()) std::fprintf(stderr, "cclr refine dir=%d omega=%g outer=%d rel=%.3e\n", dir, omega.real(), outer, rel);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
       if (rel > 0.5 * rel_prev) {
         // the last correction did not help: go back to the best iterate and stop refining
@@ -204,7 +205,7 @@ struct cclr_ctx {
   int krylov = 30;
   int maxit = 300;  // iterations per linear solve, all precisions together
 
-  double solve_diis(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+  double solve_diis(int dir, zd omega, const void *b, void *x, double tol, int depth, int maxit,
                     int *its, bool warm = false) {
     if (method >= 1) return solve_gmres(dir, omega, b, x, tol, krylov, maxit, its, warm);
     return solve_pulay(dir, omega, b, x, tol, depth, maxit, its, warm);
@@ -215,7 +216,7 @@ struct cclr_ctx {
   // weighted Hermitian inner product (singles 1, doubles 1/4), Givens rotations and the
   // small least-squares problem on the host in FP64.
   std::vector<AVec> kv;  // Krylov basis (kept between calls)
-  double solve_gmres(int dir, double omega, const void *b, void *x, double tol, int m, int maxit,
+  double solve_gmres(int dir, zd omega, const void *b, void *x, double tol, int m, int maxit,
                      int *its, bool warm) {
     m = std::max(2, std::min(m, 100));
     if ((int)kv.size() < m + 1) kv.resize(m + 1);
@@ -239,7 +240,7 @@ struct cclr_ctx {
       warm = true;
       double beta = norm(kv[0].b.p);
       rel = beta / bn;
-      if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega, used, rel, M->prec);
+      if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega.real(), used, rel, M->prec);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
       if (rel < tol || beta == 0.0) break;
       scal(zd(1.0 / beta), kv[0].b.p);
@@ -278,7 +279,7 @@ struct cclr_ctx {
         g[j + 1] = -sn[j] * g[j];
         g[j] = std::conj(cs[j]) * g[j];
         rel = std::abs(g[j + 1]) / bn;
-        if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d est=%.3e\n", dir, omega, used, rel);
+        if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d est=%.3e\n", dir, omega.real(), used, rel);
         if (rel < tol || hn == 0.0) { ++j; break; }
       }
       // y = H(0:j,0:j)^-1 g(0:j); x += P (sum_i y_i v_i)
@@ -322,7 +323,7 @@ struct cclr_ctx {
   // (the ladder's <ab||ef>~ blocks are formed once per iteration for all of them).  Each system
   // keeps its own restarted, right-preconditioned GMRES (the method of solve_gmres); rel[r]
   // receives its final relative residual, its[r] its iteration count.
-  void gmres_block(int dir, const std::vector<double> &om, const std::vector<const void *> &b,
+  void gmres_block(int dir, const std::vector<zd> &om, const std::vector<const void *> &b,
                    const std::vector<void *> &x, const std::vector<double> &tol, int m, int maxit,
                    std::vector<int> &its, std::vector<double> &rel, bool warm) {
     const int nr = (int)b.size();
@@ -382,7 +383,7 @@ struct cclr_ctx {
         const double beta = norm(q.V[0].b.p);
         rel[r] = beta / q.bn;
         if (!(rel[r] == rel[r])) throw Error(3, "solver produced NaN residual");
-        if (verbose()) std::fprintf(stderr, "cclr block gmres r=%d dir=%d omega=%g it=%d rel=%.3e prec=%d\n", r, dir, om[r], its[r], rel[r], M->prec);
+        if (verbose()) std::fprintf(stderr, "cclr block gmres r=%d dir=%d omega=%g it=%d rel=%.3e prec=%d\n", r, dir, om[r].real(), its[r], rel[r], M->prec);
         if (rel[r] < tol[r] || beta == 0.0) {
           q.done = true;
           continue;
@@ -469,7 +470,7 @@ struct cclr_ctx {
 
   // The block form of solve(): in FP64 one block GMRES; in the mixed modes a refinement whose
   // residuals (accurate precision) and corrections (working precision) are both batched.
-  void solve_block(int dir, const std::vector<double> &om, const std::vector<const void *> &b,
+  void solve_block(int dir, const std::vector<zd> &om, const std::vector<const void *> &b,
                    const std::vector<void *> &x, double tol, int maxit, std::vector<int> &its,
                    std::vector<double> &rel) {
     const int nr = (int)b.size();
@@ -512,13 +513,14 @@ struct cclr_ctx {
         }
       }
       std::vector<int> go;
-      std::vector<double> gom, gtol;
+      std::vector<zd> gom;
+      std::vector<double> gtol;
       std::vector<const void *> gb;
       std::vector<void *> gx;
       for (int r : act) {
         rel[r] = norm(rv[r].b.p) / bn[r];
         if (!(rel[r] == rel[r])) throw Error(3, "solver produced NaN residual");
-        if (verbose()) std::fprintf(stderr, "cclr block refine r=%d dir=%d omega=%g outer=%d rel=%.3e\n", r, dir, om[r], outer, rel[r]);
+        if (verbose()) std::fprintf(stderr, "cclr block refine r=%d dir=%d omega=%g outer=%d rel=%.3e\n", r, dir, om[r].real(), outer, rel[r]);
         if (rel[r] > 0.5 * prev[r]) {  // the last correction did not help
           if (rel[r] > prev[r]) {
             copy(xb[r].b.p, x[r]);
@@ -550,7 +552,7 @@ struct cclr_ctx {
     }
     // systems that stalled or ran out: finish in the accurate arithmetic, warm-started
     std::vector<int> fin;
-    std::vector<double> fom;
+    std::vector<zd> fom;
     std::vector<const void *> fb;
     std::vector<void *> fx_;
     int rest_cap = maxit;
@@ -586,7 +588,7 @@ struct cclr_ctx {
   }
 
   // Preconditioned DIIS (Pulay extrapolation over Jacobi steps) on (Op - omega) x = b.
-  double solve_pulay(int dir, double omega, const void *b, void *x, double tol, int depth, int maxit,
+  double solve_pulay(int dir, zd omega, const void *b, void *x, double tol, int depth, int maxit,
                      int *its, bool warm = false) {
     depth = std::max(2, std::min(depth, 16));
     std::vector<AVec> X(depth), Er(depth);
@@ -607,7 +609,7 @@ struct cclr_ctx {
       axpy(zd(omega), x, r.b.p);
       rel = norm(r.b.p) / bn;
       if (its) ++*its;
-      if (verbose()) std::fprintf(stderr, "cclr diis dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega, it, rel, M->prec);
+      if (verbose()) std::fprintf(stderr, "cclr diis dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega.real(), it, rel, M->prec);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
       if (rel < tol) break;
       int k = head;
@@ -972,9 +974,13 @@ cclr_status cc_lr_lambda(cclr_ctx *c, double tol, double *lam1, double *lam2) {
   });
 }
 
-cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
-                        double tol, int diis_depth, double *alpha, cclr_stats *stats) {
-  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0))
+// alpha at z = omega + i gamma for every omega (gamma = 0: the undamped response):
+//   g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w),
+//   <<A;B>>_z = 1/2 [g(A,B;z) + conj g(A,B;-z*)],  alpha = -<<A;B>>,
+// so X^C is needed at the shifts z, -z, z*, -z* (two of them when gamma = 0, one at z = 0).
+static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, double gamma, int ncomp,
+                               const int *comps, double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0) || !(gamma >= 0))
     return (cclr_status)fail(CCLR_EINVAL, "bad solve arguments");
   for (int k = 0; k < ncomp; ++k)
     if (comps[k] < 0 || comps[k] > 2) return (cclr_status)fail(CCLR_EINVAL, "component out of range");
@@ -985,29 +991,43 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
     int calls0 = c->sigma_calls;
     c->ensure_lambda(tol, diis_depth, &loc);
     for (int w = 0; w < nomega; ++w) {
-      const double om = omegas[w];
-      const int nsign = om == 0.0 ? 1 : 2;
-      // X^C(s*omega) for every component and sign
-      std::vector<AVec> X((size_t)ncomp * 2);
+      const zd z(omegas[w], gamma);
+      // distinct shifts among z, -z, z*, -z*; slot[k] = index of the shift used for the k-th
+      const zd want[4] = {z, -z, std::conj(z), -std::conj(z)};
+      std::vector<zd> shifts;
+      int slot[4];
+      for (int k = 0; k < 4; ++k) {
+        int f = -1;
+        for (size_t q = 0; q < shifts.size(); ++q)
+          if (shifts[q] == want[k]) f = (int)q;
+        if (f < 0) {
+          f = (int)shifts.size();
+          shifts.push_back(want[k]);
+        }
+        slot[k] = f;
+      }
+      const int ns = (int)shifts.size();
+      std::vector<AVec> X((size_t)ncomp * ns);
+      auto Xs = [&](int a, int k) -> AVec & { return X[(size_t)a * ns + slot[k]]; };
       auto t0 = std::chrono::steady_clock::now();
+      std::vector<AVec> B(ncomp);
+      for (int a = 0; a < ncomp; ++a) {
+        c->alloc_vec(B[a]);
+        c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, B[a].b.p);
+        c->scal(zd(-1), B[a].b.p);
+        for (int q = 0; q < ns; ++q) c->alloc_vec(X[(size_t)a * ns + q]);
+      }
       if (c->method == 2) {
-        // every component and sign in one block: the operator is applied to all of them at once
-        std::vector<AVec> B(ncomp);
-        std::vector<double> oms;
+        // every component and shift in one block: the operator is applied to all at once
+        std::vector<zd> oms;
         std::vector<const void *> bs;
         std::vector<void *> xs;
-        for (int a = 0; a < ncomp; ++a) {
-          c->alloc_vec(B[a]);
-          c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, B[a].b.p);
-          c->scal(zd(-1), B[a].b.p);
-          for (int s = 0; s < nsign; ++s) {
-            AVec &x = X[(size_t)a * 2 + s];
-            c->alloc_vec(x);
-            oms.push_back(s == 0 ? om : -om);
+        for (int a = 0; a < ncomp; ++a)
+          for (int q = 0; q < ns; ++q) {
+            oms.push_back(shifts[q]);
             bs.push_back(B[a].b.p);
-            xs.push_back(x.b.p);
+            xs.push_back(X[(size_t)a * ns + q].b.p);
           }
-        }
         std::vector<int> its;
         std::vector<double> rels;
         c->solve_block(+1, oms, bs, xs, tol, c->maxit, its, rels);
@@ -1016,43 +1036,41 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
           loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
           if (!(rels[k] < tol)) loc.converged = 0;
         }
-      }
-      for (int a = 0; a < ncomp && c->method != 2; ++a) {
-        AVec b;
-        c->alloc_vec(b);
-        c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, b.b.p);
-        c->scal(zd(-1), b.b.p);
-        for (int s = 0; s < nsign; ++s) {
-          AVec &x = X[(size_t)a * 2 + s];
-          c->alloc_vec(x);
-          int its = 0;
-          double rel = c->solve(+1, s == 0 ? om : -om, b.b.p, x.b.p, tol, diis_depth, c->maxit, &its);
-          loc.iterations += its;
-          loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
-          if (!(rel < tol)) loc.converged = 0;
-        }
+      } else {
+        for (int a = 0; a < ncomp; ++a)
+          for (int q = 0; q < ns; ++q) {
+            int its = 0;
+            double rel = c->solve(+1, shifts[q], B[a].b.p, X[(size_t)a * ns + q].b.p, tol, diis_depth, c->maxit, &its);
+            loc.iterations += its;
+            loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
+            if (!(rel < tol)) loc.converged = 0;
+          }
       }
       auto t1 = std::chrono::steady_clock::now();
       loc.time_solve_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
-      auto Xs = [&](int a, int s) -> AVec & { return X[(size_t)a * 2 + (nsign == 1 ? 0 : s)]; };
-      // eta^A . X^B(s w) and F X^A(s w)
-      std::vector<zd> ED((size_t)ncomp * ncomp * 2);
+      // eta^A . X^B at every shift, and F X^A at -z (for g(z)) and z* (for g(-z*))
+      std::vector<zd> ED((size_t)ncomp * ncomp * ns);
       for (int a = 0; a < ncomp; ++a)
         for (int b = 0; b < ncomp; ++b)
-          for (int s = 0; s < nsign; ++s) ED[((size_t)a * ncomp + b) * 2 + s] = c->eta_dot(comps[a], Xs(b, s).b.p);
-      std::vector<AVec> FX((size_t)ncomp * 2);
-      for (int a = 0; a < ncomp; ++a)
-        for (int s = 0; s < nsign; ++s) {
-          c->alloc_vec(FX[(size_t)a * 2 + s]);
-          c->fx(Xs(a, s).b.p, FX[(size_t)a * 2 + s].b.p);
+          for (int q = 0; q < ns; ++q)
+            ED[((size_t)a * ncomp + b) * ns + q] = c->eta_dot(comps[a], X[(size_t)b * ns + q].b.p);
+      auto EDs = [&](int a, int b, int k) { return ED[((size_t)a * ncomp + b) * ns + slot[k]]; };
+      std::vector<AVec> FX((size_t)ncomp * ns);
+      std::vector<char> have((size_t)ncomp * ns, 0);
+      auto FXs = [&](int a, int k) -> AVec & {
+        const size_t id = (size_t)a * ns + slot[k];
+        if (!have[id]) {
+          c->alloc_vec(FX[id]);
+          c->fx(X[id].b.p, FX[id].b.p);
+          have[id] = 1;
         }
-      auto FXs = [&](int a, int s) -> AVec & { return FX[(size_t)a * 2 + (nsign == 1 ? 0 : s)]; };
-      auto EDs = [&](int a, int b, int s) { return ED[((size_t)a * ncomp + b) * 2 + (nsign == 1 ? 0 : s)]; };
+        return FX[id];
+      };
       for (int a = 0; a < ncomp; ++a)
         for (int b = 0; b < ncomp; ++b) {
-          // g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w)
+          // k: 0 = z, 1 = -z, 2 = z*, 3 = -z*
           zd gp = EDs(a, b, 0) + EDs(b, a, 1) + c->dot(FXs(a, 1).b.p, Xs(b, 0).b.p, 0);
-          zd gm = EDs(a, b, 1) + EDs(b, a, 0) + c->dot(FXs(a, 0).b.p, Xs(b, 1).b.p, 0);
+          zd gm = EDs(a, b, 3) + EDs(b, a, 2) + c->dot(FXs(a, 2).b.p, Xs(b, 3).b.p, 0);
           zd al = -0.5 * (gp + std::conj(gm));
           size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
           alpha[k] = al.real();
@@ -1066,6 +1084,16 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
   if (stats) *stats = loc;
   if (st != CCLR_OK) return (cclr_status)st;
   return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve: tolerance not met");
+}
+
+cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
+                        double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  return solve_alpha(c, nomega, omegas, 0.0, ncomp, comps, tol, diis_depth, alpha, stats);
+}
+
+cclr_status cc_lr_solve_damped(cclr_ctx *c, int nomega, const double *omegas, double gamma, int ncomp,
+                               const int *comps, double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  return solve_alpha(c, nomega, omegas, gamma, ncomp, comps, tol, diis_depth, alpha, stats);
 }
 
 cclr_status cc_lr_get_t(cclr_ctx *c, double *t1, double *t2) {

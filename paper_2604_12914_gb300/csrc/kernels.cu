@@ -562,25 +562,33 @@ void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 
 
 // Delta = r / (D - omega), D real; in place allowed.
 template <typename T>
-__global__ void precond_kernel(int64_t n, const double *D, double omega,
+__global__ void precond_kernel(int64_t n, const double *D, double omega, double omega_im,
                                const typename cpx<T>::t *r, typename cpx<T>::t *out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double d = D[i] - omega;
-    if (fabs(d) < 1e-8) d = d < 0 ? -1e-8 : 1e-8;
     auto v = r[i];
     typename cpx<T>::t o;
-    o.x = (T)(v.x / d);
-    o.y = (T)(v.y / d);
+    if (omega_im == 0.0) {
+      double d = D[i] - omega;
+      if (fabs(d) < 1e-8) d = d < 0 ? -1e-8 : 1e-8;
+      o.x = (T)(v.x / d);
+      o.y = (T)(v.y / d);
+    } else {  // v / (d - i w_im) = v (d + i w_im) / (d^2 + w_im^2)
+      const double d = D[i] - omega, q = 1.0 / (d * d + omega_im * omega_im);
+      o.x = (T)((v.x * d - v.y * omega_im) * q);
+      o.y = (T)((v.y * d + v.x * omega_im) * q);
+    }
     out[i] = o;
   }
 }
 
-void vec_precond(int dt, int64_t n, const double *D, double omega, const void *r, void *out,
+void vec_precond(int dt, int64_t n, const double *D, double omega, double omega_im, const void *r, void *out,
                  cudaStream_t st) {
   if (n <= 0) return;
-  if (dt == C128) precond_kernel<double><<<grid_for(n), 256, 0, st>>>(n, D, omega, (const double2 *)r, (double2 *)out);
-  else precond_kernel<float><<<grid_for(n), 256, 0, st>>>(n, D, omega, (const float2 *)r, (float2 *)out);
+  if (dt == C128)
+    precond_kernel<double><<<grid_for(n), 256, 0, st>>>(n, D, omega, omega_im, (const double2 *)r, (double2 *)out);
+  else
+    precond_kernel<float><<<grid_for(n), 256, 0, st>>>(n, D, omega, omega_im, (const float2 *)r, (float2 *)out);
   count_launch();
     CCLR_CUDA(cudaGetLastError());
 }

@@ -46,7 +46,8 @@ void vec_axpy(int dt, int64_t n, zc a, const void *x, void *y, cudaStream_t st);
 void vec_scal(int dt, int64_t n, zc a, void *y, cudaStream_t st);
 void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 *part,
              double2 *out, int slot, cudaStream_t st);
-void vec_precond(int dt, int64_t n, const double *D, double omega, const void *r, void *out,
+// out = r / (D - (omega + i omega_im))
+void vec_precond(int dt, int64_t n, const double *D, double omega, double omega_im, const void *r, void *out,
                  cudaStream_t st);
 void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2,
                 cudaStream_t st);

@@ -369,3 +369,41 @@ def test_stored_ladder_ablation_matches_on_the_fly(prec, tol):
     r1, r2 = oracle_sigma(s, t1, t2, x1[0], x2[0])
     assert rel_err(g1[0], g2[0], r1, r2) < (3e-3 if prec == "tf32" else 5e-5)
     ctx.close()
+
+
+@pytest.mark.parametrize("method,prec", [("gmres", "fp64"), ("block", "fp64"), ("block", "tf32")])
+def test_damped_alpha_matches_oracle(method, prec):
+    """Damped response at z = omega + i gamma (complex shift in the solver and preconditioner)
+    against the oracle's damped alpha; mixed precision with tensor-core refinement."""
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy(), prec=prec)
+    ctx.cc_lr_set_solver(method)
+    if prec != "fp64":
+        ctx.cc_lr_set_refinement("3xtf32")
+    mu = [as_t(m) for m in s.mu]
+    for omega, gamma in [(0.0428, 0.01), (0.0, 0.05)]:
+        al, st = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-10 if prec == "fp64" else 1e-6, gamma=gamma)
+        ref = R.alpha(P, mu, omega, gamma=gamma).numpy()
+        err = np.abs(al[0] - ref).max()
+        print(f"{method}/{prec} z={omega}+{gamma}i: |delta alpha| {err:.2e}, {st}")
+        assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
+    ctx.close()
+
+
+def test_damped_alpha_two_electrons_equals_sum_over_states():
+    """o=2: the GPU damped alpha equals the exact sum over states at complex frequency."""
+    s = make_system(2, 4, 6, seed=2, scale=0.3)
+    f, g, L, _, _ = oracle_setup(s, np.zeros((2, 4)), np.zeros((2, 2, 4, 4)))
+    t1, t2, _ = R.solve_ccsd(f, g, 2, L=L)
+    ctx = gpu_context(s, t1=t1.numpy(), t2=t2.numpy())
+    bf = secondq.BruteForce(f.numpy(), g.numpy(), 2)
+    w, U = bf.fci()
+    st, _ = secondq.cc_state_overlap(U, t1.numpy(), t2.numpy(), bf)
+    ops = [bf.one_body_op(m) for m in s.mu]
+    for omega, gamma in [(0.0428, 0.01), (0.7, 0.02)]:
+        al, _ = ctx.cc_lr_solve([omega], (0, 1, 2), tol=1e-12, gamma=gamma)
+        z = complex(omega, gamma)
+        sos = np.array([[-secondq.sos_response(w, U, ops[a], ops[b], z, st) for b in range(3)]
+                        for a in range(3)])
+        assert np.abs(al[0] - sos).max() < 1e-7 * np.abs(sos).max()
+    ctx.close()
