@@ -14,6 +14,13 @@ namespace cclr {
 
 class LadderTC {
  public:
+  LadderTC() = default;
+  LadderTC(const LadderTC &) = delete;
+  LadderTC &operator=(const LadderTC &) = delete;
+  ~LadderTC() {
+    for (auto e : fev)
+      if (e) cudaEventDestroy(e);
+  }
   // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (TF32) or 3 (3xTF32).
   void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg);
   bool ready(int seg) const { return seg_ == seg && LA.p != nullptr; }

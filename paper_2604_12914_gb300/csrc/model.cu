@@ -21,7 +21,11 @@ Model::Model(int o_, int v_, int naux_, cudaStream_t st_)
   prog = build_sigma_program(o, v, naux);
 }
 
-Model::~Model() { clear_graphs(); }
+Model::~Model() {
+  clear_graphs();
+  if (tm.made)
+    for (auto &e : tm.ev) cudaEventDestroy(e);
+}
 
 static void h2d_or_d2d(void *dst, const void *src, size_t bytes, int device_ptrs, cudaStream_t st) {
   (void)device_ptrs;  // unified addressing: the copy direction follows from the pointers

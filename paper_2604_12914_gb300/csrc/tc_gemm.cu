@@ -488,9 +488,10 @@ __global__ void prep_tiled_kernel(const float2 *src, View2 mnv, View2 kv, int64_
   }
 }
 
-int *g_err = nullptr;
-std::once_flag g_once;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+constexpr int kMaxDevs = 64;
+int *g_err_dev[kMaxDevs] = {};  // bounded-wait flag, one per device
+std::mutex g_dev_mu;
 
 std::once_flag g_enc_once;
 
@@ -504,11 +505,27 @@ void fetch_encoder() {
   g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
 }
 
-void init_once() {
-  std::call_once(g_enc_once, fetch_encoder);
-  CCLR_CUDA(cudaMalloc(&g_err, sizeof(int)));
-  CCLR_CUDA(cudaMemset(g_err, 0, sizeof(int)));
-  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+int current_device() {
+  int dev = 0;
+  CCLR_CUDA(cudaGetDevice(&dev));
+  CCLR_REQUIRE(dev >= 0 && dev < kMaxDevs, "device ordinal beyond 63");
+  return dev;
+}
+
+// The current device's wait flag; the first use on a device allocates and clears it and raises
+// the kernel's shared-memory limit there.
+int *device_err() {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_dev_mu);
+  if (!g_err_dev[dev]) {
+    std::call_once(g_enc_once, fetch_encoder);
+    int *p = nullptr;
+    CCLR_CUDA(cudaMalloc(&p, sizeof(int)));
+    CCLR_CUDA(cudaMemset(p, 0, sizeof(int)));
+    CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    g_err_dev[dev] = p;
+  }
+  return g_err_dev[dev];
 }
 
 CUtensorMap make_map(const float *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
@@ -663,8 +680,7 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
 static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
                          int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
                          int max_kb_per_split, cudaStream_t st) {
-  std::call_once(g_once, init_once);
-  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kreal, C, rv, cv, alpha, accumulate, max_kb_per_split, g_err, st);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kreal, C, rv, cv, alpha, accumulate, max_kb_per_split, device_err(), st);
 }
 
 void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
@@ -688,9 +704,8 @@ void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int
 
 void tc_gemm_a_inplace(const void *A, int64_t lda_cpx, int64_t K, const float *B, int64_t ldb, int64_t M,
                        int64_t Nreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st) {
-  std::call_once(g_once, init_once);
   tc_gemm_core((const float *)A, 2 * lda_cpx, B, ldb, M, Nreal, 2 * tc_kpad(K), C, rv, cv, alpha, accumulate, 0,
-               g_err, st, 2 * K);
+               device_err(), st, 2 * K);
 }
 
 bool tc_a_inplace_ok(const void *A, int64_t lda_cpx, int64_t K) {
@@ -722,14 +737,19 @@ void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ld
 }
 
 int tc_selftest_timeout(int timeout_us, cudaStream_t st) {
-  std::call_once(g_once, init_once);
-  wait_never_kernel<<<1, 32, 0, st>>>((unsigned long long)timeout_us * 1000ull, g_err);
+  wait_never_kernel<<<1, 32, 0, st>>>((unsigned long long)timeout_us * 1000ull, device_err());
   count_launch();
   CCLR_CUDA(cudaGetLastError());
   return tc_error(st);
 }
 
 int tc_error(cudaStream_t st) {
+  int *g_err = nullptr;
+  {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lock(g_dev_mu);
+    g_err = g_err_dev[dev];
+  }
   if (!g_err) return 0;
   int h = 0;
   CCLR_CUDA(cudaMemcpyAsync(&h, g_err, sizeof(int), cudaMemcpyDeviceToHost, st));
