@@ -8,6 +8,12 @@ integrals with more than two virtual indices are built on the fly).  Nothing of 
 or v^4 is ever held, so this runs at the full workload sizes where the explicit tensors of
 ``jacobian`` do not fit; its cost is O(o^2 v^2 + naux v^2) per entry.  It is pinned against
 ``jacobian.sigma_terms`` entry by entry at small sizes.
+
+The same terms vectorised over whole blocks: ``sigma1_all`` (every singles entry),
+``sigma_rest`` (every term but the particle-particle ladder) and ``sigma_blocked`` (the whole
+vector, the ladder's <ab|ef>~ formed chunk by chunk of a from L~_vv, never held whole).  They
+are the oracle's whole-vector sigma at sizes where the v^4 tensor does not fit, and the CPU
+timing of one sigma; pinned against ``jacobian.sigma_terms`` at small sizes.
 """
 from __future__ import annotations
 
@@ -155,3 +161,81 @@ class EntrySigma:
         val = val + 0.5 * (t2[:, :, a, b] * self.Z_ij(i, j)).sum()
         val = val + ring(i, j, a, b) - ring(j, i, a, b) - ring(i, j, b, a) + ring(j, i, b, a)
         return val
+
+    # ---- whole vectors, vectorised over entries (same terms as sigma1 / sigma2 above)
+    def sigma1_all(self):
+        """Every singles entry sigma_1[i, a] at once: the terms of sigma1() with the sums over
+        (i, a) written as one einsum each (Wovvo is formed whole: o^2 v^2 entries)."""
+        x1, x2 = self.x1, self.x2
+        Wovvo = self.Wovvo_full()
+        Zp = ein("Pmf,imef->iPe", self.Lov, x2)
+        return (ein("ae,ie->ia", self.Fvv, x1) - ein("mi,ma->ia", self.Foo, x1)
+                + ein("maei,me->ia", Wovvo, x1)
+                + ein("me,imae->ia", self.fov, x2)
+                + ein("Pae,iPe->ia", self.Lvv, Zp)
+                - 0.5 * ein("mnie,mnae->ia", self.ooov, x2))
+
+    def Wovvo_full(self):
+        """Wovvo[m, b, e, j] = <mb||ej>~ - sum_nf <mn||ef> t_jn^fb (every (b, j) of Wovvo_bj)."""
+        if getattr(self, "_wovvo", None) is None:
+            self._wovvo = (ein("Pme,Pbj->mbej", self.Lov, self.Lvo) - ein("Pmj,Pbe->mbej", self.Loo, self.Lvv)
+                           - ein("mnef,jnfb->mbej", self.oovv, self.t2))
+        return self._wovvo
+
+    def Wovoo_full(self, b_chunk=16):
+        """Wovoo[m, b, i, j] for every (b, i, j) (the terms of Wovoo_bij); the <mb|ef>~ t_ij^ef
+        part is formed in chunks of b from L~ (no tensor with three virtual indices is held
+        whole)."""
+        t2 = self.t2
+        w = (ein("Pmi,Pbj->mbij", self.Loo, self.Lvo) - ein("Pmj,Pbi->mbij", self.Loo, self.Lvo)
+             - ein("me,ijbe->mbij", self.fov, t2)
+             + ein("mnie,jnbe->mbij", self.ooov, t2) - ein("mnje,inbe->mbij", self.ooov, t2))
+        for b0 in range(0, self.nv, b_chunk):
+            b1 = min(self.nv, b0 + b_chunk)
+            G = ein("Pme,Pbf->mbef", self.Lov, self.Lvv[:, b0:b1])    # <mb|ef>~ for the chunk
+            w[:, b0:b1] += ein("mbef,ijef->mbij", G, t2)
+        return w
+
+    def wx_all(self):
+        """WX[i, j, a, b] = sum_e Wvvvo[a, b, e, j] x_i^e for every entry (the terms of Wvvvo_abj
+        with the sum over e taken first: U = L~_ae x_ie, s = L~_me x_ie, V_mbif = <mb||ef>~ x_ie)."""
+        x1, t2 = self.x1, self.t2
+        U = ein("Pae,ie->Pai", self.Lvv, x1)
+        s = ein("Pme,ie->Pmi", self.Lov, x1)
+        c = ein("me,ie->mi", self.fov, x1)
+        d = ein("mnje,ie->mnji", self.ooov, x1)
+        V = ein("Pmi,Pbf->mbif", s, self.Lvv) - ein("Pmf,Pbi->mbif", self.Lov, U)
+        r = ein("Pai,Pbj->ijab", U, self.Lvo) - ein("Paj,Pbi->ijab", self.Lvo, U)
+        r = r - ein("mi,mjab->ijab", c, t2) - 0.5 * ein("mnji,mnab->ijab", d, t2)
+        r = r - ein("mbif,mjaf->ijab", V, t2) + ein("maif,mjbf->ijab", V, t2)
+        return r
+
+    def sigma_rest(self):
+        """sigma_1 and every sigma_2 term except the particle-particle ladder, vectorised."""
+        x1, x2, t2 = self.x1, self.x2, self.t2
+        s1 = self.sigma1_all()
+        Wovoo = self.Wovoo_full()
+        Wovvo = self.Wovvo_full()
+        Rab = (ein("be,ijae->ijab", self.Fvv, x2) - ein("mbij,ma->ijab", Wovoo, x1)
+               + ein("be,ijae->ijab", self.Xvv, t2))
+        Rij = (-ein("mj,imab->ijab", self.Foo, x2) + self.wx_all() - ein("mj,imab->ijab", self.Xoo, t2))
+        s2 = Rab - Rab.transpose(2, 3) + Rij - Rij.transpose(0, 1)
+        s2 = s2 + 0.5 * ein("mnij,mnab->ijab", self.Woooo, x2) + 0.5 * ein("mnab,mnij->ijab", t2, self.Z)
+        ring = ein("mbej,imae->ijab", Wovvo, x2)
+        s2 = s2 + ring - ring.transpose(0, 1) - ring.transpose(2, 3) + ring.transpose(0, 1).transpose(2, 3)
+        return s1, s2
+
+    def ladder_chunk(self, a0, a1, out):
+        """out[i, j, a, b] += sum_ef <ab|ef>~ X_ij^ef for a0 <= a < a1 (= 1/2 sum <ab||ef>~ X_ij^ef,
+        X antisymmetric in ef), with <ab|ef>~ = sum_P L~_ae L~_bf formed for the chunk only."""
+        g = ein("Pae,Pbf->abef", self.Lvv[:, a0:a1], self.Lvv)
+        out[:, :, a0:a1, :] += ein("abef,ijef->ijab", g, self.x2)
+
+    def sigma_blocked(self, a_chunk=8):
+        """The whole sigma = A X: sigma_rest plus the ladder formed chunk by chunk of a from L~_vv
+        (nothing with four virtual indices is held whole; the explicit-tensor term list of
+        jacobian.sigma_terms needs v^4 entries)."""
+        s1, s2 = self.sigma_rest()
+        for a0 in range(0, self.nv, a_chunk):
+            self.ladder_chunk(a0, min(self.nv, a0 + a_chunk), s2)
+        return s1, s2

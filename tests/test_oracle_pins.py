@@ -306,3 +306,45 @@ def test_entrywise_sigma_matches_term_list():
         a, b = rng.integers(0, v, 2)
         assert abs(E.sigma2(i, j, a, b) - q2[i, j, a, b]) < 1e-12 * sc
         assert abs(E.sigma1(i, a) - q1[i, a]) < 1e-12 * sc
+
+
+@pytest.mark.parametrize("o,v,naux,seed", [(3, 6, 8, 15), (4, 5, 11, 16)])
+def test_first_order_t2_from_L_matches_explicit_integrals(o, v, naux, seed):
+    """The Cholesky-direct first-order doubles (<ab|ij> = sum_P L^P_ai L^P_bj formed straight
+    from L, the reference for every full-size T2 check) equal first_order_t2 on the explicit
+    <pq||rs>, which the first-order-residual pin above fixes."""
+    s = _system(o, v, naux, seed=seed, scale=1.0)
+    L = as_t(s.L)
+    eps = as_t(s.eps)
+    ref = ccsd.first_order_t2(eps, eri_anti(L), o)
+    got = ccsd.first_order_t2_from_L(eps, L, o)
+    assert float((got - ref).abs().max()) < 1e-13 * float(ref.abs().max())
+    # antisymmetric in (i,j) and (a,b), and <ab||ij> / D entry by entry from the sum over P
+    assert float((got + got.transpose(0, 1)).abs().max()) < 1e-14 * float(ref.abs().max())
+    i, j, a, b = 0, o - 1, 1, v - 1
+    num = sum(s.L[P, o + a, i] * s.L[P, o + b, j] - s.L[P, o + a, j] * s.L[P, o + b, i] for P in range(naux))
+    den = s.eps[i] + s.eps[j] - s.eps[o + a] - s.eps[o + b]
+    assert abs(got[i, j, a, b].item() - num / den) < 1e-12 * abs(num / den)
+
+
+@pytest.mark.parametrize("t1_scale,a_chunk", [(0.0, 3), (0.2, 2)])
+def test_blocked_sigma_matches_term_list(t1_scale, a_chunk):
+    """oracle.sampled's vectorised whole-vector sigma (ladder formed chunk by chunk of a from L~,
+    ragged last chunk) and its all-singles block equal jacobian.sigma_terms, which the stencil
+    and the brute-force Jacobian pin."""
+    from oracle import sampled
+    o, v = 3, 7
+    s = _system(o, v, 9, seed=3, scale=0.5, t1_scale=t1_scale)
+    L = as_t(s.L)
+    f = torch.diag(as_t(s.eps).to(C))
+    _, a2 = random_amplitudes(o, v, seed=9, s1=0.2, s2=0.3)
+    t1, t2 = as_t(s.t1), as_t(a2)
+    x1, x2 = map(as_t, random_amplitudes(o, v, seed=11))
+    q1, q2 = J.sigma_terms(J.Dressed(f, L, t1, t2), x1, x2)
+    E = sampled.EntrySigma(as_t(s.eps), L, t1, t2)
+    E.set_x(x1, x2)
+    b1, b2 = E.sigma_blocked(a_chunk=a_chunk)
+    sc = float(q2.abs().max())
+    assert float((b1 - q1).abs().max()) < 1e-13 * sc
+    assert float((b2 - q2).abs().max()) < 1e-13 * sc
+    assert float((E.sigma1_all() - q1).abs().max()) < 1e-13 * sc
