@@ -57,9 +57,11 @@ typedef enum {
  * state, residuals, subspace algebra and alpha in FP64. */
 typedef enum {
   CCLR_FP64 = 0,
-  CCLR_C64_TF32 = 1,     /* one TF32 tensor-core pass                                   */
-  CCLR_C64_3XTF32 = 2,   /* split hi/lo TF32, three passes (about FP32 accuracy)        */
-  CCLR_C64_FP32 = 3      /* complex64 on FP32 CUDA cores (no tensor cores)              */
+  CCLR_C64_TF32 = 1,     /* one TF32 tensor-core pass (kind::tf32)                      */
+  CCLR_C64_3XTF32 = 2,   /* split hi/lo TF32, three products (about FP32 accuracy)      */
+  CCLR_C64_FP32 = 3,     /* complex64 on FP32 CUDA cores (no tensor cores)              */
+  CCLR_BF16X3 = 4        /* split hi/lo BF16, three products on kind::f16 (about 2^-16
+                            relative per product, at twice the TF32 rate per pass)     */
 } cclr_prec;
 
 typedef struct {
@@ -77,7 +79,12 @@ typedef struct {
  * build the stored intermediates (integrals with at most two virtual indices, the
  * one-body and o^2v^2 / o^3v / o^4 elements of H-bar) and the diagonal preconditioner.
  * lam1/lam2 ([o][v], [o][o][v][v]) give the ground-state Lambda; NULL means it is
- * solved on first use (lambda A = -dE/dT).  hbm_budget_bytes = 0: no limit.
+ * solved on first use (lambda A = -dE/dT).
+ * hbm_budget_bytes: the most device memory the context may hold (0 = no limit).  Every
+ * device allocation the context makes -- at init and later, in any call on it (workspace,
+ * solver vectors, ladder blocks, graph staging) -- is charged to it and checked before it is
+ * made; a call that would exceed the budget returns CCLR_ENOMEM and allocates nothing more
+ * (cc_lr_memory reports the bytes held).
  * cuda_stream: a cudaStream_t (NULL: the legacy default stream). */
 cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux,
                        const double *eps, const double *L, const double *mu,
@@ -114,6 +121,22 @@ cclr_status cc_lr_solve(cclr_ctx *ctx, int nomega, const double *omegas, int nco
                         const int *comps, double tol, int diis_depth, double *alpha,
                         cclr_stats *stats);
 
+/* The same alpha by the left-hand route of Sec. 2.2 (the response function written with the
+ * perturbed left amplitudes Y): X^B(w) from (A - w) X = -xi^B, Y^B(w) from
+ * Y (A + w) = -(eta^B + F X^B(w)) (transpose products, shift -w), and
+ * g(A,B;w) = Y^B(w) . xi^A + eta^A . X^B(w), <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)].
+ * Equal to cc_lr_solve's alpha within the solver tolerance ("alpha from both sides").  Same
+ * arguments, outputs and error behaviour as cc_lr_solve (real omega only). */
+cclr_status cc_lr_solve_left(cclr_ctx *ctx, int nomega, const double *omegas, int ncomp,
+                             const int *comps, double tol, int diis_depth, double *alpha,
+                             cclr_stats *stats);
+
+/* eta^A = <(1 + Lambda)|[A-bar, tau_nu]|Phi_0> (Sec. 2.2) for component comp as a vector:
+ * eta1 [o][v], eta2 [o][o][v][v] (full antisymmetric).  Formed as dE_A/dT + lambda A[mu^A], with
+ * A[mu^A] the Jacobian of the dipole operator alone; solves the ground-state Lambda first
+ * (relative residual tol) if it is not known. */
+cclr_status cc_lr_eta(cclr_ctx *ctx, int comp, double tol, double *eta1, double *eta2);
+
 /* Damped response (complex frequency z = omega + i gamma, gamma >= 0; the pole widths and
  * absorption of Sec. 2.2's response function continued off the real axis): the same as
  * cc_lr_solve with X^C solved at the complex shifts z, -z, z*, -z* ((A - s) X = -xi^C, complex
@@ -146,8 +169,8 @@ cclr_status cc_lr_set_precision(cclr_ctx *ctx, int prec);
  * otherwise. */
 cclr_status cc_lr_set_graphs(cclr_ctx *ctx, int on);
 
-/* Result of the pp-ladder autotuner for the tensor-core mode prec (CCLR_C64_TF32 or
- * CCLR_C64_3XTF32): on its first use in that mode the ladder times one product per candidate
+/* Result of the pp-ladder autotuner for the tensor-core mode prec (CCLR_C64_TF32,
+ * CCLR_C64_3XTF32 or CCLR_BF16X3): on its first use in that mode the ladder times one product per candidate
  * group size (how many a values each formed <ab|ef>~ block covers) and keeps the fastest.
  * Writes the group size in use, the number of candidates timed (*n; 0 before the first use)
  * and up to cap of them (candidate group size, milliseconds). */
@@ -185,6 +208,10 @@ cclr_status cc_lr_set_refinement(cclr_ctx *ctx, int prec);
  * each linear solve (default 300; 0 keeps the current value); a solve that reaches it
  * returns CCLR_ENOCONV with its best iterate. */
 cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace, int max_iterations);
+
+/* Device memory held by the context now (*in_use), the most it has held (*peak), and its
+ * budget (*budget, 0 = none), in bytes.  Host-side bookkeeping only (no device call). */
+cclr_status cc_lr_memory(cclr_ctx *ctx, size_t *in_use, size_t *peak, size_t *budget);
 
 /* Device-side timing (CUDA events on the context's stream) of the last sigma or
  * sigma^T product, in milliseconds; writes the first min(n, 4) of: [0] particle-particle

@@ -9,8 +9,8 @@ extern "C" {
 #endif
 
 /* Complex64 GEMM C[M][N] = A[M][K] B[K][N] on seeded random data, computed three ways
- * on the current device: tcgen05 tensor cores (mode 1 TF32, mode 2 3xTF32), FP32 CUDA
- * cores, and FP64 CUDA cores (reference).  Writes max|C_x - C_ref| / max|C_ref| for the
+ * on the current device: tcgen05 tensor cores (mode 1 TF32, mode 2 3xTF32, mode 3 bf16x3),
+ * FP32 CUDA cores, and FP64 CUDA cores (reference).  Writes max|C_x - C_ref| / max|C_ref| for the
  * tensor-core (err[0]) and FP32 (err[1]) results.  Returns 0 on success, else a
  * cclr_status code. */
 int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *err);

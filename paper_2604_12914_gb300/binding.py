@@ -17,14 +17,15 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcclr.so")
 
 CCLR_OK, CCLR_EINVAL, CCLR_ENOMEM, CCLR_ENOCONV, CCLR_EDEVICE, CCLR_ETIMEOUT, CCLR_EUNSUPPORTED = range(7)
-CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32 = range(4)
-PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32}
+CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32, CCLR_BF16X3 = range(5)
+PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32,
+        "bf16x3": CCLR_BF16X3}
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
-           "cc_lr_solve_damped",
+           "cc_lr_solve_damped", "cc_lr_solve_left", "cc_lr_eta",
            "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
            "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_ladder_storage", "cc_lr_set_solver",
-           "cc_lr_last_timings",
+           "cc_lr_last_timings", "cc_lr_memory",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
 
@@ -64,6 +65,8 @@ def load(path: str = LIB_PATH):
         "cc_lr_solve_x": [P, D, I, D, I, P, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve_damped": [P, I, P, D, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
+        "cc_lr_solve_left": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
+        "cc_lr_eta": [P, I, D, P, P],
         "cc_lr_lambda": [P, D, P, P],
         "cc_lr_get_t": [P, P, P],
         "cc_lr_set_precision": [P, I],
@@ -74,6 +77,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_graph_stats": [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)],
         "cc_lr_ladder_tuning": [P, I, ctypes.POINTER(ctypes.c_int), I, P, P, ctypes.POINTER(ctypes.c_int)],
         "cc_lr_last_timings": [P, P, I],
+        "cc_lr_memory": [P, ctypes.POINTER(S), ctypes.POINTER(S), ctypes.POINTER(S)],
         "cc_lr_free": [P],
         "cc_lr_strerror": [I],
         "cc_lr_last_error": [],
@@ -219,6 +223,26 @@ class Context:
         d["status"] = status
         return out, d
 
+    def cc_lr_solve_left(self, omegas, comps=(0, 1, 2), tol=1e-10, diis_depth=8, allow_noconv=False):
+        """alpha[w][a][b] by the left-hand (Y) route."""
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        cp = np.ascontiguousarray(comps, dtype=np.int32)
+        out = np.zeros((len(om), len(cp), len(cp)), dtype=np.complex128)
+        st = cclr_stats()
+        status = _check(load().cc_lr_solve_left(self._h, len(om), _ptr(om), len(cp), _ptr(cp), float(tol), diis_depth,
+                                                _ptr(out), ctypes.byref(st)),
+                        allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["status"] = status
+        return out, d
+
+    def cc_lr_eta(self, comp, tol=1e-10):
+        o, v = self.o, self.v
+        e1 = self._out((o, v))
+        e2 = self._out((o, o, v, v))
+        _check(load().cc_lr_eta(self._h, comp, float(tol), _ptr(e1), _ptr(e2)))
+        return e1, e2
+
     def cc_lr_lambda(self, tol=1e-10):
         o, v = self.o, self.v
         l1 = self._out((o, v))
@@ -267,6 +291,12 @@ class Context:
     def cc_lr_set_solver(self, method="gmres", subspace=30, max_iterations=0):
         m = {"gmres": 1, "diis": 0, "block": 2}[method] if isinstance(method, str) else int(method)
         _check(load().cc_lr_set_solver(self._h, m, int(subspace), int(max_iterations)))
+
+    def cc_lr_memory(self):
+        """(bytes held, peak bytes held, budget) of this context's device memory."""
+        a, b, c = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
+        _check(load().cc_lr_memory(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+        return a.value, b.value, c.value
 
     def cc_lr_last_timings(self):
         """[ladder, everything else, total, ladder formation GEMMs] of the last product (ms)."""

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 ROOT = os.path.dirname(HERE)
 OUT = os.path.join(HERE, "libcclr.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["kernels.cu", "engine.cu", "model.cu", "capi.cu", "tc_gemm.cu", "ladder_tc.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "engine.cu", "model.cu", "capi.cu", "tc_gemm.cu", "ladder_tc.cu", "ladder_cc.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -26,7 +26,9 @@ int fail(int status, const std::string &msg) {
   return status;
 }
 
-// Amplitude vector: singles [o][v] then doubles [o][o][v][v], complex128, contiguous.
+// Amplitude vector, complex128, contiguous: singles [o][v] then the doubles block -- packed
+// unique amplitudes [(i<j)][(a<b)] for the solver's vectors, the full [o][o][v][v] tensor for
+// boundary staging.
 struct AVec {
   DevBuf b;
   void *p1() const { return b.p; }
@@ -35,23 +37,29 @@ struct AVec {
 }  // namespace
 
 struct cclr_ctx {
+  MemAcct acct;                   // device memory of this context (first member: released last)
   std::unique_ptr<Model> M;
   int o = 0, v = 0, naux = 0;
-  int64_t n1 = 0, n2 = 0;
+  int64_t n1 = 0, n2 = 0, n2p = 0;  // singles, full doubles o^2 v^2, packed doubles P_o P_v
   int device_ptrs = 0;
   cudaStream_t st = nullptr;
-  size_t budget = 0;
   bool have_lambda = false;
-  AVec lam;
-  std::vector<AVec> stage_in, stage_out;  // host <-> device staging (complex128), per RHS
+  AVec lam;                       // ground-state Lambda (packed)
+  AVec fullA, fullB;              // full-layout complex128 scratch (xi, shifted amplitudes, unpacking)
+  std::vector<AVec> stage_in, stage_out;  // host <-> device staging (full complex128), per RHS
   CstSet shift;                   // intermediates at shifted amplitudes (F X stencils)
+  CstSet onebody[3];              // H-bar of each dipole component alone (eta^A = lambda A[mu^A])
+  AVec eta_v[3];                  // eta^A vectors (packed), formed once lambda is known
+  bool eta_ok[3] = {false, false, false};
   CstSet shift64;                 // their complex64 rounding (tensor-core F X stencils)
   // arithmetic of the mixed modes' accurate sigma products: the refinement residuals, the
   // final polish and the F X stencils (CCLR_FP64, or CCLR_C64_3XTF32 on the tensor cores)
   int hi_prec = CCLR_FP64;
   int sigma_calls = 0;
 
-  int64_t ntot() const { return n1 + n2; }
+  // length of a solver vector (packed) and of a full-layout vector
+  int64_t ntot() const { return n1 + n2p; }
+  int64_t nfull() const { return n1 + n2; }
   // CCLR_VERBOSE=1 prints solver residual histories to stderr (diagnostics)
   static bool verbose() {
     static const bool v = std::getenv("CCLR_VERBOSE") && std::getenv("CCLR_VERBOSE")[0] == '1';
@@ -59,17 +67,17 @@ struct cclr_ctx {
   }
 
   void alloc_vec(AVec &v_) { if (!v_.b.p) v_.b.alloc((size_t)ntot() * 16); }
+  void alloc_full(AVec &v_) { if (!v_.b.p) v_.b.alloc((size_t)nfull() * 16); }
 
-  // weighted dot: sum_ia conj?(a) b + 1/4 sum_ijab conj?(a) b, FP64 accumulation
+  // bilinear (herm = 0) or Hermitian (herm = 1) product over unique amplitudes, FP64 accumulation
   zd dot(const void *a, const void *b, int herm) {
     double2 *part = M->E.dot_scratch();
     double2 *res = M->E.dot_results();
-    vec_dot(C128, n1, a, b, herm, part, res, 0, st);
-    vec_dot(C128, n2, (const char *)a + n1 * 16, (const char *)b + n1 * 16, herm, part, res, 1, st);
-    double2 h[2];
-    CCLR_CUDA(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
+    vec_dot(C128, ntot(), a, b, herm, part, res, 0, st);
+    double2 h;
+    CCLR_CUDA(cudaMemcpyAsync(&h, res, sizeof(h), cudaMemcpyDeviceToHost, st));
     CCLR_CUDA(cudaStreamSynchronize(st));
-    return zd(h[0].x, h[0].y) + 0.25 * zd(h[1].x, h[1].y);
+    return zd(h.x, h.y);
   }
   double norm(const void *a) { return std::sqrt(std::max(0.0, dot(a, a, 1).real())); }
   void axpy(zd a, const void *x, void *y) { vec_axpy(C128, ntot(), zc(a.real(), a.imag()), x, y, st); }
@@ -77,46 +85,71 @@ struct cclr_ctx {
   void scal(zd a, void *y) { vec_scal(C128, ntot(), zc(a.real(), a.imag()), y, st); }
   void precond(zd omega, const void *r, void *out) {
     vec_precond(C128, n1, M->D1.as<double>(), omega.real(), omega.imag(), r, out, st);
-    vec_precond(C128, n2, M->D2.as<double>(), omega.real(), omega.imag(), (const char *)r + n1 * 16,
+    vec_precond(C128, n2p, M->D2.as<double>(), omega.real(), omega.imag(), (const char *)r + n1 * 16,
                 (char *)out + n1 * 16, st);
   }
+  // packed <-> full layouts (complex128 packed; the full side in dtype dt)
+  void unpack_to(const void *packed, void *full, int dt) {
+    M->E.permute(zc(1), make_tens((void *)packed, C128, {n1}), "a", make_tens(full, dt, {n1}), "a", false);
+    unpack_doubles(C128, dt, o, v, (const char *)packed + n1 * 16, (char *)full + n1 * dt_size(dt), zc(1), false, st);
+  }
+  void pack_from(const void *full, int dt, void *packed) {
+    M->E.permute(zc(1), make_tens((void *)full, dt, {n1}), "a", make_tens(packed, C128, {n1}), "a", false);
+    pack_doubles(dt, C128, o, v, (const char *)full + n1 * dt_size(dt), (char *)packed + n1 * 16, st);
+  }
 
-  // s = A x (dir +1) or x A (dir -1) in the current precision; x, s complex128 amplitude vectors
+  // s = A x (dir +1) or x A (dir -1) in the current precision; x, s packed complex128 vectors
   void op(int dir, const void *x, void *s, const CstSet *set = nullptr) { op_batch(dir, 1, &x, &s, set); }
 
-  // the same for nr vectors at once (the ladder's integral blocks are formed once for all)
-  std::vector<DevBuf> x64, s64;   // complex64 copies for the mixed-precision sigma
-  std::vector<DevBuf> x128, s128; // fixed staging of FP64 sigma arguments when graphs are on
+  // the same for nr packed vectors at once (the ladder's integral blocks are formed once for
+  // all): each is unpacked into a fixed full-layout buffer in the set's precision, the sigma
+  // program runs on those, and the results are packed back.  The buffers stay at fixed
+  // addresses, so repeated products can replay one captured CUDA graph.
+  std::vector<DevBuf> xfs[2], sfs[2];  // full-layout operands of the sigma program, per dtype and RHS
+  void stage_full(int dt, int nr) {
+    auto &xf = xfs[dt], &sf = sfs[dt];
+    if ((int)xf.size() < nr) { xf.resize(nr); sf.resize(nr); }
+    for (int r = 0; r < nr; ++r)
+      if (!xf[r].p) { xf[r].alloc((size_t)nfull() * dt_size(dt)); sf[r].alloc((size_t)nfull() * dt_size(dt)); }
+  }
   void op_batch(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set = nullptr) {
     sigma_calls += nr;
     if (set == nullptr) set = &M->cst_for(M->prec);
+    const int dt = set->dt;
+    const size_t es = dt_size(dt);
+    stage_full(dt, nr);
+    auto &xf = xfs[dt], &sf = sfs[dt];
     std::vector<const void *> a1(nr), a2(nr);
     std::vector<void *> b1(nr), b2(nr);
-    const size_t es = set->dt == C128 ? 16 : 8;
-    if (set->dt == C64 && (int)x64.size() < nr) {
-      x64.resize(nr);
-      s64.resize(nr);
+    for (int r = 0; r < nr; ++r) {
+      unpack_to(xs[r], xf[r].p, dt);
+      a1[r] = xf[r].p;
+      a2[r] = (const char *)xf[r].p + n1 * es;
+      b1[r] = sf[r].p;
+      b2[r] = (char *)sf[r].p + n1 * es;
     }
-    // with CUDA graphs on, FP64 arguments go through fixed buffers too, so that repeated
-    // products present the same addresses and replay one captured program
-    const bool stage128 = set->dt == C128 && M->graphs;
-    if (stage128 && (int)x128.size() < nr) {
-      x128.resize(nr);
-      s128.resize(nr);
-    }
+    M->apply_batch(dir, *set, nr, a1.data(), a2.data(), b1.data(), b2.data());
+    for (int r = 0; r < nr; ++r) pack_from(sf[r].p, dt, ss[r]);
+  }
+  // sigma of full-layout complex128 vectors (the boundary's layout), nr at once
+  void op_batch_full(int dir, int nr, const void *const *xs, void *const *ss) {
+    sigma_calls += nr;
+    const CstSet *set = &M->cst_for(M->prec);
+    const int dt = set->dt;
+    const size_t es = dt_size(dt);
+    // complex64 products and graph replay go through the fixed full-layout buffers
+    const bool stage = dt == C64 || M->graphs;
+    if (stage) stage_full(dt, nr);
+    auto &xf = xfs[dt], &sf = sfs[dt];
+    std::vector<const void *> a1(nr), a2(nr);
+    std::vector<void *> b1(nr), b2(nr);
     for (int r = 0; r < nr; ++r) {
       const void *x = xs[r];
       void *s = ss[r];
-      if (set->dt == C64) {
-        if (!x64[r].p) { x64[r].alloc((size_t)ntot() * 8); s64[r].alloc((size_t)ntot() * 8); }
-        M->E.permute(zc(1), make_tens((void *)x, C128, {ntot()}), "a", make_tens(x64[r].p, C64, {ntot()}), "a", false);
-        x = x64[r].p;
-        s = s64[r].p;
-      } else if (stage128) {
-        if (!x128[r].p) { x128[r].alloc((size_t)ntot() * 16); s128[r].alloc((size_t)ntot() * 16); }
-        CCLR_CUDA(cudaMemcpyAsync(x128[r].p, x, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st));
-        x = x128[r].p;
-        s = s128[r].p;
+      if (stage) {
+        M->E.permute(zc(1), make_tens((void *)x, C128, {nfull()}), "a", make_tens(xf[r].p, dt, {nfull()}), "a", false);
+        x = xf[r].p;
+        s = sf[r].p;
       }
       a1[r] = x;
       a2[r] = (const char *)x + n1 * es;
@@ -124,12 +157,9 @@ struct cclr_ctx {
       b2[r] = (char *)s + n1 * es;
     }
     M->apply_batch(dir, *set, nr, a1.data(), a2.data(), b1.data(), b2.data());
-    if (set->dt == C64)
+    if (stage)
       for (int r = 0; r < nr; ++r)
-        M->E.permute(zc(1), make_tens(s64[r].p, C64, {ntot()}), "a", make_tens(ss[r], C128, {ntot()}), "a", false);
-    else if (stage128)
-      for (int r = 0; r < nr; ++r)
-        CCLR_CUDA(cudaMemcpyAsync(ss[r], s128[r].p, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st));
+        M->E.permute(zc(1), make_tens(sf[r].p, dt, {nfull()}), "a", make_tens(ss[r], C128, {nfull()}), "a", false);
   }
 
   // Solve (Op - omega) x = b.  FP64 mode: preconditioned DIIS.  Mixed modes: iterative
@@ -317,6 +347,14 @@ struct cclr_ctx {
     bool done = false, cyc = false;
   };
   std::vector<BlockSys> blk;
+
+  // frees the solver's Krylov bases and the full-layout scratch at the end of a solve call
+  void release_scratch() {
+    kv.clear();
+    blk.clear();
+    fullA.b.release();
+    fullB.b.release();
+  }
 
   // Block solve: nr independent systems (Op - omega_r) x_r = b_r advanced in lockstep, so that
   // each iteration applies the operator to every unconverged system in one batched product
@@ -575,13 +613,14 @@ struct cclr_ctx {
   }
 
   // restart length of the block solver: the Krylov bases of all systems must fit in half of
-  // the free device memory
+  // the free device memory (and of what the context's budget leaves)
   int block_restart(int nr) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       (void)cudaGetLastError();
       return krylov;
     }
+    if (acct.budget) free_b = std::min(free_b, acct.budget > acct.used ? acct.budget - acct.used : (size_t)0);
     const double vec = (double)ntot() * 16;
     const int fit = (int)(0.5 * (double)free_b / (vec * std::max(1, nr))) - 4;
     return std::max(2, std::min(krylov, fit));
@@ -680,19 +719,21 @@ struct cclr_ctx {
     return x;
   }
 
+  // xi^comp at amplitudes (t1d, t2d) (full layouts), written packed into out
   void xi_vec(int comp, const void *t1d, const void *t2d, void *out) {
+    alloc_full(fullA);
     const int64_t nn = (int64_t)M->n * M->n;
-    M->xi((char *)M->mu.p + (size_t)comp * nn * 16, t1d, t2d, out, (char *)out + n1 * 16);
+    M->xi((char *)M->mu.p + (size_t)comp * nn * 16, t1d, t2d, fullA.p1(), fullA.p2(n1));
+    pack_from(fullA.b.p, C128, out);
   }
 
-  // eta0 = dE/dT = [ sum_jb <ij||ab> t_jb ; <ij||ab> ] (canonical Fock: f_ia = 0)
+  // eta0 = dE/dT = [ sum_jb <ij||ab> t_jb ; <ij||ab> ] (canonical Fock: f_ia = 0), packed
   void eta0(void *out) {
-    const Tens &oovv = M->oovv128();
+    const void *oovv = M->oovv_packed();
     Tens e1 = make_tens(out, C128, {o, v});
-    Tens e2 = make_tens((char *)out + n1 * 16, C128, {o, o, v, v});
     M->E.zero(e1);
-    M->E.contract(zc(1), oovv, "ijab", make_tens(M->t1.p, C128, {o, v}), "jb", e1, "ia");
-    M->E.permute(zc(1), oovv, "ijab", e2, "ijab", false);
+    packed_doubles_dot_singles(o, v, oovv, M->t1.p, out, zc(1), st);
+    CCLR_CUDA(cudaMemcpyAsync((char *)out + n1 * 16, oovv, (size_t)n2p * 16, cudaMemcpyDeviceToDevice, st));
     // f_ia of diag(eps) is zero; the one-body h keeps any ov part of the input Fock
   }
 
@@ -733,16 +774,40 @@ struct cclr_ctx {
     return std::sqrt(h[0].x + 0.25 * h[1].x);
   }
 
-  // shifted amplitudes T + k h X into (t1s, t2s)
-  void shifted(const void *x, double kh, AVec &ts) {
-    alloc_vec(ts);
-    CCLR_CUDA(cudaMemcpyAsync(ts.p1(), M->t1.p, (size_t)n1 * 16, cudaMemcpyDeviceToDevice, st));
-    CCLR_CUDA(cudaMemcpyAsync(ts.p2(n1), M->t2.p, (size_t)n2 * 16, cudaMemcpyDeviceToDevice, st));
-    axpy(zd(kh), x, ts.b.p);
+  // shifted amplitudes T + k h X (X packed) into the full-layout scratch fullB
+  AVec &shifted(const void *x, double kh) {
+    alloc_full(fullB);
+    CCLR_CUDA(cudaMemcpyAsync(fullB.p1(), M->t1.p, (size_t)n1 * 16, cudaMemcpyDeviceToDevice, st));
+    CCLR_CUDA(cudaMemcpyAsync(fullB.p2(n1), M->t2.p, (size_t)n2 * 16, cudaMemcpyDeviceToDevice, st));
+    vec_axpy(C128, n1, zc(kh), x, fullB.p1(), st);
+    unpack_doubles(C128, C128, o, v, (const char *)x + n1 * 16, fullB.p2(n1), zc(kh), true, st);
+    return fullB;
   }
 
-  // eta^A . X = sum_ia mu^A_ia X_ia + d/de lambda . xi^A(T + eX)   (4-point stencil)
-  zd eta_dot(int comp, const void *x) {
+  // eta^A = dE_A/dT + lambda dxi^A/dT = [mu^A_ia ; 0] + lambda A[mu^A], with A[mu^A] the
+  // Jacobian of the one-body operator mu^A alone (xi^A(T) = Omega[mu^A](T), Omega linear in the
+  // Hamiltonian): the transpose program on mu^A's own H-bar set, in FP64.  Packed, cached.
+  const void *eta_vec(int comp) {
+    if (!eta_ok[comp]) {
+      const int64_t nn = (int64_t)M->n * M->n;
+      const void *mub = (char *)M->mu.p + (size_t)comp * nn * 16;
+      if (!onebody[comp].valid) M->build_set_onebody(mub, M->t1.p, M->t2.p, onebody[comp]);
+      alloc_vec(eta_v[comp]);
+      op(-1, lam.b.p, eta_v[comp].b.p, &onebody[comp]);
+      Tens muA = make_tens((void *)mub, C128, {M->n, M->n});
+      M->E.permute(zc(1), muA.slice(0, 0, o).slice(1, o, M->n), "ia", make_tens(eta_v[comp].b.p, C128, {o, v}), "ia",
+                   true);
+      eta_ok[comp] = true;
+    }
+    return eta_v[comp].b.p;
+  }
+
+  // eta^A . X (bilinear over unique amplitudes)
+  zd eta_dot(int comp, const void *x) { return dot(eta_vec(comp), x, 0); }
+
+  // eta^A . X = sum_ia mu^A_ia X_ia + d/de lambda . xi^A(T + eX)   (4-point stencil; the
+  // definition, kept as a check of eta_vec)
+  zd eta_dot_stencil(int comp, const void *x) {
     const int64_t nn = (int64_t)M->n * M->n;
     Tens muA = make_tens((char *)M->mu.p + (size_t)comp * nn * 16, C128, {M->n, M->n});
     // sum_ia mu_ia X_ia
@@ -758,11 +823,11 @@ struct cclr_ctx {
     zd val(hv.x, hv.y);
     const double h = step(x);
     static const double cs[4] = {-1, 8, -8, 1}, ks[4] = {2, 1, -1, -2};
-    AVec ts, xv;
+    AVec xv;
     alloc_vec(xv);
     zd acc = 0.0;
     for (int s = 0; s < 4; ++s) {
-      shifted(x, ks[s] * h, ts);
+      AVec &ts = shifted(x, ks[s] * h);
       xi_vec(comp, ts.p1(), ts.p2(n1), xv.b.p);
       acc += cs[s] * dot(lam.b.p, xv.b.p, 0);
     }
@@ -773,11 +838,11 @@ struct cclr_ctx {
   void fx(const void *x, void *out) {
     const double h = step(x);
     static const double cs[4] = {-1, 8, -8, 1}, ks[4] = {2, 1, -1, -2};
-    AVec ts, sv;
+    AVec sv;
     alloc_vec(sv);
     CCLR_CUDA(cudaMemsetAsync(out, 0, (size_t)ntot() * 16, st));
     for (int s = 0; s < 4; ++s) {
-      shifted(x, ks[s] * h, ts);
+      AVec &ts = shifted(x, ks[s] * h);
       const int saved = M->prec;
       const int use = M->prec == CCLR_FP64 ? CCLR_FP64 : hi_prec;
       M->prec = use;
@@ -795,8 +860,7 @@ struct cclr_ctx {
       axpy(zd(cs[s] / (12.0 * h)), sv.b.p, out);
     }
     // d eta0 / dT along X: sum_jb <ij||ab> X_jb (singles only)
-    Tens o1 = make_tens(out, C128, {o, v});
-    M->E.contract(zc(1), M->oovv128(), "ijab", make_tens((void *)x, C128, {o, v}), "jb", o1, "ia");
+    packed_doubles_dot_singles(o, v, M->oovv_packed(), x, out, zc(1), st);
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
 };
@@ -811,6 +875,12 @@ template <typename F> int guarded(F &&f) {
   } catch (const std::exception &e) {
     return fail(CCLR_EDEVICE, e.what());
   }
+}
+
+// the same with the call's device allocations charged to (and limited by) the context's account
+template <typename F> int guarded_ctx(cclr_ctx *c, F &&f) {
+  AcctScope scope(&c->acct);
+  return guarded(std::forward<F>(f));
 }
 
 }  // namespace
@@ -843,16 +913,17 @@ cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps
   *ctx = nullptr;
   if (o < 1 || v < 1 || naux < 1) return (cclr_status)fail(CCLR_EINVAL, "o, v and naux must be >= 1");
   if (!eps || !L || !mu) return (cclr_status)fail(CCLR_EINVAL, "eps, L and mu are required");
-  if (prec < 0 || prec > 3) return (cclr_status)fail(CCLR_EINVAL, "unknown precision mode");
+  if (prec < 0 || prec > 4) return (cclr_status)fail(CCLR_EINVAL, "unknown precision mode");
   if ((lam1 == nullptr) != (lam2 == nullptr)) return (cclr_status)fail(CCLR_EINVAL, "lam1 and lam2 must both be given or both be NULL");
   auto c = new cclr_ctx();
-  int st = guarded([&] {
+  c->acct.budget = hbm_budget_bytes;
+  int st = guarded_ctx(c, [&] {
     c->o = o; c->v = v; c->naux = naux;
     c->n1 = (int64_t)o * v;
     c->n2 = (int64_t)o * o * v * v;
+    c->n2p = (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2);
     c->device_ptrs = device_ptrs;
     c->st = (cudaStream_t)cuda_stream;
-    c->budget = hbm_budget_bytes;
     int dev = 0;
     CCLR_CUDA(cudaGetDevice(&dev));
     c->M.reset(new Model(o, v, naux, c->st));
@@ -862,13 +933,13 @@ cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps
     c->M->build_diagonal();
     if (lam1) {
       c->alloc_vec(c->lam);
-      to_dev(c, lam1, c->lam.p1(), (size_t)c->n1 * 16);
-      to_dev(c, lam2, c->lam.p2(c->n1), (size_t)c->n2 * 16);
+      c->alloc_full(c->fullA);
+      to_dev(c, lam1, c->fullA.p1(), (size_t)c->n1 * 16);
+      to_dev(c, lam2, c->fullA.p2(c->n1), (size_t)c->n2 * 16);
+      c->pack_from(c->fullA.b.p, C128, c->lam.b.p);
       c->have_lambda = true;
     }
     CCLR_CUDA(cudaStreamSynchronize(c->st));
-    if (c->budget && device_bytes_in_use() > c->budget)
-      throw Error(CCLR_ENOMEM, "HBM budget exceeded: " + std::to_string(device_bytes_in_use()) + " bytes in use");
   });
   if (st != CCLR_OK) {
     delete c;
@@ -882,7 +953,7 @@ static cclr_status sigma_common(cclr_ctx *c, int dir, int nrhs, const double *x1
                                 double *s1, double *s2) {
   if (!c || nrhs < 0 || (nrhs > 0 && (!x1 || !x2 || !s1 || !s2)))
     return (cclr_status)fail(CCLR_EINVAL, "bad sigma arguments");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
     // all right-hand sides go through the device together (shared integral formation)
     const int chunk = std::max(1, std::min(nrhs, 32));
     for (int r0 = 0; r0 < nrhs; r0 += chunk) {
@@ -895,14 +966,14 @@ static cclr_status sigma_common(cclr_ctx *c, int dir, int nrhs, const double *x1
       std::vector<void *> ss(nr);
       for (int q = 0; q < nr; ++q) {
         const int r = r0 + q;
-        c->alloc_vec(c->stage_in[q]);
-        c->alloc_vec(c->stage_out[q]);
+        c->alloc_full(c->stage_in[q]);
+        c->alloc_full(c->stage_out[q]);
         to_dev(c, x1 + (size_t)r * c->n1 * 2, c->stage_in[q].p1(), (size_t)c->n1 * 16);
         to_dev(c, x2 + (size_t)r * c->n2 * 2, c->stage_in[q].p2(c->n1), (size_t)c->n2 * 16);
         xs[q] = c->stage_in[q].b.p;
         ss[q] = c->stage_out[q].b.p;
       }
-      c->op_batch(dir, nr, xs.data(), ss.data());
+      c->op_batch_full(dir, nr, xs.data(), ss.data());
       for (int q = 0; q < nr; ++q) {
         const int r = r0 + q;
         from_dev(c, c->stage_out[q].p1(), s1 + (size_t)r * c->n1 * 2, (size_t)c->n1 * 16);
@@ -923,12 +994,12 @@ cclr_status cc_lr_sigma_T(cclr_ctx *c, int nrhs, const double *y1, const double 
 
 cclr_status cc_lr_xi(cclr_ctx *c, int comp, double *xi1, double *xi2) {
   if (!c || comp < 0 || comp > 2 || !xi1 || !xi2) return (cclr_status)fail(CCLR_EINVAL, "bad xi arguments");
-  return (cclr_status)guarded([&] {
-    AVec out;
-    c->alloc_vec(out);
-    c->xi_vec(comp, c->M->t1.p, c->M->t2.p, out.b.p);
-    from_dev(c, out.p1(), xi1, (size_t)c->n1 * 16);
-    from_dev(c, out.p2(c->n1), xi2, (size_t)c->n2 * 16);
+  return (cclr_status)guarded_ctx(c, [&] {
+    c->alloc_full(c->fullA);
+    const int64_t nn = (int64_t)c->M->n * c->M->n;
+    c->M->xi((char *)c->M->mu.p + (size_t)comp * nn * 16, c->M->t1.p, c->M->t2.p, c->fullA.p1(), c->fullA.p2(c->n1));
+    from_dev(c, c->fullA.p1(), xi1, (size_t)c->n1 * 16);
+    from_dev(c, c->fullA.p2(c->n1), xi2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
   });
 }
@@ -937,7 +1008,7 @@ cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int d
                           double *x1, double *x2, cclr_stats *stats) {
   if (!c || comp < 0 || comp > 2 || !x1 || !x2 || !(tol > 0)) return (cclr_status)fail(CCLR_EINVAL, "bad solve_x arguments");
   double rel = 0;
-  int st = guarded([&] {
+  int st = guarded_ctx(c, [&] {
     auto t0 = std::chrono::steady_clock::now();
     AVec b, x;
     c->alloc_vec(b);
@@ -947,8 +1018,10 @@ cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int d
     int its = 0;
     int calls0 = c->sigma_calls;
     rel = c->solve(+1, omega, b.b.p, x.b.p, tol, diis_depth, c->maxit, &its);
-    from_dev(c, x.p1(), x1, (size_t)c->n1 * 16);
-    from_dev(c, x.p2(c->n1), x2, (size_t)c->n2 * 16);
+    c->alloc_full(c->fullA);
+    c->unpack_to(x.b.p, c->fullA.b.p, C128);
+    from_dev(c, c->fullA.p1(), x1, (size_t)c->n1 * 16);
+    from_dev(c, c->fullA.p2(c->n1), x2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
     if (stats) {
       std::memset(stats, 0, sizeof(*stats));
@@ -966,10 +1039,12 @@ cclr_status cc_lr_solve_x(cclr_ctx *c, double omega, int comp, double tol, int d
 
 cclr_status cc_lr_lambda(cclr_ctx *c, double tol, double *lam1, double *lam2) {
   if (!c || !lam1 || !lam2) return (cclr_status)fail(CCLR_EINVAL, "bad lambda arguments");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
     c->ensure_lambda(tol, 8, nullptr);
-    from_dev(c, c->lam.p1(), lam1, (size_t)c->n1 * 16);
-    from_dev(c, c->lam.p2(c->n1), lam2, (size_t)c->n2 * 16);
+    c->alloc_full(c->fullA);
+    c->unpack_to(c->lam.b.p, c->fullA.b.p, C128);
+    from_dev(c, c->fullA.p1(), lam1, (size_t)c->n1 * 16);
+    from_dev(c, c->fullA.p2(c->n1), lam2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
   });
 }
@@ -987,7 +1062,7 @@ static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, do
   cclr_stats loc;
   std::memset(&loc, 0, sizeof(loc));
   loc.converged = 1;
-  int st = guarded([&] {
+  int st = guarded_ctx(c, [&] {
     int calls0 = c->sigma_calls;
     c->ensure_lambda(tol, diis_depth, &loc);
     for (int w = 0; w < nomega; ++w) {
@@ -1080,10 +1155,137 @@ static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, do
     }
     loc.sigma_calls = c->sigma_calls - calls0;
     loc.refinements = c->refinements;
+    c->release_scratch();
   });
   if (stats) *stats = loc;
   if (st != CCLR_OK) return (cclr_status)st;
   return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve: tolerance not met");
+}
+
+// Right (X) solves of every component at the shifts in sh, in one block or one by one.
+static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const std::vector<const void *> &bs,
+                        const std::vector<void *> &xs, double tol, int diis_depth, cclr_stats &loc) {
+  if (c->method == 2) {
+    std::vector<int> its;
+    std::vector<double> rels;
+    c->solve_block(dir, sh, bs, xs, tol, c->maxit, its, rels);
+    for (size_t k = 0; k < its.size(); ++k) {
+      loc.iterations += its[k];
+      loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
+      if (!(rels[k] < tol)) loc.converged = 0;
+    }
+    return;
+  }
+  for (size_t k = 0; k < bs.size(); ++k) {
+    int its = 0;
+    const double rel = c->solve(dir, sh[k], bs[k], xs[k], tol, diis_depth, c->maxit, &its);
+    loc.iterations += its;
+    loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
+    if (!(rel < tol)) loc.converged = 0;
+  }
+}
+
+// alpha by the left-hand route (Sec. 2.2): X^B(w) from (A - w) X = -xi^B, Y^B(w) from
+// Y (A + w) = -(eta^B + F X^B(w)), and g(A,B;w) = Y^B(w) . xi^A + eta^A . X^B(w);
+// <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)], alpha = -<<A;B>>.
+static cclr_status solve_alpha_left(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
+                                    double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0))
+    return (cclr_status)fail(CCLR_EINVAL, "bad solve_left arguments");
+  for (int k = 0; k < ncomp; ++k)
+    if (comps[k] < 0 || comps[k] > 2) return (cclr_status)fail(CCLR_EINVAL, "component out of range");
+  cclr_stats loc;
+  std::memset(&loc, 0, sizeof(loc));
+  loc.converged = 1;
+  int st = guarded_ctx(c, [&] {
+    const int calls0 = c->sigma_calls;
+    c->ensure_lambda(tol, diis_depth, &loc);
+    std::vector<AVec> XI(ncomp), RB(ncomp);
+    for (int a = 0; a < ncomp; ++a) {
+      c->alloc_vec(XI[a]);
+      c->alloc_vec(RB[a]);
+      c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, XI[a].b.p);
+      c->copy(XI[a].b.p, RB[a].b.p);
+      c->scal(zd(-1), RB[a].b.p);
+    }
+    for (int w = 0; w < nomega; ++w) {
+      std::vector<zd> shifts{zd(omegas[w])};
+      if (omegas[w] != 0.0) shifts.push_back(zd(-omegas[w]));
+      const int ns = (int)shifts.size();
+      auto slot = [&](int k) { return (k == 1 && ns == 2) ? 1 : 0; };  // k = 0: +w, 1: -w
+      std::vector<AVec> X((size_t)ncomp * ns), Y((size_t)ncomp * ns);
+      auto t0 = std::chrono::steady_clock::now();
+      std::vector<zd> sh;
+      std::vector<const void *> bs;
+      std::vector<void *> xs;
+      for (int b = 0; b < ncomp; ++b)
+        for (int q = 0; q < ns; ++q) {
+          c->alloc_vec(X[(size_t)b * ns + q]);
+          sh.push_back(shifts[q]);
+          bs.push_back(RB[b].b.p);
+          xs.push_back(X[(size_t)b * ns + q].b.p);
+        }
+      solve_right(c, +1, sh, bs, xs, tol, diis_depth, loc);
+      auto t1 = std::chrono::steady_clock::now();
+      // left right-hand sides -(eta^B + F X^B(s)), then Y^B(s) with the shift -s
+      std::vector<AVec> LB((size_t)ncomp * ns);
+      std::vector<zd> lsh;
+      std::vector<const void *> lbs;
+      std::vector<void *> ys;
+      for (int b = 0; b < ncomp; ++b)
+        for (int q = 0; q < ns; ++q) {
+          AVec &r = LB[(size_t)b * ns + q];
+          c->alloc_vec(r);
+          c->fx(X[(size_t)b * ns + q].b.p, r.b.p);
+          c->axpy(zd(1), c->eta_vec(comps[b]), r.b.p);
+          c->scal(zd(-1), r.b.p);
+          c->alloc_vec(Y[(size_t)b * ns + q]);
+          lsh.push_back(-shifts[q]);
+          lbs.push_back(r.b.p);
+          ys.push_back(Y[(size_t)b * ns + q].b.p);
+        }
+      auto t2 = std::chrono::steady_clock::now();
+      solve_right(c, -1, lsh, lbs, ys, tol, diis_depth, loc);
+      auto t3 = std::chrono::steady_clock::now();
+      for (int a = 0; a < ncomp; ++a)
+        for (int b = 0; b < ncomp; ++b) {
+          auto g = [&](int k) {
+            const size_t id = (size_t)b * ns + slot(k);
+            return c->dot(Y[id].b.p, XI[a].b.p, 0) + c->eta_dot(comps[a], X[id].b.p);
+          };
+          const zd al = -0.5 * (g(0) + std::conj(g(1)));
+          const size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
+          alpha[k] = al.real();
+          alpha[k + 1] = al.imag();
+        }
+      auto t4 = std::chrono::steady_clock::now();
+      loc.time_solve_ms += std::chrono::duration<double, std::milli>((t1 - t0) + (t3 - t2)).count();
+      loc.time_alpha_ms += std::chrono::duration<double, std::milli>((t2 - t1) + (t4 - t3)).count();
+    }
+    loc.sigma_calls = c->sigma_calls - calls0;
+    loc.refinements = c->refinements;
+    c->release_scratch();
+  });
+  if (stats) *stats = loc;
+  if (st != CCLR_OK) return (cclr_status)st;
+  return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve_left: tolerance not met");
+}
+
+cclr_status cc_lr_solve_left(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
+                             double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  return solve_alpha_left(c, nomega, omegas, ncomp, comps, tol, diis_depth, alpha, stats);
+}
+
+cclr_status cc_lr_eta(cclr_ctx *c, int comp, double tol, double *eta1, double *eta2) {
+  if (!c || comp < 0 || comp > 2 || !eta1 || !eta2 || !(tol > 0)) return (cclr_status)fail(CCLR_EINVAL, "bad eta arguments");
+  return (cclr_status)guarded_ctx(c, [&] {
+    c->ensure_lambda(tol, 8, nullptr);
+    c->alloc_full(c->fullA);
+    c->unpack_to(c->eta_vec(comp), c->fullA.b.p, C128);
+    from_dev(c, c->fullA.p1(), eta1, (size_t)c->n1 * 16);
+    from_dev(c, c->fullA.p2(c->n1), eta2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
 }
 
 cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
@@ -1098,7 +1300,7 @@ cclr_status cc_lr_solve_damped(cclr_ctx *c, int nomega, const double *omegas, do
 
 cclr_status cc_lr_get_t(cclr_ctx *c, double *t1, double *t2) {
   if (!c || !t1 || !t2) return (cclr_status)fail(CCLR_EINVAL, "bad get_t arguments");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
     from_dev(c, c->M->t1.p, t1, (size_t)c->n1 * 16);
     from_dev(c, c->M->t2.p, t2, (size_t)c->n2 * 16);
     CCLR_CUDA(cudaStreamSynchronize(c->st));
@@ -1106,8 +1308,8 @@ cclr_status cc_lr_get_t(cclr_ctx *c, double *t1, double *t2) {
 }
 
 cclr_status cc_lr_set_precision(cclr_ctx *c, int prec) {
-  if (!c || prec < 0 || prec > 3) return (cclr_status)fail(CCLR_EINVAL, "bad precision");
-  return (cclr_status)guarded([&] {
+  if (!c || prec < 0 || prec > 4) return (cclr_status)fail(CCLR_EINVAL, "bad precision");
+  return (cclr_status)guarded_ctx(c, [&] {
     c->M->prec = prec;
     if (prec != CCLR_FP64) c->M->cst_for(prec);
   });
@@ -1117,7 +1319,7 @@ cclr_status cc_lr_set_graphs(cclr_ctx *c, int on) {
   if (!c || (on != 0 && on != 1)) return (cclr_status)fail(CCLR_EINVAL, "graphs must be 0 or 1");
   if (on && (c->st == nullptr || c->st == cudaStreamLegacy || c->st == cudaStreamPerThread))
     return (cclr_status)fail(CCLR_EUNSUPPORTED, "CUDA graphs need a context created with its own (non-default) stream");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
     CCLR_CUDA(cudaStreamSynchronize(c->st));
     c->M->graphs = on != 0;
     if (!on) c->M->clear_graphs();
@@ -1132,10 +1334,10 @@ cclr_status cc_lr_graph_stats(cclr_ctx *c, int *captures, int *launches) {
 }
 
 cclr_status cc_lr_ladder_tuning(cclr_ctx *c, int prec, int *group_size, int cap, int *cand, double *ms, int *n) {
-  if (!c || (prec != CCLR_C64_TF32 && prec != CCLR_C64_3XTF32) || !group_size || !n || cap < 0 ||
+  if (!c || (prec != CCLR_C64_TF32 && prec != CCLR_C64_3XTF32 && prec != CCLR_BF16X3) || !group_size || !n || cap < 0 ||
       (cap > 0 && (!cand || !ms)))
     return (cclr_status)fail(CCLR_EINVAL, "bad ladder_tuning arguments");
-  const LadderTC &l = c->M->ltc[prec == CCLR_C64_3XTF32 ? 1 : 0];
+  const LadderTC &l = c->M->ltc[prec == CCLR_C64_3XTF32 ? 1 : prec == CCLR_BF16X3 ? 2 : 0];
   *group_size = l.group_size();
   *n = (int)l.tune_log.size();
   for (int k = 0; k < cap && k < *n; ++k) {
@@ -1147,7 +1349,7 @@ cclr_status cc_lr_ladder_tuning(cclr_ctx *c, int prec, int *group_size, int cap,
 
 cclr_status cc_lr_set_ladder_storage(cclr_ctx *c, int store) {
   if (!c || (store != 0 && store != 1)) return (cclr_status)fail(CCLR_EINVAL, "ladder storage must be 0 or 1");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
     CCLR_CUDA(cudaStreamSynchronize(c->st));
     for (auto &l : c->M->ltc) l.set_store(store != 0);
   });
@@ -1156,9 +1358,21 @@ cclr_status cc_lr_set_ladder_storage(cclr_ctx *c, int store) {
 cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
   if (!c || (prec != CCLR_FP64 && prec != CCLR_C64_3XTF32))
     return (cclr_status)fail(CCLR_EINVAL, "refinement precision must be CCLR_FP64 or CCLR_C64_3XTF32");
-  return (cclr_status)guarded([&] {
+  return (cclr_status)guarded_ctx(c, [&] {
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
     c->hi_prec = prec;
-    if (prec != CCLR_FP64) c->M->cst_for(prec);
+    if (prec != CCLR_FP64) {
+      c->M->cst_for(prec);
+      if (c->M->prec != CCLR_FP64) {
+        c->M->oovv_packed();  // formed from the complex128 set while it exists
+        // no FP64 product remains in this configuration: its set and buffers are freed (an FP64
+        // product requested later rebuilds them)
+        c->M->release_fp64();
+        c->xfs[C128].clear();
+        c->sfs[C128].clear();
+        c->M->release_set(c->shift);
+      }
+    }
   });
 }
 
@@ -1168,6 +1382,14 @@ cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace, int max_iter
   c->method = method;
   if (subspace >= 2) c->krylov = subspace;
   if (max_iterations > 0) c->maxit = max_iterations;
+  return CCLR_OK;
+}
+
+cclr_status cc_lr_memory(cclr_ctx *c, size_t *in_use, size_t *peak, size_t *budget) {
+  if (!c || !in_use || !peak || !budget) return (cclr_status)fail(CCLR_EINVAL, "bad memory arguments");
+  *in_use = c->acct.used;
+  *peak = c->acct.peak;
+  *budget = c->acct.budget;
   return CCLR_OK;
 }
 
@@ -1216,13 +1438,13 @@ int cc_lr_selftest_timeout(int timeout_us, int *flag) {
 }
 
 int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
-  if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || reps < 1 || !ms) return fail(CCLR_EINVAL, "bad bench_gemm arguments");
+  if (M < 1 || N < 1 || K < 1 || mode < 1 || mode > 3 || reps < 1 || !ms) return fail(CCLR_EINVAL, "bad bench_gemm arguments");
   return guarded([&] {
     cudaStream_t st;
     CCLR_CUDA(cudaStreamCreate(&st));
-    const int seg = mode == 2 ? 3 : 1;
-    const int64_t ld = 2 * tc_kpad(K) * seg;
-    DevBuf A((size_t)M * ld * 4), B((size_t)2 * N * ld * 4), C((size_t)M * N * 8);
+    const int seg = mode == 1 ? 1 : 3, kind = mode == 3 ? TC_BF16 : TC_TF32;
+    const int64_t ld = 2 * tc_kpad(K) * seg, es = tc_esize(kind);
+    DevBuf A((size_t)M * ld * es), B((size_t)2 * N * ld * es), C((size_t)M * N * 8);
     // deterministic small values (exact content is irrelevant for timing)
     CCLR_CUDA(cudaMemsetAsync(A.p, 0, A.bytes, st));
     CCLR_CUDA(cudaMemsetAsync(B.p, 0, B.bytes, st));
@@ -1230,12 +1452,10 @@ int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
     cudaEvent_t e0, e1;
     CCLR_CUDA(cudaEventCreate(&e0));
     CCLR_CUDA(cudaEventCreate(&e1));
-    tc_gemm_seg(A.as<float>(), ld, B.as<float>(), ld, M, 2 * N, 2 * tc_kpad(K), seg, C.as<float>(), 2 * N,
-                zc(1), false, st);
+    tc_gemm_seg(A.p, ld, B.p, ld, M, 2 * N, 2 * tc_kpad(K), seg, kind, C.as<float>(), 2 * N, zc(1), false, st);
     CCLR_CUDA(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; ++r)
-      tc_gemm_seg(A.as<float>(), ld, B.as<float>(), ld, M, 2 * N, 2 * tc_kpad(K), seg, C.as<float>(), 2 * N,
-                  zc(1), false, st);
+      tc_gemm_seg(A.p, ld, B.p, ld, M, 2 * N, 2 * tc_kpad(K), seg, kind, C.as<float>(), 2 * N, zc(1), false, st);
     CCLR_CUDA(cudaEventRecord(e1, st));
     CCLR_CUDA(cudaEventSynchronize(e1));
     float t = 0;
@@ -1250,7 +1470,7 @@ int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
 }
 
 int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *err) {
-  if (M < 1 || N < 1 || K < 1 || (mode != 1 && mode != 2) || !err) return fail(CCLR_EINVAL, "bad selftest arguments");
+  if (M < 1 || N < 1 || K < 1 || mode < 1 || mode > 3 || !err) return fail(CCLR_EINVAL, "bad selftest arguments");
   return guarded([&] {
     std::mt19937_64 g(seed);
     std::normal_distribution<double> nd(0.0, 1.0);

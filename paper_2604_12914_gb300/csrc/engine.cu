@@ -1,7 +1,9 @@
 // Contraction engine: classifies the modes of C += A*B into batch / M / N / K groups,
 // views each operand as a strided batched matrix when its modes merge, and permutes it
 // into a contiguous scratch layout otherwise.
+#include <algorithm>
 #include <atomic>
+#include <numeric>
 #include <cstdio>
 #include <cstdlib>
 
@@ -18,9 +20,18 @@ static std::atomic<unsigned long long> g_epoch{1};
 unsigned long long state_epoch() { return g_epoch.load(); }
 void bump_state_epoch() { ++g_epoch; }
 
+MemAcct *&current_acct() {
+  static thread_local MemAcct *a = nullptr;
+  return a;
+}
+
 void DevBuf::alloc(size_t b) {
   release();
   if (b == 0) return;
+  MemAcct *a = current_acct();
+  if (a && a->budget && a->used + b > a->budget)
+    throw Error(2, "HBM budget of " + std::to_string(a->budget) + " bytes exceeded: " + std::to_string(a->used) +
+                       " bytes held, " + std::to_string(b) + " more requested");
   cudaError_t e = cudaMalloc(&p, b);
   if (e != cudaSuccess) {
     p = nullptr;
@@ -28,6 +39,11 @@ void DevBuf::alloc(size_t b) {
     throw Error(2, "cudaMalloc of " + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
   }
   bytes = b;
+  acct = a;
+  if (a) {
+    a->used += b;
+    a->peak = std::max(a->peak, a->used);
+  }
   g_bytes_in_use += b;
 }
 
@@ -36,9 +52,11 @@ void DevBuf::release() {
     ++g_epoch;
     cudaFree(p);
     g_bytes_in_use -= bytes;
+    if (acct) acct->used -= bytes;
   }
   p = nullptr;
   bytes = 0;
+  acct = nullptr;
 }
 
 void *Engine::ws(int slot, size_t bytes) {
@@ -320,29 +338,59 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
     T = contiguous_like(ws(2, nb * M * N * es), C64, C, mc, order);
     c0 = M * N; cm = view1(N); cn = view1(1);
   }
-  const int seg = tc_mode == 2 ? 3 : 1;
-  const int64_t ld = 2 * tc_kpad(K) * seg;
+  const int seg = tc_mode == 1 ? 1 : 3;
+  const int kind = tc_mode == 3 ? TC_BF16 : TC_TF32;
+  const int64_t ld = 2 * tc_kpad(K) * seg, tes = tc_esize(kind);
   if (trace_on())
     std::fprintf(stderr, "cclr contract tc %s,%s->%s nb=%lld M=%lld N=%lld K=%lld A[%s|%s]%s B[%s|%s]%s C[%s|%s]%s\n",
                  ma.c_str(), mb.c_str(), mc.c_str(), (long long)nb, (long long)M, (long long)N, (long long)K,
                  vstr(am).c_str(), vstr(ak).c_str(), Ap == A.p ? "" : "(permuted)", vstr(bk).c_str(),
                  vstr(bn).c_str(), Bp == B.p ? "" : "(permuted)", vstr(cm).c_str(), vstr(cn).c_str(),
                  direct ? "" : "(temporary)");
-  float *Ao = (float *)ws(3, (size_t)M * ld * 4);
-  float *Bo = (float *)ws(4, (size_t)2 * N * ld * 4);
+  // prepared operands are bounded (2 GiB each): B in chunks of columns, A in chunks of rows,
+  // each chunk starting on a whole block of a two-level view
+  const int64_t per_col = 2 * ld * tes, per_row = ld * tes, capb = 2ll << 30;
+  auto unit_of = [](const View2 &x, const View2 &y) {
+    int64_t u = 1;
+    if (x.din != TC_ONE_LEVEL) u = std::lcm(u, x.din);
+    if (y.din != TC_ONE_LEVEL) u = std::lcm(u, y.din);
+    return u;
+  };
+  int64_t Nc = N, Mc = M;
+  {
+    const int64_t u = unit_of(bn, cn);
+    if (N * per_col > capb && u < N) Nc = std::max(u, capb / per_col / u * u);
+  }
+  {
+    const int64_t u = unit_of(am, cm);
+    if (M * per_row > capb && u < M) Mc = std::max(u, capb / per_row / u * u);
+  }
+  void *Ao = nullptr;
+  void *Bo = ws(4, (size_t)(Nc * per_col));
   // TF32 reads A in place when its K index is contiguous and its rows are one strided level
   const bool a_direct = seg == 1 && ak.sin == 1 && ak.din == TC_ONE_LEVEL && am.din == TC_ONE_LEVEL &&
                         (M == 1 || tc_a_inplace_ok(Ap, am.sin, K)) && (nb == 1 || (a0 * es) % 16 == 0);
   for (int64_t b = 0; b < nb; ++b) {
     const void *Ab = (const char *)Ap + b * a0 * es;
     const bool ad = a_direct && tc_a_inplace_ok(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K);
-    if (!ad) tc_prep_a2(Ab, am, ak, M, K, seg, Ao, ld, st);
-    tc_prep_b2((const char *)Bp + b * b0 * es, bk, bn, K, N, seg, Bo, ld, st);
-    float *Cp = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
-    if (ad)
-      tc_gemm_a_inplace(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K, Bo, ld, M, 2 * N, Cp, cm, cn, alpha, direct, st);
-    else
-      tc_gemm_seg_v(Ao, ld, Bo, ld, M, 2 * N, 2 * tc_kpad(K), seg, Cp, cm, cn, alpha, direct, st);
+    if (!ad && !Ao) Ao = ws(3, (size_t)(Mc * per_row));
+    float *Cb = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
+    for (int64_t n0 = 0; n0 < N; n0 += Nc) {
+      const int64_t nn = std::min(Nc, N - n0);
+      tc_prep_b2((const char *)Bp + (b * b0 + v2off(bn, n0)) * es, bk, bn, K, nn, seg, kind, Bo, ld, st);
+      float *Cn = Cb + 2 * v2off(cn, n0);
+      if (ad) {
+        tc_gemm_a_inplace(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K, (const float *)Bo, ld, M, 2 * nn, Cn, cm, cn,
+                          alpha, direct, st);
+        continue;
+      }
+      for (int64_t m0 = 0; m0 < M; m0 += Mc) {
+        const int64_t mm = std::min(Mc, M - m0);
+        if (n0 == 0 || Mc < M) tc_prep_a2((const char *)Ab + v2off(am, m0) * es, am, ak, mm, K, seg, kind, Ao, ld, st);
+        tc_gemm_seg_v(Ao, ld, Bo, ld, mm, 2 * nn, 2 * tc_kpad(K), seg, kind, Cn + 2 * v2off(cm, m0), cm, cn, alpha,
+                      direct, st);
+      }
+    }
     ++tc_calls;
   }
   if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);

@@ -8,17 +8,40 @@
 
 namespace cclr {
 
-// Owning device allocation.
+// Device memory charged to one owner (a context): bytes held now, the most ever held, and
+// an optional limit (0 = none) that every allocation charged to it is checked against.
+struct MemAcct {
+  size_t used = 0, peak = 0, budget = 0;
+};
+// The account that allocations made on this thread are charged to (nullptr: none).
+MemAcct *&current_acct();
+// Charges the allocations of a scope (one library call) to an account.
+struct AcctScope {
+  MemAcct *prev;
+  explicit AcctScope(MemAcct *a) : prev(current_acct()) { current_acct() = a; }
+  ~AcctScope() { current_acct() = prev; }
+  AcctScope(const AcctScope &) = delete;
+  AcctScope &operator=(const AcctScope &) = delete;
+};
+
+// Owning device allocation.  An allocation over the current account's budget throws status 2
+// (CCLR_ENOMEM) before cudaMalloc is called; the bytes are returned to the same account when
+// the buffer is released, whichever thread releases it.
 struct DevBuf {
   void *p = nullptr;
   size_t bytes = 0;
+  MemAcct *acct = nullptr;
   DevBuf() = default;
   explicit DevBuf(size_t b) { alloc(b); }
   DevBuf(const DevBuf &) = delete;
   DevBuf &operator=(const DevBuf &) = delete;
-  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf &&o) noexcept : p(o.p), bytes(o.bytes), acct(o.acct) { o.p = nullptr; o.bytes = 0; o.acct = nullptr; }
   DevBuf &operator=(DevBuf &&o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) {
+      release();
+      p = o.p; bytes = o.bytes; acct = o.acct;
+      o.p = nullptr; o.bytes = 0; o.acct = nullptr;
+    }
     return *this;
   }
   ~DevBuf() { release(); }
@@ -37,7 +60,7 @@ class Engine {
  public:
   cudaStream_t st = nullptr;
   // complex64 contractions above a size threshold run on the tcgen05 tensor cores:
-  // 0 = never (CUDA-core FP32), 1 = TF32, 2 = 3xTF32 split.
+  // 0 = never (CUDA-core FP32), 1 = TF32, 2 = 3xTF32 split, 3 = bf16x3 split.
   int tc_mode = 0;
   bool tc_force = false;  // route every complex64 contraction to the tensor cores (self-test)
   int64_t tc_calls = 0;

@@ -593,33 +593,162 @@ void vec_precond(int dt, int64_t n, const double *D, double omega, double omega_
     CCLR_CUDA(cudaGetLastError());
 }
 
-// D1[i,a] = Fvv_aa - Foo_ii ; D2[i,j,a,b] = Fvv_aa + Fvv_bb - Foo_ii - Foo_jj (real parts).
-__global__ void diag_kernel(int o, int v, const double2 *Foo, const double2 *Fvv, double *D1,
-                            double *D2) {
-  int64_t n1 = (int64_t)o * v, n2 = n1 * o * v;
+// pair (p < q) of n indices -> its row-major position among all pairs, and back
+__host__ __device__ __forceinline__ int64_t pair_id(int64_t p, int64_t q, int64_t n) {
+  return p * n - p * (p + 1) / 2 + (q - p - 1);
+}
+__device__ __forceinline__ void pair_of(int64_t k, int n, int &p, int &q) {
+  // p = largest row with start(p) = p n - p (p + 1) / 2 <= k: the root of the quadratic in
+  // single precision (this GPU's FP64 rate is low), then corrected by whole steps
+  const float nn = 2.0f * (float)n - 1.0f;
+  int r = (int)((nn - sqrtf(fmaxf(0.0f, nn * nn - 8.0f * (float)k))) * 0.5f);
+  r = max(0, min(r, n - 2));
+  while (r > 0 && pair_id(r, r + 1, n) > k) --r;
+  while (r < n - 2 && pair_id(r + 1, r + 2, n) <= k) ++r;
+  p = r;
+  q = (int)(k - pair_id(r, r + 1, n)) + r + 1;
+}
+
+// D1[i,a] = Fvv_aa - Foo_ii ; D2p[(i<j),(a<b)] = Fvv_aa + Fvv_bb - Foo_ii - Foo_jj (real parts).
+__global__ void diag_kernel(int o, int v, const double2 *Foo, const double2 *Fvv, double *D1, double *D2p) {
+  const int64_t n1 = (int64_t)o * v;
+  const int64_t Pv = (int64_t)v * (v - 1) / 2, n2 = (int64_t)o * (o - 1) / 2 * Pv;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1 + n2;
        e += (int64_t)gridDim.x * blockDim.x) {
     if (e < n1) {
       int i = (int)(e / v), a = (int)(e % v);
       D1[e] = Fvv[(int64_t)a * v + a].x - Foo[(int64_t)i * o + i].x;
     } else {
-      int64_t r = e - n1;
-      int b = (int)(r % v); r /= v;
-      int a = (int)(r % v); r /= v;
-      int j = (int)(r % o); r /= o;
-      int i = (int)r;
-      D2[e - n1] = Fvv[(int64_t)a * v + a].x + Fvv[(int64_t)b * v + b].x -
-                   Foo[(int64_t)i * o + i].x - Foo[(int64_t)j * o + j].x;
+      const int64_t r = e - n1;
+      int i, j, a, b;
+      pair_of(r / Pv, o, i, j);
+      pair_of(r % Pv, v, a, b);
+      D2p[r] = Fvv[(int64_t)a * v + a].x + Fvv[(int64_t)b * v + b].x - Foo[(int64_t)i * o + i].x -
+               Foo[(int64_t)j * o + j].x;
     }
   }
 }
 
-void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2,
+void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2p,
                 cudaStream_t st) {
-  int64_t n = (int64_t)o * v * (1 + (int64_t)o * v);
-  diag_kernel<<<grid_for(n), 256, 0, st>>>(o, v, (const double2 *)Foo, (const double2 *)Fvv, D1, D2);
+  const int64_t n = (int64_t)o * v + (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2);
+  diag_kernel<<<grid_for(n), 256, 0, st>>>(o, v, (const double2 *)Foo, (const double2 *)Fvv, D1, D2p);
   count_launch();
-    CCLR_CUDA(cudaGetLastError());
+  CCLR_CUDA(cudaGetLastError());
+}
+
+// F (+)= alpha * unpack(P), one thread per full entry (writes coalesced; the packed row of one
+// (i,j) pair is read with a stride that depends on the (a,b) order, from L2).
+template <typename TP, typename TF>
+__global__ void unpack_doubles_kernel(int o, int v, const typename cpx<TP>::t *P, typename cpx<TF>::t *F,
+                                      double ar, double ai, int acc) {
+  const int64_t vv = (int64_t)v * v, n = (int64_t)o * o * vv, Pv = (int64_t)v * (v - 1) / 2;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ab = e % vv, ij = e / vv;
+    const int a = (int)(ab / v), b = (int)(ab % v), i = (int)(ij / o), j = (int)(ij % o);
+    typename cpx<TP>::t z;
+    z.x = 0;
+    z.y = 0;
+    double sg = 0.0;
+    if (i != j && a != b) {
+      const int p = min(i, j), q = max(i, j), r = min(a, b), s = max(a, b);
+      sg = ((i < j) == (a < b)) ? 1.0 : -1.0;
+      z = P[pair_id(p, q, o) * Pv + pair_id(r, s, v)];
+    }
+    const double zr = sg * (double)z.x, zi = sg * (double)z.y;
+    double wr = ar * zr - ai * zi, wi = ar * zi + ai * zr;
+    if (acc) {
+      wr += (double)F[e].x;
+      wi += (double)F[e].y;
+    }
+    typename cpx<TF>::t w;
+    w.x = (TF)wr;
+    w.y = (TF)wi;
+    F[e] = w;
+  }
+}
+
+// P = F[i<j, a<b], one thread per packed entry (writes coalesced, reads along b).
+template <typename TF, typename TP>
+__global__ void pack_doubles_kernel(int o, int v, const typename cpx<TF>::t *F, typename cpx<TP>::t *P) {
+  const int64_t Pv = (int64_t)v * (v - 1) / 2, n = (int64_t)o * (o - 1) / 2 * Pv;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, a, b;
+    pair_of(k / Pv, o, i, j);
+    pair_of(k % Pv, v, a, b);
+    const typename cpx<TF>::t f = F[(((int64_t)i * o + j) * v + a) * v + b];
+    typename cpx<TP>::t w;
+    w.x = (TP)f.x;
+    w.y = (TP)f.y;
+    P[k] = w;
+  }
+}
+
+void unpack_doubles(int dt_p, int dt_f, int o, int v, const void *P, void *F, zc alpha, bool acc, cudaStream_t st) {
+  const int64_t n = (int64_t)o * o * v * v;
+  if (n == 0) return;
+  const unsigned g = grid_for(n);
+  const int a = acc ? 1 : 0;
+  if (dt_p == C128 && dt_f == C128)
+    unpack_doubles_kernel<double, double><<<g, 256, 0, st>>>(o, v, (const double2 *)P, (double2 *)F, alpha.re, alpha.im, a);
+  else if (dt_p == C128 && dt_f == C64)
+    unpack_doubles_kernel<double, float><<<g, 256, 0, st>>>(o, v, (const double2 *)P, (float2 *)F, alpha.re, alpha.im, a);
+  else if (dt_p == C64 && dt_f == C128)
+    unpack_doubles_kernel<float, double><<<g, 256, 0, st>>>(o, v, (const float2 *)P, (double2 *)F, alpha.re, alpha.im, a);
+  else
+    unpack_doubles_kernel<float, float><<<g, 256, 0, st>>>(o, v, (const float2 *)P, (float2 *)F, alpha.re, alpha.im, a);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+// one block per i, threads over a; each thread sums over (j, b) with the packed entry's sign
+__global__ void packed_dot_singles_kernel(int o, int v, const double2 *W, const double2 *x1, double2 *out1,
+                                          double ar, double ai) {
+  const int i = blockIdx.x;
+  const int64_t Pv = (int64_t)v * (v - 1) / 2;
+  for (int a = threadIdx.x; a < v; a += blockDim.x) {
+    double sr = 0.0, si = 0.0;
+    for (int j = 0; j < o; ++j) {
+      if (j == i) continue;
+      const int64_t row = pair_id(min(i, j), max(i, j), o) * Pv;
+      const double sij = i < j ? 1.0 : -1.0;
+      for (int b = 0; b < v; ++b) {
+        if (b == a) continue;
+        const double sg = (a < b) ? sij : -sij;
+        const double2 w = W[row + pair_id(min(a, b), max(a, b), v)];
+        const double2 x = x1[(int64_t)j * v + b];
+        sr += sg * (w.x * x.x - w.y * x.y);
+        si += sg * (w.x * x.y + w.y * x.x);
+      }
+    }
+    double2 *p = out1 + (int64_t)i * v + a;
+    p->x += ar * sr - ai * si;
+    p->y += ar * si + ai * sr;
+  }
+}
+
+void packed_doubles_dot_singles(int o, int v, const void *Wp, const void *x1, void *out1, zc alpha, cudaStream_t st) {
+  if (o < 2 || v < 2) return;
+  packed_dot_singles_kernel<<<o, 128, 0, st>>>(o, v, (const double2 *)Wp, (const double2 *)x1, (double2 *)out1,
+                                               alpha.re, alpha.im);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+void pack_doubles(int dt_f, int dt_p, int o, int v, const void *F, void *P, cudaStream_t st) {
+  const int64_t n = (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2);
+  if (n == 0) return;
+  const unsigned g = grid_for(n);
+  if (dt_f == C128 && dt_p == C128)
+    pack_doubles_kernel<double, double><<<g, 256, 0, st>>>(o, v, (const double2 *)F, (double2 *)P);
+  else if (dt_f == C64 && dt_p == C128)
+    pack_doubles_kernel<float, double><<<g, 256, 0, st>>>(o, v, (const float2 *)F, (double2 *)P);
+  else if (dt_f == C128 && dt_p == C64)
+    pack_doubles_kernel<double, float><<<g, 256, 0, st>>>(o, v, (const double2 *)F, (float2 *)P);
+  else
+    pack_doubles_kernel<float, float><<<g, 256, 0, st>>>(o, v, (const float2 *)F, (float2 *)P);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
 }
 
 // t2[i,j,a,b] = w[i,j,a,b] / (e_i + e_j - e_a - e_b)

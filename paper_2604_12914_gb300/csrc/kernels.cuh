@@ -49,8 +49,22 @@ void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 
 // out = r / (D - (omega + i omega_im))
 void vec_precond(int dt, int64_t n, const double *D, double omega, double omega_im, const void *r, void *out,
                  cudaStream_t st);
-void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2,
+// D1[i,a] = Fvv_aa - Foo_ii; D2p[(i<j),(a<b)] = Fvv_aa + Fvv_bb - Foo_ii - Foo_jj over the
+// packed doubles (real parts of complex128 Foo, Fvv).
+void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2p,
                 cudaStream_t st);
+
+// Packed (unique-amplitude) doubles: P[(i<j) * P_v + (a<b)], pairs (p<q) of n indices numbered
+// row by row, pair(p, q) = p n - p (p + 1) / 2 + q - p - 1.  The full tensor F[o][o][v][v] is
+// antisymmetric in (i,j) and (a,b).
+// F (+)= alpha * unpack(P): every entry of F is written (zero where i = j or a = b).
+// dt_p / dt_f: C128 or C64 (conversion on the fly).
+void unpack_doubles(int dt_p, int dt_f, int o, int v, const void *P, void *F, zc alpha, bool acc, cudaStream_t st);
+// P = F[i<j, a<b] (dt_f -> dt_p).
+void pack_doubles(int dt_f, int dt_p, int o, int v, const void *F, void *P, cudaStream_t st);
+// out1[i,a] += alpha * sum_{j,b} W[i,j,a,b] x1[j,b] for W antisymmetric in (i,j) and (a,b), given
+// packed (complex128; x1, out1 complex128 [o][v]).
+void packed_doubles_dot_singles(int o, int v, const void *Wp, const void *x1, void *out1, zc alpha, cudaStream_t st);
 void apply_denominator(int o, int v, const double *eps, void *t2, cudaStream_t st);
 void set_diag(int n, const double *d, void *out, cudaStream_t st);
 

@@ -7,40 +7,10 @@
 namespace cclr {
 namespace {
 
-__device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t u = __float_as_uint(x);
-  u = (u + 0x1000u) & 0xFFFFE000u;
-  return __uint_as_float(u);
-}
-
-// store complex value v as element k of an A-format row (K-major, [hi|hi|lo] when seg = 3)
-__device__ __forceinline__ void put_a(float *row, int64_t k, int64_t Kp, int seg, float2 v) {
-  if (seg == 1) {
-    row[2 * k] = v.x;
-    row[2 * k + 1] = v.y;
-  } else {
-    const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
-    row[2 * k] = hr; row[2 * k + 1] = hi;
-    row[2 * Kp + 2 * k] = hr; row[2 * Kp + 2 * k + 1] = hi;
-    row[4 * Kp + 2 * k] = v.x - hr; row[4 * Kp + 2 * k + 1] = v.y - hi;
-  }
-}
-
-// store complex value v as element k of the embedded B rows r0 (re, -im), r1 (im, re)
-__device__ __forceinline__ void put_b(float *r0, float *r1, int64_t k, int64_t Kp, int seg, float2 v) {
-  if (seg == 1) {
-    r0[2 * k] = v.x; r0[2 * k + 1] = -v.y; r1[2 * k] = v.y; r1[2 * k + 1] = v.x;
-  } else {
-    const float hr = tf32_hi(v.x), hi = tf32_hi(v.y), lr = v.x - hr, li = v.y - hi;
-    r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
-    r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
-    r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
-  }
-}
-
 // Packed X as the contraction B operand: B(k = (e<f), n = (i<j)) = X[i,j,e,f].
+template <int KIND>
 __global__ void pack_x_b(const float2 *X, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
-                         int64_t Pv, int64_t Kp, int seg, float *dst, int64_t ldd) {
+                         int64_t Pv, int64_t Kp, int seg, typename TcElem<KIND>::T *dst, int64_t ldd) {
   const int64_t total = Po * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -50,14 +20,15 @@ __global__ void pack_x_b(const float2 *X, int o, int v, const int2 *op, const in
       const int2 ij = op[n], ef = vp[k];
       val = X[(((int64_t)ij.x * o + ij.y) * v + ef.x) * v + ef.y];
     }
-    put_b(dst + (2 * n) * ldd, dst + (2 * n + 1) * ldd, k, Kp, seg, val);
+    tc_put_b<KIND>(dst + (2 * n) * ldd, dst + (2 * n + 1) * ldd, k, Kp, seg, val);
   }
 }
 
 // Y (transpose direction) as the A operand over a group of (a<b) pairs:
 // A(m = (i<j), k = r) = Y[i,j,a,b] - Y[j,i,a,b] - Y[i,j,b,a] + Y[j,i,b,a], (a,b) = pair(p0 + r).
+template <int KIND>
 __global__ void pack_y_a(const float2 *Y, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
-                         int64_t p0, int64_t np, int64_t Kp, int seg, float *dst, int64_t ldd) {
+                         int64_t p0, int64_t np, int64_t Kp, int seg, typename TcElem<KIND>::T *dst, int64_t ldd) {
   const int64_t total = Po * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -70,7 +41,7 @@ __global__ void pack_y_a(const float2 *Y, int o, int v, const int2 *op, const in
       const float2 y3 = Y[((i * o + j) * v + b) * v + a], y4 = Y[((j * o + i) * v + b) * v + a];
       val = make_float2(y1.x - y2.x - y3.x + y4.x, y1.y - y2.y - y3.y + y4.y);
     }
-    put_a(dst + m * ldd, k, Kp, seg, val);
+    tc_put_a<KIND>(dst + m * ldd, k, Kp, seg, val);
   }
 }
 
@@ -78,8 +49,10 @@ __global__ void pack_y_a(const float2 *Y, int o, int v, const int2 *op, const in
 //   <ab||ef>~ = W[(b-a0)v+f][(a-a0)v+e] - W[(b-a0)v+e][(a-a0)v+f],  a in group, b > a, e < f.
 // mode 0: A operand rows r = (a,b) pair - p0, K = (e<f)      (forward contraction)
 // mode 1: B operand rows 2(e<f), 2(e<f)+1, K = r              (transpose contraction)
+template <int KIND>
 __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *vp, int64_t p0,
-                       int64_t np, int64_t Pv, int64_t Kp, int seg, int mode, float *dst, int64_t ldd) {
+                       int64_t np, int64_t Pv, int64_t Kp, int seg, int mode, typename TcElem<KIND>::T *dst,
+                       int64_t ldd) {
   const int64_t total = mode == 0 ? np * Kp : Pv * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -94,8 +67,8 @@ __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *
       const float2 w2 = W[(rb + ef.x) * ldw + ca + ef.y];
       val = make_float2(w1.x - w2.x, w1.y - w2.y);
     }
-    if (mode == 0) put_a(dst + r * ldd, q, Kp, seg, val);
-    else put_b(dst + (2 * q) * ldd, dst + (2 * q + 1) * ldd, r, Kp, seg, val);
+    if (mode == 0) tc_put_a<KIND>(dst + r * ldd, q, Kp, seg, val);
+    else tc_put_b<KIND>(dst + (2 * q) * ldd, dst + (2 * q + 1) * ldd, r, Kp, seg, val);
   }
 }
 
@@ -149,19 +122,19 @@ int64_t pair_start(int v, int a) { return (int64_t)a * v - (int64_t)a * (a + 1) 
 
 }  // namespace
 
-void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg) {
+void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind) {
   cudaStream_t st = E.st;
   wall_ready_ = false;  // a stored block belongs to the previous L~_vv
-  o_ = o; v_ = v; naux_ = naux; seg_ = seg;
+  o_ = o; v_ = v; naux_ = naux; seg_ = seg; kind_ = kind;
   Po_ = (int64_t)o * (o - 1) / 2;
   Pv_ = (int64_t)v * (v - 1) / 2;
-  const int64_t ld = 2 * tc_kpad(naux) * seg;
+  const int64_t ld = 2 * tc_kpad(naux) * seg, es = tc_esize(kind);
   const int64_t vv = (int64_t)v * v;
-  LA.alloc((size_t)vv * ld * 4);
-  LB.alloc((size_t)2 * vv * ld * 4);
-  // A(m = (b,f), k = P) = L[P,b,f]; B(k = P, n = (a,e)) = L[P,a,e]
-  tc_prep_a(Lvv.p, 1, vv, vv, naux, seg, LA.as<float>(), ld, st);
-  tc_prep_b(Lvv.p, vv, 1, naux, vv, seg, LB.as<float>(), ld, st);
+  Lvv_ = Lvv.p;
+  LA.alloc((size_t)vv * ld * es);
+  LB.release();  // the embedded B rows are prepared per group (only the group's a values)
+  // A(m = (b,f), k = P) = L[P,b,f]
+  tc_prep_a(Lvv.p, 1, vv, vv, naux, seg, kind, LA.p, ld, st);
   auto op = pairs(o), vp = pairs(v);
   opairs.alloc(std::max<size_t>(1, op.size()) * sizeof(int2));
   vpairs.alloc(std::max<size_t>(1, vp.size()) * sizeof(int2));
@@ -188,10 +161,11 @@ void LadderTC::tune(Engine &E) {
   float best_ms = 1e30f;
   const bool store_saved = store_;
   store_ = false;  // the tuner times the on-the-fly formation
-  for (int cand : {16, 32, 64}) {
+  for (int cand : {8, 16, 32, 64}) {
     const int ga = std::min(cand, v_);
+    // the group block W [(v - a0) v][ga v] complex64: at most 8 GB (the smallest group always)
     const double wbytes = (double)v_ * v_ * ga * v_ * 8;
-    if (cand > 16 && wbytes > 16e9) continue;
+    if (cand > 8 && wbytes > 8e9) continue;
     if (!tune_log.empty() && tune_log.back().first == ga) continue;
     ga_ = ga;
     apply(E, +1, zc(1.0), 1, in, out);  // the first run allocates the group buffers
@@ -214,10 +188,10 @@ void LadderTC::tune(Engine &E) {
 
 void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *in, void *const *out) {
   cudaStream_t st = E.st;
-  const int o = o_, v = v_, seg = seg_;
+  const int o = o_, v = v_, seg = seg_, kind = kind_;
   const int64_t Po = Po_, Pv = Pv_;
   if (Po == 0 || Pv == 0 || nrhs < 1) return;
-  const int64_t vv = (int64_t)v * v;
+  const int64_t vv = (int64_t)v * v, es = tc_esize(kind);
   const int64_t ldL = 2 * tc_kpad(naux_) * seg;
   const int64_t KpPv = tc_kpad(Pv), ldPv = 2 * KpPv * seg;
   const int ga = std::min(ga_, v);
@@ -225,18 +199,25 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   // buffers sized for the first (largest) group
   const int64_t maxpairs = pair_start(v, ga);
   if (W.bytes < (size_t)vv * ga * v * 8) W.alloc((size_t)vv * ga * v * 8);
+  if (LB.bytes < (size_t)2 * ga * v * ldL * es) LB.alloc((size_t)2 * ga * v * ldL * es);
   const int64_t kpg = tc_kpad(maxpairs);
-  const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldPv * 4 : (size_t)2 * Pv * (2 * kpg * seg) * 4;
+  const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldPv * es : (size_t)2 * Pv * (2 * kpg * seg) * es;
   if (Wp.bytes < wp_bytes) Wp.alloc(wp_bytes);
-  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * NR * ldPv * 4 : (size_t)Po * NR * (2 * kpg * seg) * 4;
+  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * NR * ldPv * es : (size_t)Po * NR * (2 * kpg * seg) * es;
   if (Xp.bytes < xp_bytes) Xp.alloc(xp_bytes);
   if (sig.bytes < (size_t)Po * Pv * NR * 8) sig.alloc((size_t)Po * Pv * NR * 8);
   const int2 *op = opairs.as<int2>(), *vp = vpairs.as<int2>();
+  char *LAb = (char *)LA.p, *LBb = (char *)LB.p, *Wpb = (char *)Wp.p, *Xpb = (char *)Xp.p;
   nform_ = 0;
   if (dir > 0) {
     for (int64_t r = 0; r < NR; ++r) {
-      pack_x_b<<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
-                                                  Xp.as<float>() + 2 * Po * r * ldPv, ldPv);
+      void *dst = Xpb + 2 * Po * r * ldPv * es;
+      if (kind == TC_BF16)
+        pack_x_b<TC_BF16><<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
+                                                              (__nv_bfloat16 *)dst, ldPv);
+      else
+        pack_x_b<TC_TF32><<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
+                                                              (float *)dst, ldPv);
       count_launch();
     }
   } else {
@@ -244,9 +225,20 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   }
   const bool use_wall = store_ && dir > 0;
   if (use_wall && !wall_ready_) {
-    const size_t wall_bytes = (size_t)Pv * ldPv * 4;
+    const size_t wall_bytes = (size_t)Pv * ldPv * es;
     if (Wall.bytes != wall_bytes) Wall.alloc(wall_bytes);
   }
+  // pack_w launch into dst (rows of ldd elements of the mode's operand type)
+  auto packw = [&](int a0, int64_t p0, int64_t np, int64_t cols, int64_t Kp, int mode, void *dst, int64_t ldd) {
+    const int64_t total = mode == 0 ? np * Kp : Pv * Kp;
+    if (kind == TC_BF16)
+      pack_w<TC_BF16><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, Kp, seg, mode,
+                                                     (__nv_bfloat16 *)dst, ldd);
+    else
+      pack_w<TC_TF32><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, Kp, seg, mode,
+                                                     (float *)dst, ldd);
+    count_launch();
+  };
   for (int a0 = 0; a0 < v - 1 && !(use_wall && wall_ready_); a0 += ga) {
     const int a1 = std::min(v, a0 + ga);
     const int64_t p0 = pair_start(v, a0), np = pair_start(v, a1) - p0;
@@ -258,43 +250,44 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
       for (auto &e : fev)
         if (!e) CCLR_CUDA(cudaEventCreate(&e));
     }
+    // B(k = P, n = (a,e)) = L[P,a,e] for the group's a values, embedded
+    tc_prep_b((const char *)Lvv_ + (size_t)a0 * v * 8, vv, 1, naux_, cols, seg, kind, LBb, ldL, st);
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_], st));
-    tc_gemm_seg(LA.as<float>() + (int64_t)a0 * v * ldL, ldL, LB.as<float>() + 2 * (int64_t)a0 * v * ldL, ldL,
-                rows, 2 * cols, ldL / seg, seg, W.as<float>(), 2 * cols, zc(1.0), false, st);
+    tc_gemm_seg(LAb + (int64_t)a0 * v * ldL * es, ldL, LBb, ldL, rows, 2 * cols, ldL / seg, seg, kind, W.as<float>(),
+                2 * cols, zc(1.0), false, st);
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_ + 1], st));
     ++nform_;
     if (use_wall) {  // pack the group's rows into the stored block; contract once afterwards
-      pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
-                                                Wall.as<float>() + p0 * ldPv, ldPv);
-      count_launch();
+      packw(a0, p0, np, cols, KpPv, 0, (char *)Wall.p + p0 * ldPv * es, ldPv);
     } else if (dir > 0) {
-      pack_w<<<grid1d(np * KpPv), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, KpPv, seg, 0,
-                                                Wp.as<float>(), ldPv);
-      count_launch();
+      packw(a0, p0, np, cols, KpPv, 0, Wpb, ldPv);
       // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f]  for the group's pairs, all RHS
-      tc_gemm_seg(Wp.as<float>(), ldPv, Xp.as<float>(), ldPv, np, 2 * Po * NR, ldPv / seg, seg,
+      tc_gemm_seg(Wpb, ldPv, Xpb, ldPv, np, 2 * Po * NR, ldPv / seg, seg, kind,
                   sig.as<float>() + 2 * p0 * Po * NR, 2 * Po * NR, zc(1.0), false, st);
     } else {
       const int64_t kg = tc_kpad(np), ldg = 2 * kg * seg;
-      pack_w<<<grid1d(Pv * kg), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, kg, seg, 1,
-                                              Wp.as<float>(), ldg);
-      count_launch();
+      packw(a0, p0, np, cols, kg, 1, Wpb, ldg);
       for (int64_t r = 0; r < NR; ++r) {
-        pack_y_a<<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, p0, np, kg, seg,
-                                                   Xp.as<float>() + Po * r * ldg, ldg);
+        void *dst = Xpb + Po * r * ldg * es;
+        if (kind == TC_BF16)
+          pack_y_a<TC_BF16><<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, p0, np, kg, seg,
+                                                              (__nv_bfloat16 *)dst, ldg);
+        else
+          pack_y_a<TC_TF32><<<grid1d(Po * kg), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, p0, np, kg, seg,
+                                                              (float *)dst, ldg);
         count_launch();
       }
       // Z[(r, ij)][(ef)] += sum_{(ab) in group} Y'_r[(ij)][(ab)] <ab||ef>~
-      tc_gemm_seg(Xp.as<float>(), ldg, Wp.as<float>(), ldg, Po * NR, 2 * Pv, ldg / seg, seg, sig.as<float>(),
-                  2 * Pv, zc(1.0), true, st);
+      tc_gemm_seg(Xpb, ldg, Wpb, ldg, Po * NR, 2 * Pv, ldg / seg, seg, kind, sig.as<float>(), 2 * Pv, zc(1.0), true,
+                  st);
     }
     CCLR_CUDA(cudaGetLastError());
   }
   if (use_wall) {
     wall_ready_ = true;
     // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f] for every pair at once
-    tc_gemm_seg(Wall.as<float>(), ldPv, Xp.as<float>(), ldPv, Pv, 2 * Po * NR, ldPv / seg, seg, sig.as<float>(),
-                2 * Po * NR, zc(1.0), false, st);
+    tc_gemm_seg(Wall.p, ldPv, Xpb, ldPv, Pv, 2 * Po * NR, ldPv / seg, seg, kind, sig.as<float>(), 2 * Po * NR, zc(1.0),
+                false, st);
     CCLR_CUDA(cudaGetLastError());
   }
   for (int64_t r = 0; r < NR; ++r) {

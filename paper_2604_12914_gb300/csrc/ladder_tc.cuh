@@ -1,4 +1,4 @@
-// Particle-particle ladder on tcgen05 tensor cores (complex64 data, TF32 or 3xTF32):
+// Particle-particle ladder on tcgen05 tensor cores (complex64 data; TF32, 3xTF32 or bf16x3):
 //   out[i,j,a,b] += alpha * sum_{e<f} <ab||ef>~ X[i,j,e,f],   <ab|ef>~ = sum_P L~[P,a,e] L~[P,b,f]
 // over packed pairs i<j, a<b, e<f (the four antisymmetric images of each output are written).
 // <ab|ef>~ is formed on the fly from L~_vv for one group of a at a time and never stored
@@ -21,9 +21,10 @@ class LadderTC {
     for (auto e : fev)
       if (e) cudaEventDestroy(e);
   }
-  // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (TF32) or 3 (3xTF32).
-  void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg);
-  bool ready(int seg) const { return seg_ == seg && LA.p != nullptr; }
+  // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (one pass) or 3 (split); kind = TC_TF32
+  // or TC_BF16 (operand type of the tensor-core GEMMs).
+  void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind);
+  bool ready(int seg, int kind) const { return seg_ == seg && kind_ == kind && LA.p != nullptr; }
   // dir +1: out[r] += alpha * ladder(in[r]);  dir -1: out[r] += alpha * ladder^T(in[r]),
   // r = 0..nrhs-1, all complex64 [o][o][v][v].  Each <ab||ef>~ group block is formed once
   // and contracted with every right-hand side.
@@ -31,13 +32,14 @@ class LadderTC {
   // device time (ms) of the formation GEMMs of the last apply(); call once its work has completed
   float formation_ms();
   // Autotuner: times one product for each candidate group size (a values per formed block:
-  // 16, 32, 64, those whose block fits in 16 GB) on zero input and keeps the fastest.  Runs
+  // 8, 16, 32, 64, those whose block fits in 8 GB) on zero input and keeps the fastest.  Runs
   // once per object, on its first preparation; group_size() and tune_log report the result.
   void tune(Engine &E);
   int group_size() const { return ga_; }
   // Ablation: keep the whole packed <ab||ef>~ (P_v x P_v, TF32 rows) once formed, so that later
   // sigma products (dir +1) skip the formation and run one contraction GEMM.  The transpose
-  // product still forms the blocks on the fly.  Costs P_v^2 x 8 bytes (x 3 for 3xTF32).
+  // product still forms the blocks on the fly.  Costs P_v^2 x 8 bytes (x 3 for 3xTF32, x 1.5 for
+  // bf16x3).
   void set_store(bool on) {
     store_ = on;
     if (!on) { Wall.release(); wall_ready_ = false; }
@@ -47,9 +49,10 @@ class LadderTC {
   std::vector<std::pair<int, float>> tune_log;
 
  private:
-  int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0;
+  int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0, kind_ = 0;
   int64_t Po_ = 0, Pv_ = 0;
-  DevBuf LA, LB;            // formation operands: rows (b,f) and embedded rows (a,e), K = naux
+  DevBuf LA, LB;            // formation operands: rows (b,f) (all), embedded rows (a,e) of one group; K = naux
+  const void *Lvv_ = nullptr;  // the complex64 L~_vv the operands are prepared from
   DevBuf opairs, vpairs;    // pair tables (p, q), p < q, row-major pair order
   DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result
   int ga_ = 32;             // a values per group (set by tune())

@@ -238,15 +238,55 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
   E.tc_mode = tc_saved;
-  for (int k = 0; k < 2; ++k)  // a ladder prepared from this buffer is stale
+  for (int k = 0; k < 3; ++k)  // a ladder prepared from this buffer is stale
     if (ltc_src[k] == out.t[K_LVV].p) ltc_src[k] = nullptr;
   bump_state_epoch();  // and so is any captured program that read the set
   out.valid = true;
 }
 
+// H-bar of a one-body operator B (Hamiltonian without two-body part) with the T1 dressing
+// B~ = (1 - t) B (1 + t): Fov = B~_ov, Foo = B~_oo, Fvv = B~_vv, Wovoo = -Fov_me t_ij^be; every
+// element with a two-body integral (Woooo, Wovvo, Wooov, <mn||ef>, L~) vanishes.
+void Model::build_set_onebody(const void *Bd, const void *t1d, const void *t2d, CstSet &out) {
+  out.dt = C128;
+  const int tc_saved = E.tc_mode;
+  E.tc_mode = 0;
+  Tens Bm = make_tens((void *)Bd, C128, {n, n});
+  Tens t1t = make_tens((void *)t1d, C128, {o, v});
+  Tens t2t = make_tens((void *)t2d, C128, {o, o, v, v});
+  auto alloc = [&](int id, std::initializer_list<int64_t> dims) {
+    int64_t ne = 1;
+    for (auto d : dims) ne *= d;
+    if (out.buf[id].bytes != (size_t)ne * 16) out.buf[id].alloc((size_t)ne * 16);
+    out.t[id] = make_tens(out.buf[id].p, C128, dims);
+    E.zero(out.t[id]);
+    return out.t[id];
+  };
+  Tens boo = Bm.slice(0, 0, o).slice(1, 0, o), bov = Bm.slice(0, 0, o).slice(1, o, n),
+       bvv = Bm.slice(0, o, n).slice(1, o, n);
+  Tens Foo = alloc(K_FOO, {o, o}), Fov = alloc(K_FOV, {o, v}), Fvv = alloc(K_FVV, {v, v});
+  E.permute(zc(1), boo, "ij", Foo, "ij", false);
+  E.contract(zc(1), bov, "ib", t1t, "jb", Foo, "ij");
+  E.permute(zc(1), bov, "ia", Fov, "ia", false);
+  E.permute(zc(1), bvv, "ab", Fvv, "ab", false);
+  E.contract(zc(-1), t1t, "ma", bov, "mb", Fvv, "ab");
+  Tens T2 = alloc(K_T2, {o, o, v, v});
+  E.permute(zc(1), t2t, "ijab", T2, "ijab", false);
+  Tens Wovoo = alloc(K_WOVOO, {o, v, o, o});
+  E.contract(zc(-1), Fov, "me", T2, "ijbe", Wovoo, "mbij");
+  for (int k = 0; k < K_NCST; ++k) out.zero[k] = true;
+  for (int k : {K_FOO, K_FOV, K_FVV, K_T2, K_WOVOO}) out.zero[k] = false;
+  for (int k = 0; k < K_NCST; ++k)
+    if (out.zero[k]) out.buf[k].release();
+  E.tc_mode = tc_saved;
+  CCLR_CUDA(cudaStreamSynchronize(st));
+  bump_state_epoch();
+  out.valid = true;
+}
+
 void Model::build_diagonal() {
   D1.alloc(sizeof(double) * o * v);
-  D2.alloc(sizeof(double) * (size_t)o * o * v * v);
+  D2.alloc(sizeof(double) * std::max<size_t>(1, (size_t)o * (o - 1) / 2 * ((size_t)v * (v - 1) / 2)));
   const CstSet &C = c128.valid ? c128 : c64;
   DevBuf f((size_t)(o * o + v * v) * 16);
   Tens foo = make_tens(f.p, C128, {o, o}), fvv = make_tens((char *)f.p + (size_t)o * o * 16, C128, {v, v});
@@ -260,6 +300,7 @@ void Model::build_diagonal() {
 void Model::round_set(const CstSet &src, CstSet &dst) {
   CCLR_REQUIRE(src.valid && src.dt == C128, "round_set: source must be a valid complex128 set");
   dst.dt = C64;
+  dst.zero = src.zero;
   for (int k = 0; k < K_NCST; ++k) {
     const Tens &s = src.t[k];
     const size_t bytes = (size_t)s.numel() * 8;
@@ -273,11 +314,25 @@ void Model::round_set(const CstSet &src, CstSet &dst) {
   }
   // a tensor-core ladder prepared from this set's L~_vv (same buffer) is now stale, and so is
   // any captured program that read it
-  for (int k = 0; k < 2; ++k)
+  for (int k = 0; k < 3; ++k)
     if (ltc_src[k] == dst.t[K_LVV].p) ltc_src[k] = nullptr;
   bump_state_epoch();
   CCLR_CUDA(cudaStreamSynchronize(st));
   dst.valid = true;
+}
+
+void Model::release_set(CstSet &s) {
+  for (int k = 0; k < 3; ++k)
+    if (s.t[K_LVV].p && ltc_src[k] == s.t[K_LVV].p) ltc_src[k] = nullptr;
+  for (auto &b : s.buf) b.release();
+  s.valid = false;
+}
+
+void Model::release_fp64() {
+  release_set(c128);
+  tmp128.clear();
+  x2bar[C128].clear();
+  lcc.release();
 }
 
 // The working intermediates are built in FP64; the complex64 modes read a rounded copy.
@@ -288,32 +343,35 @@ const CstSet &Model::cst_for(int p) {
   return c64;
 }
 
-// <ij||ab> in complex128 (the T1-independent oovv block), for dE/dT and the F X stencil.
-const Tens &Model::oovv128() {
-  if (!oovv_b.p) {
-    oovv_b.alloc((size_t)o * o * v * v * 16);
-    oovv_t = make_tens(oovv_b.p, C128, {o, o, v, v});
+// <ij||ab> in complex128, packed (the T1-independent oovv block), for dE/dT and the F X stencil:
+// from the complex128 set when it exists, else formed from the undressed L_ov (the ov block is
+// unchanged by the T1 dressing) in a temporary full tensor.
+const void *Model::oovv_packed() {
+  if (!oovvp.p) {
+    oovvp.alloc((size_t)std::max<int64_t>(1, (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2)) * 16);
     if (c128.valid) {
-      E.permute(zc(1), c128.t[K_OOVV], "mnef", oovv_t, "mnef", false);
+      pack_doubles(C128, C128, o, v, c128.t[K_OOVV].p, oovvp.p, st);
     } else {
+      DevBuf full((size_t)o * o * v * v * 16);
+      Tens F = make_tens(full.p, C128, {o, o, v, v});
       Tens Lov = T(Lov0, {naux, o, v});
-      E.zero(oovv_t);
-      E.contract(zc(1), Lov, "Pme", Lov, "Pnf", oovv_t, "mnef");
-      E.contract(zc(-1), Lov, "Pmf", Lov, "Pne", oovv_t, "mnef");
+      E.zero(F);
+      E.contract(zc(1), Lov, "Pme", Lov, "Pnf", F, "mnef");
+      E.contract(zc(-1), Lov, "Pmf", Lov, "Pne", F, "mnef");
+      pack_doubles(C128, C128, o, v, full.p, oovvp.p, st);
+      CCLR_CUDA(cudaStreamSynchronize(st));
     }
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
-  return oovv_t;
+  return oovvp.p;
 }
 
-std::vector<DevBuf> &Model::temps(int dt, int r) {
-  auto &all = dt == C128 ? tmp128 : tmp64;
-  if ((int)all.size() <= r) all.resize(r + 1);
-  auto &tv = all[r];
+std::vector<DevBuf> &Model::temps(int dt) {
+  auto &tv = dt == C128 ? tmp128 : tmp64;
   if (tv.empty()) {
     tv.resize(prog.vars.size());
     for (size_t k = 0; k < prog.vars.size(); ++k) {
-      if (k == 0 || k == 2) continue;  // x1 / s1 always come from the caller
+      if (k < 4) continue;  // x1, x2, s1, s2 (and their bars) live in per-RHS buffers
       int64_t ne = 1;
       for (auto d : prog.vars[k].dims) ne *= d;
       tv[k].alloc((size_t)ne * dt_size(dt));
@@ -336,17 +394,18 @@ Tens Model::var_tens(int id, int dt, void *p) const {
   return t;
 }
 
-// pp-ladder on CUDA cores: out[i,j,a,b] += alpha sum_ef <ab|ef>~ in[i,j,e,f] (dir +1), or the
-// transpose in'[i,j,e,f] += alpha sum_ab <ab|ef>~ in[i,j,a,b] (dir -1), <ab|ef>~ formed in
-// chunks of a from L~_vv and never stored whole.
+// pp-ladder: out[i,j,a,b] += alpha sum_ef <ab|ef>~ in[i,j,e,f] (dir +1), or the transpose
+// in'[i,j,e,f] += alpha sum_ab <ab|ef>~ in[i,j,a,b] (dir -1), over packed pairs with <ab|ef>~
+// formed per group of a from L~_vv and never stored whole: tcgen05 tensor cores in the TF32 /
+// 3xTF32 modes, CUDA cores otherwise.
 void Model::ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &in,
                    const std::vector<Tens> &out) {
   const int dt = C.dt;
   const int nr = (int)in.size();
   if (dt == C64 && E.tc_mode) {
-    const int seg = E.tc_mode == 2 ? 3 : 1, k = E.tc_mode == 2 ? 1 : 0;
-    if (!ltc[k].ready(seg) || ltc_src[k] != C.t[K_LVV].p) {
-      ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg);
+    const int k = E.tc_mode - 1, seg = E.tc_mode == 1 ? 1 : 3, kind = E.tc_mode == 3 ? TC_BF16 : TC_TF32;
+    if (!ltc[k].ready(seg, kind) || ltc_src[k] != C.t[K_LVV].p) {
+      ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg, kind);
       ltc_src[k] = C.t[K_LVV].p;
     }
     std::vector<const void *> ip(nr);
@@ -355,21 +414,11 @@ void Model::ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &
     ltc[k].apply(E, dir, alpha, nr, ip.data(), outp.data());
     return;
   }
-  // CUDA cores: <ab|ef>~ formed in chunks of a and contracted with every right-hand side
-  const Tens &Lvv = C.t[K_LVV];
-  const int64_t per_a = (int64_t)v * v * v * dt_size(dt);
-  int64_t ac = std::max<int64_t>(1, std::min<int64_t>(v, (int64_t)(1ll << 30) / per_a));
-  if (ladW.bytes < (size_t)(ac * per_a)) ladW.alloc((size_t)(ac * per_a));
-  for (int64_t a0 = 0; a0 < v; a0 += ac) {
-    int64_t a1 = std::min<int64_t>(v, a0 + ac);
-    Tens W = make_tens(ladW.p, dt, {a1 - a0, v, v, v});
-    E.zero(W);
-    E.contract(zc(1), Lvv.slice(1, a0, a1), "Pae", Lvv, "Pbf", W, "aebf");
-    for (int r = 0; r < nr; ++r) {
-      if (dir > 0) E.contract(alpha, W, "aebf", in[r], "ijef", out[r].slice(2, a0, a1), "ijab");
-      else E.contract(alpha, W, "aebf", in[r].slice(2, a0, a1), "ijab", out[r], "ijef");
-    }
-  }
+  // CUDA cores (FP64 DFMA or FP32 FFMA): the same packed algorithm
+  std::vector<const void *> ip(nr);
+  std::vector<void *> outp(nr);
+  for (int r = 0; r < nr; ++r) { ip[r] = in[r].p; outp[r] = out[r].p; }
+  lcc.apply(E, dt, C.t[K_LVV], o, v, naux, dir, alpha, nr, ip.data(), outp.data());
 }
 
 void Model::apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2) {
@@ -380,14 +429,17 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
                        void *const *s1, void *const *s2, bool timed, float &lad_ms, float &form_ms) {
   const int dt = C.dt;
   const int nv = (int)prog.vars.size();
+  // One set of program temporaries serves every right-hand side in turn; only the ladder, which
+  // forms each <ab||ef>~ block once for all of them, sees all right-hand sides at once.  Its
+  // output (input, in the transpose) is a per-RHS buffer, so it can run first (last).
+  auto &tv = temps(dt);
   std::vector<std::vector<void *>> ptr(nr, std::vector<void *>(nv, nullptr));
-  for (int r = 0; r < nr; ++r) {
-    auto &tv = temps(dt, r);
+  for (int r = 0; r < nr; ++r)
     for (int k = 4; k < nv; ++k) ptr[r][k] = tv[k].p;
-  }
   auto V = [&](int r, int id) { return var_tens(id, dt, ptr[r][id]); };
   auto Cst = [&](int id) { return C.t[id]; };
   auto run_ladder = [&](int d, zc a, int in_id, int out_id) {
+    if (C.zero[K_LVV]) return;
     std::vector<Tens> in(nr), out(nr);
     for (int r = 0; r < nr; ++r) { in[r] = V(r, in_id); out[r] = V(r, out_id); }
     if (!timed) {
@@ -401,17 +453,21 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
     float ms = 0.f;
     CCLR_CUDA(cudaEventElapsedTime(&ms, tm.ev[1], tm.ev[2]));
     lad_ms += ms;
-    if (dt == C64 && E.tc_mode) form_ms += ltc[E.tc_mode == 2 ? 1 : 0].formation_ms();
+    if (dt == C64 && E.tc_mode) form_ms += ltc[E.tc_mode - 1].formation_ms();
   };
+  const Op *lad = nullptr;
+  for (const Op &op : prog.ops)
+    if (op.kind == OP_LADDER) lad = &op;
   if (dir > 0) {
     for (int r = 0; r < nr; ++r) {
       ptr[r][0] = (void *)x1[r]; ptr[r][1] = (void *)x2[r]; ptr[r][2] = s1[r]; ptr[r][3] = s2[r];
       E.zero(V(r, 2));
       E.zero(V(r, 3));
     }
-    for (const Op &op : prog.ops) {
-      if (op.kind == OP_LADDER) { run_ladder(+1, op.alpha, op.in, op.out); continue; }
-      for (int r = 0; r < nr; ++r) {
+    if (lad) run_ladder(+1, lad->alpha, lad->in, lad->out);
+    for (int r = 0; r < nr; ++r)
+      for (const Op &op : prog.ops) {
+        if (op.kind == OP_LADDER || (op.kind == OP_CONTRACT && C.zero[op.cst])) continue;
         switch (op.kind) {
           case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.in), op.mi, V(r, op.out), op.mo); break;
           case OP_PERM: E.permute(op.alpha, V(r, op.in), op.mi, V(r, op.out), op.mo, true); break;
@@ -423,25 +479,27 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
           default: break;
         }
       }
-    }
   } else {
-    // bars: s1 <- y1 (x1 argument), s2 <- y2 / 4 (unique-amplitude weight), outputs to
-    // x1-bar (s1 argument) and a temporary x2-bar projected onto antisymmetric tensors.
+    // bars: s1-bar = y1 (the x1 argument), s2-bar = y2 / 4 (unique-amplitude weight), held in
+    // the s2 output until the end; x1-bar accumulates in the s1 output and x2-bar in a per-RHS
+    // buffer, which is projected onto antisymmetric tensors into s2 at the end
+    auto &xb = x2bar[dt];
+    if ((int)xb.size() < nr) xb.resize(nr);
     for (int r = 0; r < nr; ++r) {
-      auto &tv = temps(dt, r);
+      if (!xb[r].p) xb[r].alloc((size_t)o * o * v * v * dt_size(dt));
       ptr[r][2] = (void *)x1[r];
-      ptr[r][3] = tv[3].p;
+      ptr[r][3] = s2[r];
       ptr[r][0] = s1[r];
-      ptr[r][1] = tv[1].p;
+      ptr[r][1] = xb[r].p;
       E.permute(zc(0.25), var_tens(3, dt, (void *)x2[r]), "ijab", V(r, 3), "ijab", false);
       E.zero(V(r, 0));
       E.zero(V(r, 1));
-      for (int k = 4; k < nv; ++k) E.zero(V(r, k));
     }
-    for (auto it = prog.ops.rbegin(); it != prog.ops.rend(); ++it) {
-      const Op &op = *it;
-      if (op.kind == OP_LADDER) { run_ladder(-1, op.alpha, op.out, op.in); continue; }
-      for (int r = 0; r < nr; ++r) {
+    for (int r = 0; r < nr; ++r) {
+      for (int k = 4; k < nv; ++k) E.zero(V(r, k));
+      for (auto it = prog.ops.rbegin(); it != prog.ops.rend(); ++it) {
+        const Op &op = *it;
+        if (op.kind == OP_LADDER || (op.kind == OP_CONTRACT && C.zero[op.cst])) continue;
         switch (op.kind) {
           case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.out), op.mo, V(r, op.in), op.mi); break;
           case OP_PERM: E.permute(op.alpha, V(r, op.out), op.mo, V(r, op.in), op.mi, true); break;
@@ -454,6 +512,9 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
         }
       }
     }
+    // the transposed ladder reads only s2-bar, which is final once the projection (the first
+    // transposed operation) has run, and adds into x2-bar
+    if (lad) run_ladder(-1, lad->alpha, lad->out, lad->in);
     for (int r = 0; r < nr; ++r) {
       Tens out2 = var_tens(3, dt, s2[r]);
       Tens z2 = V(r, 1);
@@ -475,8 +536,9 @@ void Model::clear_graphs() {
 void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
                         void *const *s1, void *const *s2) {
   const int dt = C.dt;
-  // tensor cores for complex64: TF32 (prec 1) or 3xTF32 (prec 2); FP32 CUDA cores for prec 3
-  E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : 0) : 0;
+  // tensor cores for complex64: TF32 (prec 1), 3xTF32 (prec 2) or bf16x3 (prec 4); FP32 CUDA cores
+  // for prec 3
+  E.tc_mode = dt == C64 ? (prec == 1 ? 1 : prec == 2 ? 2 : prec == 4 ? 3 : 0) : 0;
   if (!tm.made) {
     for (auto &e : tm.ev) CCLR_CUDA(cudaEventCreate(&e));
     tm.made = true;
@@ -602,16 +664,14 @@ void Model::xi(const void *mub, const void *t1d, const void *t2d, void *xi1, voi
   Tens X2 = make_tens(xi2, C128, {o, o, v, v});
   E.permute(zc(1), Mvo, "ai", X1, "ia", false);
   E.contract(zc(1), mov, "me", t2t, "imae", X1, "ia");
-  DevBuf rb((size_t)o * o * v * v * 16);
-  Tens R = make_tens(rb.p, C128, {o, o, v, v});
-  E.zero(R);
-  E.contract(zc(1), Mvv, "be", t2t, "ijae", R, "ijab");
-  E.permute(zc(1), R, "ijab", X2, "ijab", false);
-  E.permute(zc(-1), R, "ijab", X2, "ijba", true);
-  E.zero(R);
-  E.contract(zc(-1), Moo, "mj", t2t, "imab", R, "ijab");
-  E.permute(zc(1), R, "ijab", X2, "ijab", true);
-  E.permute(zc(-1), R, "ijab", X2, "jiab", true);
+  // f = sum_e mu~_be t_ij^ae is antisymmetric in (i,j), g = sum_m mu~_mj t_im^ab in (a,b); the
+  // projection onto tensors antisymmetric in both pairs maps f - g to (P(ab) f - P(ij) g) / 2,
+  // so xi_2 = 2 project(f - g), formed in place (no temporary of o^2 v^2 entries)
+  E.zero(X2);
+  E.contract(zc(1), Mvv, "be", t2t, "ijae", X2, "ijab");
+  E.contract(zc(-1), Moo, "mj", t2t, "imab", X2, "ijab");
+  antisym_project(C128, o, v, X2.p, st);
+  vec_scal(C128, X2.numel(), zc(2.0), X2.p, st);
   CCLR_CUDA(cudaStreamSynchronize(st));
 }
 

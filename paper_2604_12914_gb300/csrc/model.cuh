@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "engine.cuh"
+#include "ladder_cc.cuh"
 #include "ladder_tc.cuh"
 
 namespace cclr {
@@ -23,6 +24,9 @@ struct CstSet {
   int dt = C128;
   std::array<DevBuf, K_NCST> buf;
   std::array<Tens, K_NCST> t;
+  // constants known to be zero: the operations that read them are skipped (a set built for a
+  // one-body operator alone has no two-body elements)
+  std::array<bool, K_NCST> zero{};
   bool valid = false;
 };
 
@@ -83,17 +87,17 @@ class Model {
   DevBuf t1, t2;                    // [o][v], [o][o][v][v]
   DevBuf h;                         // one-body part of H, [n][n]
   DevBuf Loo64, Lov64, Lvo64, Lvv64, h64;  // complex64 copies (complex64 builds)
-  DevBuf oovv_b;
-  Tens oovv_t;
+  DevBuf oovvp;                     // <ij||ab> packed [(i<j)][(a<b)], complex128 (T1-independent)
 
   CstSet c128, c64;                 // intermediates at the current T
-  DevBuf D1, D2;                    // preconditioner diagonal (real)
+  DevBuf D1, D2;                    // preconditioner diagonal (real): singles [o][v], packed doubles
   Program prog;
-  std::vector<std::vector<DevBuf>> tmp128, tmp64;  // program temporaries per precision and RHS
+  std::vector<DevBuf> tmp128, tmp64;  // program temporaries per precision (shared by the RHS)
+  std::vector<DevBuf> x2bar[2];       // per-RHS x2-bar of the transpose product, per precision
   int prec = 0;
-  DevBuf ladW;                      // ladder formation scratch (CUDA-core path)
-  LadderTC ltc[2];                  // packed tensor-core ladder: [0] TF32, [1] 3xTF32
-  const void *ltc_src[2] = {nullptr, nullptr};
+  LadderCC lcc;                     // packed CUDA-core ladder (FP64 and FP32 modes)
+  LadderTC ltc[3];                  // packed tensor-core ladder: [0] TF32, [1] 3xTF32, [2] bf16x3
+  const void *ltc_src[3] = {nullptr, nullptr, nullptr};
   float ms_last[4] = {0, 0, 0, 0};  // last apply(): ladder, everything else, total, ladder formation (ms)
   Timers tm;
   // CUDA graphs: with graphs on, a sigma program whose arguments (direction, constant set,
@@ -110,11 +114,19 @@ class Model {
   // Build dressed blocks + intermediates for amplitudes (t1d, t2d; complex128 device) in
   // precision dt (complex64 on the tensor cores with the 3xTF32 split).
   void build_set(const void *t1d, const void *t2d, CstSet &out, int dt);
+  // The set of the one-body operator B alone (no two-body part; complex128) at amplitudes
+  // (t1d, t2d): its sigma program is the Jacobian of xi^B(T) = Omega[B](T).
+  void build_set_onebody(const void *Bd, const void *t1d, const void *t2d, CstSet &out);
   void ensure_src64();
-  const Tens &oovv128();
+  const void *oovv_packed();
   void build_diagonal();
   const CstSet &cst_for(int prec_) ;
   void round_set(const CstSet &src, CstSet &dst);
+  // frees a set's buffers (it is rebuilt on its next use)
+  void release_set(CstSet &s);
+  // frees everything the FP64 products hold (the complex128 set, temporaries and the CUDA-core
+  // ladder's blocks); an FP64 product afterwards rebuilds them
+  void release_fp64();
 
   // sigma (dir = +1) or sigma^T (dir = -1) on device buffers of the given dtype.
   void apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2);
@@ -133,7 +145,7 @@ class Model {
   // the program itself; timed = event timing of the ladder (not while capturing)
   void apply_body(int dir, const CstSet &C, int nr, const void *const *x1, const void *const *x2,
                   void *const *s1, void *const *s2, bool timed, float &lad_ms, float &form_ms);
-  std::vector<DevBuf> &temps(int dt, int r);
+  std::vector<DevBuf> &temps(int dt);
   Tens var_tens(int id, int dt, void *p) const;
 };
 

@@ -164,8 +164,8 @@ extern "C" int cc_lr_selftest_gemm_noalloc(int M, int N, int K, int mode, unsign
     narrow(at(l.a128), at(l.a64), (int64_t)M * K, s);
     narrow(at(l.b128), at(l.b64), (int64_t)K * N, s);
     gemm_plain(C128, at(l.a128), at(l.b128), at(l.c128), M, N, K, s);  // FP64 reference
-    tc_prep_a(at(l.a64), K, 1, M, K, seg, (float *)at(l.ao), l.ld, s);
-    tc_prep_b(at(l.b64), N, 1, K, N, seg, (float *)at(l.bo), l.ld, s);
+    tc_prep_a(at(l.a64), K, 1, M, K, seg, TC_TF32, at(l.ao), l.ld, s);
+    tc_prep_b(at(l.b64), N, 1, K, N, seg, TC_TF32, at(l.bo), l.ld, s);
     tc_gemm_seg_flagged((const float *)at(l.ao), l.ld, (const float *)at(l.bo), l.ld, M, 2 * (int64_t)N,
                         2 * tc_kpad(K), seg, (float *)at(l.ct), 2 * (int64_t)N, zc(1.0), true, (int *)at(l.flag), s);
     gemm_plain(C64, at(l.a64), at(l.b64), at(l.cs), M, N, K, s);  // FP32 CUDA cores

@@ -1,4 +1,5 @@
-// tcgen05 TF32 GEMM for sm_103a, persistent and warp-specialised: one CTA per SM walks a
+// tcgen05 GEMM (kind::tf32 on TF32 operands, kind::f16 on BF16 operands) for sm_103a,
+// persistent and warp-specialised: one CTA per SM walks a
 // static list of (tile, K split) work units.  Warp 0 streams A/B K blocks with TMA (128-byte
 // swizzle) into a 4-stage shared-memory ring, warp 1 issues tcgen05.mma into one of two TMEM
 // accumulators, and warps 2-9 drain the other accumulator (tcgen05.ld -> registers ->
@@ -19,7 +20,7 @@ namespace cclr {
 namespace {
 
 constexpr int BM = 128;      // UMMA M
-constexpr int BK = 32;       // fp32 elements per K block = 128 bytes = one swizzle row
+constexpr int BKB = 128;     // bytes per K block = one 128-byte swizzle row (32 TF32 or 64 BF16)
 constexpr int STAGES = 4;
 constexpr unsigned long long TIMEOUT_NS = 2000000000ull;  // 2 s per wait
 
@@ -92,18 +93,29 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::tf32 / kind::f16: D FP32 (bits 4-5), A and B type (bits 7-9
+// and 10-12: TF32 = 2, BF16 = 1), both K-major, N >> 3 (bits 17-22), M >> 4 (bits 24-28).
+__host__ __device__ constexpr uint32_t idesc_mma(int kind, int M, int N) {
+  return (1u << 4) | ((kind == TC_BF16 ? 1u : 2u) << 7) | ((kind == TC_BF16 ? 1u : 2u) << 10) |
+         ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
-                                         uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-      :
-      : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+// one MMA of K = 32 bytes per row (8 TF32 or 16 BF16), D (+)= A B^T in TMEM
+template <int KIND>
+__device__ __forceinline__ void mma_issue(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  if constexpr (KIND == TC_BF16) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+        :
+        : "r"(tmem), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t bar) {
@@ -157,15 +169,17 @@ __device__ __forceinline__ void unit_coords(const TcParams &p, int u, int &m_til
 
 constexpr int EPI_PITCH = 18;  // floats per staged row (16 + 2): conflict-free float2 traffic
 
+template <int KIND>
 __global__ void __launch_bounds__(320, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    TcParams p) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  constexpr int BK = BKB / (KIND == TC_BF16 ? 2 : 4);  // operand elements per K block
   const int BN = p.BN;
-  float *sA = (float *)smem;
-  float *sB = (float *)(smem + STAGES * BM * BK * 4);
-  float *stage = (float *)(smem + STAGES * (BM + BN) * BK * 4);  // 8 warps x 32 rows x EPI_PITCH
+  uint8_t *sA = smem;
+  uint8_t *sB = smem + STAGES * BM * BKB;
+  float *stage = (float *)(smem + STAGES * (BM + BN) * BKB);  // 8 warps x 32 rows x EPI_PITCH
   // barriers: full[S], empty[S], tfull[2], tempty[2], drain
   uint64_t *bars = (uint64_t *)(stage + 8 * 32 * EPI_PITCH);
   uint64_t *full = bars, *empty = bars + STAGES, *tfull = bars + 2 * STAGES, *tempty = tfull + 2,
@@ -212,7 +226,7 @@ __global__ void __launch_bounds__(320, 1)
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer: K blocks of every unit of this CTA, through the ring
-      const uint32_t bytes = (uint32_t)(BM + BN) * BK * 4;
+      const uint32_t bytes = (uint32_t)(BM + BN) * BKB;
       int g = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x) {
@@ -226,8 +240,8 @@ __global__ void __launch_bounds__(320, 1)
           if (!mbar_wait_ab(su32(empty + s), ph ^ 1u, p.err, abort_flag)) { ok = false; break; }
           asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(full + s)), "r"(bytes)
                        : "memory");
-          tma_load_2d(sA + s * BM * BK, &tmA, (kb0 + kb) * BK, mt * BM, su32(full + s));
-          tma_load_2d(sB + s * BN * BK, &tmB, (kb0 + kb) * BK, nt * BN, su32(full + s));
+          tma_load_2d(sA + s * BM * BKB, &tmA, (kb0 + kb) * BK, mt * BM, su32(full + s));
+          tma_load_2d(sB + s * BN * BKB, &tmB, (kb0 + kb) * BK, nt * BN, su32(full + s));
           issued[0] = g + 1;
         }
       }
@@ -236,7 +250,7 @@ __global__ void __launch_bounds__(320, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer: accumulator buffer it & 1 for the it-th unit of this CTA
-      const uint32_t idesc = idesc_tf32(BM, BN);
+      const uint32_t idesc = idesc_mma(KIND, BM, BN);
       int g = 0, it = 0;
       bool ok = true;
       for (int u = blockIdx.x; u < units && ok; u += gridDim.x, ++it) {
@@ -254,11 +268,11 @@ __global__ void __launch_bounds__(320, 1)
           if (!mbar_wait_ab(su32(full + s), ph, p.err, abort_flag)) { ok = false; break; }
           consumed[0] = g + 1;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint64_t da = sw128_desc(su32(sA + s * BM * BK));
-          const uint64_t db = sw128_desc(su32(sB + s * BN * BK));
+          const uint64_t da = sw128_desc(su32(sA + s * BM * BKB));
+          const uint64_t db = sw128_desc(su32(sB + s * BN * BKB));
 #pragma unroll
-          for (int kk = 0; kk < BK / 8; ++kk)  // 8 tf32 = 32 bytes per instruction
-            mma_tf32(dacc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
+          for (int kk = 0; kk < BKB / 32; ++kk)  // 32 bytes of K per instruction (+2 in 16-byte units)
+            mma_issue<KIND>(dacc, da + 2 * kk, db + 2 * kk, idesc, (kb | kk) != 0 ? 1u : 0u);
           mma_commit(su32(empty + s));
         }
         if (ok) mma_commit(su32(tfull + buf));  // arrives once this unit's MMAs have completed
@@ -387,14 +401,9 @@ __global__ void wait_never_kernel(unsigned long long timeout_ns, int *err) {
 }
 
 // ---------------- operand preparation ----------------
-__device__ __forceinline__ float tf32_hi(float x) {
-  uint32_t u = __float_as_uint(x);
-  u = (u + 0x1000u) & 0xFFFFE000u;  // round the 13 dropped mantissa bits to nearest
-  return __uint_as_float(u);
-}
-
-__global__ void prep_a_kernel(const float2 *A, View2 mv, View2 kv, int64_t M, int64_t K,
-                              int64_t Kp, int seg, float *dst, int64_t ldd) {
+template <int KIND>
+__global__ void prep_a_kernel(const float2 *A, View2 mv, View2 kv, int64_t M, int64_t K, int64_t Kp, int seg,
+                              typename TcElem<KIND>::T *dst, int64_t ldd) {
   const int64_t total = M * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -402,24 +411,13 @@ __global__ void prep_a_kernel(const float2 *A, View2 mv, View2 kv, int64_t M, in
     if (kv.sin == 1 || mv.sin != 1) { k = e % Kp; m = e / Kp; } else { m = e % M; k = e / M; }
     float2 v = make_float2(0.f, 0.f);
     if (k < K) v = A[v2off(mv, m) + v2off(kv, k)];
-    float *row = dst + m * ldd;
-    if (seg == 1) {
-      row[2 * k] = v.x;
-      row[2 * k + 1] = v.y;
-    } else {
-      const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
-      row[2 * k] = hr;                 // [hi | hi | lo]
-      row[2 * k + 1] = hi;
-      row[2 * Kp + 2 * k] = hr;
-      row[2 * Kp + 2 * k + 1] = hi;
-      row[4 * Kp + 2 * k] = v.x - hr;
-      row[4 * Kp + 2 * k + 1] = v.y - hi;
-    }
+    tc_put_a<KIND>(dst + m * ldd, k, Kp, seg, v);
   }
 }
 
-__global__ void prep_b_kernel(const float2 *B, View2 kv, View2 nv, int64_t K, int64_t N,
-                              int64_t Kp, int seg, float *dst, int64_t ldd) {
+template <int KIND>
+__global__ void prep_b_kernel(const float2 *B, View2 kv, View2 nv, int64_t K, int64_t N, int64_t Kp, int seg,
+                              typename TcElem<KIND>::T *dst, int64_t ldd) {
   const int64_t total = N * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -427,27 +425,15 @@ __global__ void prep_b_kernel(const float2 *B, View2 kv, View2 nv, int64_t K, in
     if (kv.sin == 1 || nv.sin != 1) { k = e % Kp; n = e / Kp; } else { n = e % N; k = e / N; }
     float2 v = make_float2(0.f, 0.f);
     if (k < K) v = B[v2off(kv, k) + v2off(nv, n)];
-    float *r0 = dst + (2 * n) * ldd, *r1 = dst + (2 * n + 1) * ldd;
-    if (seg == 1) {
-      r0[2 * k] = v.x;
-      r0[2 * k + 1] = -v.y;
-      r1[2 * k] = v.y;
-      r1[2 * k + 1] = v.x;
-    } else {
-      const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
-      const float lr = v.x - hr, li = v.y - hi;
-      // [hi | lo | hi]
-      r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
-      r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
-      r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
-    }
+    tc_put_b<KIND>(dst + (2 * n) * ldd, dst + (2 * n + 1) * ldd, k, Kp, seg, v);
   }
 }
 
 // Transposing preparation: the source is contiguous along m (A) or n (B) and strided along
 // k; 32 x 32 tiles through shared memory so that reads and writes are both coalesced.
-__global__ void prep_tiled_kernel(const float2 *src, View2 mnv, View2 kv, int64_t MN, int64_t K,
-                                  int64_t Kp, int seg, int isB, float *dst, int64_t ldd) {
+template <int KIND>
+__global__ void prep_tiled_kernel(const float2 *src, View2 mnv, View2 kv, int64_t MN, int64_t K, int64_t Kp, int seg,
+                                  int isB, typename TcElem<KIND>::T *dst, int64_t ldd) {
   __shared__ float2 tile[32][33];
   const int64_t tmn = (MN + 31) / 32, tk = (Kp + 31) / 32;
   for (int64_t t = blockIdx.x; t < tmn * tk; t += gridDim.x) {
@@ -463,25 +449,8 @@ __global__ void prep_tiled_kernel(const float2 *src, View2 mnv, View2 kv, int64_
       const int64_t mn = mn0 + r, k = k0 + threadIdx.x;
       if (mn < MN && k < Kp) {
         const float2 v = tile[threadIdx.x][r];
-        if (!isB) {
-          float *row = dst + mn * ldd;
-          if (seg == 1) { row[2 * k] = v.x; row[2 * k + 1] = v.y; }
-          else {
-            const float hr = tf32_hi(v.x), hi = tf32_hi(v.y);
-            row[2 * k] = hr; row[2 * k + 1] = hi;
-            row[2 * Kp + 2 * k] = hr; row[2 * Kp + 2 * k + 1] = hi;
-            row[4 * Kp + 2 * k] = v.x - hr; row[4 * Kp + 2 * k + 1] = v.y - hi;
-          }
-        } else {
-          float *r0 = dst + (2 * mn) * ldd, *r1 = dst + (2 * mn + 1) * ldd;
-          if (seg == 1) { r0[2 * k] = v.x; r0[2 * k + 1] = -v.y; r1[2 * k] = v.y; r1[2 * k + 1] = v.x; }
-          else {
-            const float hr = tf32_hi(v.x), hi = tf32_hi(v.y), lr = v.x - hr, li = v.y - hi;
-            r0[2 * k] = hr; r0[2 * k + 1] = -hi; r1[2 * k] = hi; r1[2 * k + 1] = hr;
-            r0[2 * Kp + 2 * k] = lr; r0[2 * Kp + 2 * k + 1] = -li; r1[2 * Kp + 2 * k] = li; r1[2 * Kp + 2 * k + 1] = lr;
-            r0[4 * Kp + 2 * k] = hr; r0[4 * Kp + 2 * k + 1] = -hi; r1[4 * Kp + 2 * k] = hi; r1[4 * Kp + 2 * k + 1] = hr;
-          }
-        }
+        if (!isB) tc_put_a<KIND>(dst + mn * ldd, k, Kp, seg, v);
+        else tc_put_b<KIND>(dst + (2 * mn) * ldd, dst + (2 * mn + 1) * ldd, k, Kp, seg, v);
       }
     }
     __syncthreads();
@@ -512,6 +481,12 @@ int current_device() {
   return dev;
 }
 
+// raises the dynamic shared-memory limit of every kernel instantiation on the current device
+void set_smem_limits() {
+  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TC_TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel<TC_BF16>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+}
+
 // The current device's wait flag; the first use on a device allocates and clears it and raises
 // the kernel's shared-memory limit there.
 int *device_err() {
@@ -522,21 +497,24 @@ int *device_err() {
     int *p = nullptr;
     CCLR_CUDA(cudaMalloc(&p, sizeof(int)));
     CCLR_CUDA(cudaMemset(p, 0, sizeof(int)));
-    CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    set_smem_limits();
     g_err_dev[dev] = p;
   }
   return g_err_dev[dev];
 }
 
-CUtensorMap make_map(const float *base, int64_t rows, int64_t cols, int64_t ld, int box_rows) {
+// 2-D tensor map over a row-major operand (rows x cols elements, ld elements apart), boxes of
+// one 128-byte K block by box_rows rows, 128-byte swizzle
+CUtensorMap make_map(const void *base, int64_t rows, int64_t cols, int64_t ld, int box_rows, int kind) {
   CUtensorMap m;
+  const int64_t es = tc_esize(kind);
   cuuint64_t gdim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-  cuuint64_t gstride[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint64_t gstride[1] = {(cuuint64_t)(ld * es)};
+  cuuint32_t box[2] = {(cuuint32_t)(BKB / es), (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = g_encode(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)base, gdim, gstride,
-                                      box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = g_encode(&m, kind == TC_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        (void *)base, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) throw Error(4, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return m;
 }
@@ -570,60 +548,67 @@ unsigned grid1d(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
 }
 
+template <int KIND>
+void prep_launch(const void *src, View2 mv, View2 kv, int64_t MN, int64_t K, int seg, int isB, void *dst, int64_t ldd,
+                 cudaStream_t st) {
+  using T = typename TcElem<KIND>::T;
+  const int64_t Kp = tc_kpad(K);
+  const bool tiled = kv.sin != 1 && mv.sin == 1 && MN >= 8;
+  if (tiled) {
+    const int64_t nt = ((MN + 31) / 32) * ((Kp + 31) / 32);
+    prep_tiled_kernel<KIND><<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
+        (const float2 *)src, mv, kv, MN, K, Kp, seg, isB, (T *)dst, ldd);
+  } else if (!isB) {
+    prep_a_kernel<KIND><<<grid1d(MN * Kp), 256, 0, st>>>((const float2 *)src, mv, kv, MN, K, Kp, seg, (T *)dst, ldd);
+  } else {
+    prep_b_kernel<KIND><<<grid1d(MN * Kp), 256, 0, st>>>((const float2 *)src, kv, mv, K, MN, Kp, seg, (T *)dst, ldd);
+  }
+}
+
 }  // namespace
 
-void tc_prep_a2(const void *A, View2 mv, View2 kv, int64_t M, int64_t K, int seg, float *dst, int64_t ldd,
+void tc_prep_a2(const void *A, View2 mv, View2 kv, int64_t M, int64_t K, int seg, int kind, void *dst, int64_t ldd,
                 cudaStream_t st) {
-  const int64_t Kp = tc_kpad(K);
-  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_a: row too short");
-  if (kv.sin != 1 && mv.sin == 1 && M >= 8) {
-    const int64_t nt = ((M + 31) / 32) * ((Kp + 31) / 32);
-    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
-        (const float2 *)A, mv, kv, M, K, Kp, seg, 0, dst, ldd);
-  } else {
-    prep_a_kernel<<<grid1d(M * Kp), 256, 0, st>>>((const float2 *)A, mv, kv, M, K, Kp, seg, dst, ldd);
-  }
+  CCLR_REQUIRE(ldd >= 2 * tc_kpad(K) * seg, "tc_prep_a: row too short");
+  if (kind == TC_BF16) prep_launch<TC_BF16>(A, mv, kv, M, K, seg, 0, dst, ldd, st);
+  else prep_launch<TC_TF32>(A, mv, kv, M, K, seg, 0, dst, ldd, st);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
-void tc_prep_b2(const void *B, View2 kv, View2 nv, int64_t K, int64_t N, int seg, float *dst, int64_t ldd,
+void tc_prep_b2(const void *B, View2 kv, View2 nv, int64_t K, int64_t N, int seg, int kind, void *dst, int64_t ldd,
                 cudaStream_t st) {
-  const int64_t Kp = tc_kpad(K);
-  CCLR_REQUIRE(ldd >= 2 * Kp * seg, "tc_prep_b: row too short");
-  if (kv.sin != 1 && nv.sin == 1 && N >= 8) {
-    const int64_t nt = ((N + 31) / 32) * ((Kp + 31) / 32);
-    prep_tiled_kernel<<<(unsigned)std::min<int64_t>(nt, 152 * 64), dim3(32, 8), 0, st>>>(
-        (const float2 *)B, nv, kv, N, K, Kp, seg, 1, dst, ldd);
-  } else {
-    prep_b_kernel<<<grid1d(N * Kp), 256, 0, st>>>((const float2 *)B, kv, nv, K, N, Kp, seg, dst, ldd);
-  }
+  CCLR_REQUIRE(ldd >= 2 * tc_kpad(K) * seg, "tc_prep_b: row too short");
+  if (kind == TC_BF16) prep_launch<TC_BF16>(B, nv, kv, N, K, seg, 1, dst, ldd, st);
+  else prep_launch<TC_TF32>(B, nv, kv, N, K, seg, 1, dst, ldd, st);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
-void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, float *dst,
+void tc_prep_a(const void *A, int64_t sam, int64_t sak, int64_t M, int64_t K, int seg, int kind, void *dst,
                int64_t ldd, cudaStream_t st) {
-  tc_prep_a2(A, view1(sam), view1(sak), M, K, seg, dst, ldd, st);
+  tc_prep_a2(A, view1(sam), view1(sak), M, K, seg, kind, dst, ldd, st);
 }
 
-void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, float *dst,
+void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, int seg, int kind, void *dst,
                int64_t ldd, cudaStream_t st) {
-  tc_prep_b2(B, view1(sbk), view1(sbn), K, N, seg, dst, ldd, st);
+  tc_prep_b2(B, view1(sbk), view1(sbn), K, N, seg, kind, dst, ldd, st);
 }
 
-// a_cols: real columns A actually holds per row (<= Kreal; the rest reads as zero)
-static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-                         int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+// a_cols: operand elements A actually holds per row (<= Kreal; the rest reads as zero).
+// lda, ldb, Kreal in elements of the operand type.
+static void tc_gemm_core(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kreal, int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
                          int max_kb_per_split, int *err, cudaStream_t st, int64_t a_cols = -1) {
   if (M <= 0 || Nreal <= 0) return;
+  const int64_t es = tc_esize(kind), BK = BKB / es;
   CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
-  CCLR_REQUIRE(lda % 4 == 0 && ldb % 4 == 0, "tc_gemm: leading dimensions must be multiples of 16 bytes");
+  CCLR_REQUIRE((lda * es) % 16 == 0 && (ldb * es) % 16 == 0, "tc_gemm: row pitches must be multiples of 16 bytes");
   CCLR_REQUIRE(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, "tc_gemm: operands must be 16-byte aligned");
   CCLR_REQUIRE(M < (1ll << 31) && Nreal < (1ll << 31) && Kreal < (1ll << 31), "tc_gemm: dimension too large");
   const int BN = pick_bn(Nreal);
-  const CUtensorMap ma = make_map(A, M, a_cols < 0 ? Kreal : a_cols, lda, BM);
-  const CUtensorMap mb = make_map(B, Nreal, Kreal, ldb, BN);
+  const CUtensorMap ma = make_map(A, M, a_cols < 0 ? Kreal : a_cols, lda, BM, kind);
+  const CUtensorMap mb = make_map(B, Nreal, Kreal, ldb, BN, kind);
   TcParams p;
   p.M = (int)M;
   p.N = (int)Nreal;
@@ -632,7 +617,7 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
   p.nMt = (int)((M + BM - 1) / BM);
   p.nNt = (int)((Nreal + BN - 1) / BN);
   // band of M tiles whose A rows (about 32 MB) stay in L2 while N sweeps
-  p.band = (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * 4 + 1)));
+  p.band = (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * es + 1)));
   const int nk = (int)((Kreal + BK - 1) / BK);
   const int64_t tiles = (int64_t)p.nMt * p.nNt;
   const int nsm = num_sms();
@@ -666,45 +651,43 @@ static void tc_gemm_core(const float *A, int64_t lda, const float *B, int64_t ld
   CCLR_REQUIRE(units < (1ll << 31), "tc_gemm: too many work units");
   static const bool trace = std::getenv("CCLR_TRACE") && std::getenv("CCLR_TRACE")[0] == '1';
   if (trace)
-    std::fprintf(stderr, "cclr tc_gemm M=%lld N=%lld K=%lld BN=%d tiles=%lld splits=%d band=%d atomic=%d transposed=%d\n",
-                 (long long)M, (long long)Nreal, (long long)Kreal, BN, (long long)tiles, splits, p.band, p.atomic,
+    std::fprintf(stderr, "cclr tc_gemm kind=%d M=%lld N=%lld K=%lld BN=%d tiles=%lld splits=%d band=%d atomic=%d transposed=%d\n",
+                 kind, (long long)M, (long long)Nreal, (long long)Kreal, BN, (long long)tiles, splits, p.band, p.atomic,
                  p.transposed);
-  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BK * 4 + (size_t)8 * 32 * EPI_PITCH * 4 +
+  const size_t smem = 1024 + (size_t)STAGES * (BM + BN) * BKB + (size_t)8 * 32 * EPI_PITCH * 4 +
                       (2 * STAGES + 5) * 8 + 16;
   const unsigned grid = (unsigned)std::min<int64_t>(units, nsm);
-  tc_gemm_kernel<<<grid, 320, smem, st>>>(ma, mb, p);
+  if (kind == TC_BF16) tc_gemm_kernel<TC_BF16><<<grid, 320, smem, st>>>(ma, mb, p);
+  else tc_gemm_kernel<TC_TF32><<<grid, 320, smem, st>>>(ma, mb, p);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
-static void tc_gemm_impl(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-                         int64_t Kreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
-                         int max_kb_per_split, cudaStream_t st) {
-  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kreal, C, rv, cv, alpha, accumulate, max_kb_per_split, device_err(), st);
-}
-
 void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
              int64_t Kreal, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
-  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kreal, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, 0, st);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kreal, TC_TF32, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, 0,
+               device_err(), st);
 }
 
 // The tensor-core accumulation error was measured to grow linearly with the chain length,
-// so the split passes keep every accumulator to at most 64 K blocks (2048 real K) and sum
-// the partial tiles in FP32.
-void tc_gemm_seg_v(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-                   int64_t Kseg, int seg, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
-                   cudaStream_t st) {
+// so the split passes keep every accumulator to at most 64 K blocks (2048 real K in TF32, 4096
+// in BF16) and sum the partial tiles in FP32.
+void tc_gemm_seg_v(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal, int64_t Kseg,
+                   int seg, int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st) {
+  int *err = device_err();
   if (seg == 1) {
-    tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, accumulate, 0, st);
+    tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, kind, C, rv, cv, alpha, accumulate, 0, err, st);
     return;
   }
-  tc_gemm_impl(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, rv, cv, alpha, accumulate, 64, st);
-  tc_gemm_impl(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, true, 64, st);
+  const int64_t es = tc_esize(kind);
+  tc_gemm_core((const char *)A + Kseg * es, lda, (const char *)B + Kseg * es, ldb, M, Nreal, 2 * Kseg, kind, C, rv,
+               cv, alpha, accumulate, 64, err, st);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, kind, C, rv, cv, alpha, true, 64, err, st);
 }
 
 void tc_gemm_a_inplace(const void *A, int64_t lda_cpx, int64_t K, const float *B, int64_t ldb, int64_t M,
                        int64_t Nreal, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st) {
-  tc_gemm_core((const float *)A, 2 * lda_cpx, B, ldb, M, Nreal, 2 * tc_kpad(K), C, rv, cv, alpha, accumulate, 0,
+  tc_gemm_core(A, 2 * lda_cpx, B, ldb, M, Nreal, 2 * tc_kpad(K), TC_TF32, C, rv, cv, alpha, accumulate, 0,
                device_err(), st, 2 * K);
 }
 
@@ -712,15 +695,14 @@ bool tc_a_inplace_ok(const void *A, int64_t lda_cpx, int64_t K) {
   return ((uintptr_t)A % 16) == 0 && lda_cpx % 2 == 0 && lda_cpx >= K && 8 * lda_cpx < (1ll << 40);
 }
 
-void tc_gemm_seg(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
-                 int64_t Kseg, int seg, float *C, int64_t ldc_floats, zc alpha, bool accumulate,
-                 cudaStream_t st) {
-  tc_gemm_seg_v(A, lda, B, ldb, M, Nreal, Kseg, seg, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, st);
+void tc_gemm_seg(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal, int64_t Kseg,
+                 int seg, int kind, float *C, int64_t ldc_floats, zc alpha, bool accumulate, cudaStream_t st) {
+  tc_gemm_seg_v(A, lda, B, ldb, M, Nreal, Kseg, seg, kind, C, view1(ldc_floats / 2), view1(1), alpha, accumulate, st);
 }
 
 void tc_setup_device_flagged() {
   std::call_once(g_enc_once, fetch_encoder);
-  CCLR_CUDA(cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  set_smem_limits();
 }
 
 void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
@@ -729,11 +711,11 @@ void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ld
   CCLR_REQUIRE(g_encode != nullptr, "tc_gemm_seg_flagged: tc_setup_device_flagged was not called");
   const View2 rv = view1(ldc_floats / 2), cv = view1(1);
   if (seg == 1) {
-    tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, accumulate, 0, err, st);
+    tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, TC_TF32, C, rv, cv, alpha, accumulate, 0, err, st);
     return;
   }
-  tc_gemm_core(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, C, rv, cv, alpha, accumulate, 64, err, st);
-  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, C, rv, cv, alpha, true, 64, err, st);
+  tc_gemm_core(A + Kseg, lda, B + Kseg, ldb, M, Nreal, 2 * Kseg, TC_TF32, C, rv, cv, alpha, accumulate, 64, err, st);
+  tc_gemm_core(A, lda, B, ldb, M, Nreal, Kseg, TC_TF32, C, rv, cv, alpha, true, 64, err, st);
 }
 
 int tc_selftest_timeout(int timeout_us, cudaStream_t st) {

@@ -80,3 +80,20 @@ def test_binding_declares_every_signature(lib):
         fn = getattr(lib, name)
         assert fn.argtypes is not None, name
         assert len(fn.argtypes) == n, (name, len(fn.argtypes), n)
+
+
+def _enum(name):
+    src = open(os.path.join(ROOT, "include", "cclr.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef enum \{([^}]*)\}\s*" + name + ";", src).group(1)
+    return {k: int(v) for k, v in re.findall(r"(CCLR_\w+)\s*=\s*(\d+)", body)}
+
+
+def test_precision_enum_matches_binding():
+    """cclr_prec in the header (FP64, TF32, 3xTF32, FP32, BF16X3) is what the binding passes."""
+    from paper_2604_12914_gb300 import binding
+    e = _enum("cclr_prec")
+    assert e == {"CCLR_FP64": 0, "CCLR_C64_TF32": 1, "CCLR_C64_3XTF32": 2, "CCLR_C64_FP32": 3, "CCLR_BF16X3": 4}
+    assert binding.PREC == {"fp64": 0, "tf32": 1, "3xtf32": 2, "fp32": 3, "bf16x3": 4}
+    st = _enum("cclr_status")
+    assert st["CCLR_ENOMEM"] == binding.CCLR_ENOMEM and st["CCLR_ENOCONV"] == binding.CCLR_ENOCONV
