@@ -7,7 +7,13 @@ vectors, the ring / crossed, hole-hole and three-body terms, and the antisymmetr
 Workload: o=32 occupied, v=240 virtual spinors, naux=1200 Cholesky vectors (synthetic,
 seeded; T1 = 0, first-order T2), the single-RHS sigma configuration.
 
-  python bench.py [--gpus N --steps K --warmup W --prec tf32|3xtf32|fp32|fp64]
+Beside the headline (TF32 on the tensor cores) the line carries: sigma-vectors/s in every
+precision mode, the batched sigma (9 RHS), the HBM-bound kernels against the copy bandwidth,
+time-to-alpha (FP64 against mixed precision at o=10 v=40; mixed precision by both response
+routes at o=32 v=240), the 21-RHS batch at o=40 v=320 and the o=56 v=480 workload with their
+device memory, and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N --steps K --warmup W --prec tf32|3xtf32|bf16x3|fp32|fp64]
   python bench.py --impl reference     (the CPU oracle on a bounded sample)
 
 Prints one JSON line (rank 0).  N > 1 (torchrun): independent replicas, one per GPU
@@ -40,13 +46,17 @@ def parse():
     ap.add_argument("--prec", default=os.environ.get("CCLR_BENCH_PREC", "tf32"))
     ap.add_argument("--config", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-ladder-chunks", type=int, default=2)
     ap.add_argument("--no-alpha", action="store_true")
     ap.add_argument("--alpha-config", default="C1")
     ap.add_argument("--alpha-scale", type=float, default=0.2)
     ap.add_argument("--batch-rhs", type=int, default=9)
     ap.add_argument("--no-alpha-large", action="store_true")
     ap.add_argument("--no-ablation", action="store_true")
+    ap.add_argument("--no-precisions", action="store_true")
+    ap.add_argument("--no-hbm", action="store_true")
+    ap.add_argument("--no-c3", action="store_true")
+    ap.add_argument("--no-c5", action="store_true")
     ap.add_argument("--alpha-large-config", default="C2")
     ap.add_argument("--alpha-large-scale", type=float, default=0.05)
     return ap.parse_args()
@@ -58,15 +68,17 @@ def algorithmic(o, v, naux):
     form = naux * Pv * v * v          # <ab|ef>~ for a<b, all (e, f)
     contr = Po * Pv * Pv              # sum_{e<f} <ab||ef>~ X_ij^ef
     ring = o ** 3 * v ** 3
+    hh = 3 * Po * Po * Pv
+    ovn = o * o * v * v * naux
     return {"ladder_cmac": form + contr, "form_cmac": form, "ring_cmac": ring,
-            "n_unique": o * v + Po * Pv}
+            "total_cmac": form + contr + ring + hh + ovn, "n_unique": o * v + Po * Pv}
 
 
-# DRAM bytes (read + write) per executed FLOP of the formation GEMM, from the ncu capture in
-# profiles/tc_gemm_ladder_formation_C2.md (one launch of 28800 x 7680 x 1200 complex:
-# 1.793388 GB read + 1.740861 GB written for 8 M N K = 2.1234e12 FLOP).  With K = naux fixed,
-# both the output writes and the per-band operand reads scale with M N, so the ratio carries
-# over to every group of the same workload.
+# DRAM bytes (read + write) per executed FLOP of the formation GEMM: one ncu capture of one
+# formation launch of the workload (M = 28800 rows (b,f), N = 7680 complex columns (a,e),
+# K = 1200: 1.793388 GB read + 1.740861 GB written for 8 M N K = 2.1234e12 FLOP).  With K =
+# naux fixed, both the output writes and the per-band operand reads scale with M N, so the
+# ratio carries over to every group of the same workload.
 FORMATION_BYTES_PER_FLOP = (1.793388e9 + 1.740861e9) / (8 * 28800 * 7680 * 1200)
 
 
@@ -94,6 +106,8 @@ def ladder_peak(prec):
     if prec in ("tf32", "3xtf32"):
         # tf32 dense is half the bf16 dense rate (1.1 vs 2.25 PFLOP/s nominal)
         return "tensor", d["bf16_tflops"] * (1.1 / 2.25), f"{how} bf16 x nominal tf32/bf16 ratio"
+    if prec == "bf16x3":
+        return "tensor", d["bf16_tflops"], f"{how} bf16"
     if prec == "fp32":
         # 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
         return "alu", 152 * 128 * 2 * 2.07e9 / 1e12, "derived: SM count x FP32 lanes x max clock"
@@ -170,53 +184,101 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-class OracleSample:
-    """The oracle, as it is, on a bounded sample: sigma entries evaluated one by one."""
+def host_cpu():
+    model = ""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for l in out.splitlines():
+            if l.startswith("Model name"):
+                model = l.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return {"nproc": os.cpu_count(), "model": model}
+
+
+class OracleTiming:
+    """The oracle as it stands (oracle.sampled's whole-vector sigma: every term but the ladder
+    vectorised, the ladder's <ab|ef>~ formed chunk by chunk of 8 a values from L~_vv), timed on
+    the host cores.  T-dependent intermediates (first-order T2, dressed blocks, Wovvo, Wovoo) are
+    set-up and excluded, as the library's init is; the X-dependent work is timed."""
+
+    CHUNK = 8
 
     def __init__(self, cfg, seed):
         import torch
         from oracle import ccsd, sampled
         from oracle.integrals import as_t
-        from paper_2604_12914_gb300.inputs import make_config, random_amplitudes
-
+        from paper_2604_12914_gb300.inputs import make_config
         s = make_config(cfg, seed=seed)
         self.cfg, self.o, self.v, self.naux = cfg, s.o, s.v, s.naux
-        L, eps = as_t(s.L), as_t(s.eps)
         t0 = time.perf_counter()
+        eps, L = as_t(s.eps), as_t(s.L)
         t2 = ccsd.first_order_t2_from_L(eps, L, s.o)
         self.E = sampled.EntrySigma(eps, L, torch.zeros(s.o, s.v, dtype=torch.complex128), t2)
-        x1, x2 = map(as_t, random_amplitudes(s.o, s.v, seed=seed + 1000))
-        self.E.set_x(x1, x2)
+        self.E.Wovvo_full()
+        self.E.Wovoo_full()
         self.setup = time.perf_counter() - t0
         self.threads = torch.get_num_threads()
-        import numpy as np
-        self.rng = np.random.default_rng(seed)
+        self.nchunks = (s.v + self.CHUNK - 1) // self.CHUNK
+        self.seed = seed
+        self.t_rest = None
+        self.k = 0
 
-    def sample(self, seconds):
-        o, v, E, rng = self.o, self.v, self.E, self.rng
-        n2 = n1 = 0
-        t2 = t1 = 0.0
+    def rest(self):
+        """X-dependent work of one sigma except the ladder (seconds)."""
+        from oracle.integrals import as_t
+        from paper_2604_12914_gb300.inputs import random_amplitudes
+        x1, x2 = map(as_t, random_amplitudes(self.o, self.v, seed=self.seed + 1000))
         t0 = time.perf_counter()
-        while time.perf_counter() - t0 < seconds or n1 == 0:
-            i, j = rng.choice(o, 2, replace=False)
-            a, b = rng.choice(v, 2, replace=False)
-            ta = time.perf_counter()
-            E.sigma2(int(i), int(j), int(a), int(b))
-            t2 += time.perf_counter() - ta
-            n2 += 1
-            if n2 % 8 == 0 or n1 == 0:
-                ta = time.perf_counter()
-                E.sigma1(int(rng.integers(o)), int(rng.integers(v)))
-                t1 += time.perf_counter() - ta
-                n1 += 1
-        alg = algorithmic(o, v, self.naux)
-        # time of one vector = per-entry time x number of unique entries of each block
-        t_vec = (t2 / n2) * (alg["n_unique"] - o * v) + (t1 / n1) * (o * v)
-        return {"value": 1.0 / t_vec, "unit": "sigma-vectors/s", "cores": self.threads,
-                "kind": "oracle",
-                "sample": f"{n2} doubles + {n1} singles entries of sigma at {self.cfg} "
-                          f"(oracle.sampled, {t1 + t2:.1f} s; setup {self.setup:.1f} s excluded), "
-                          f"scaled by the {alg['n_unique']} unique amplitudes of one vector"}
+        self.E.set_x(x1, x2)
+        _, self.s2 = self.E.sigma_rest()
+        self.t_rest = time.perf_counter() - t0
+        return self.t_rest
+
+    def chunk(self):
+        """One ladder chunk (the next of evenly spread a0 values), seconds."""
+        a0 = ((self.k * 7) % self.nchunks) * self.CHUNK
+        self.k += 1
+        t0 = time.perf_counter()
+        self.E.ladder_chunk(a0, min(self.v, a0 + self.CHUNK), self.s2)
+        return time.perf_counter() - t0
+
+    def sigma_time(self, chunk_times):
+        return self.t_rest + self.nchunks * sum(chunk_times) / len(chunk_times)
+
+    def describe(self, nchunks_timed):
+        return (f"one sigma at {self.cfg} o={self.o} v={self.v} naux={self.naux}: oracle.sampled's X-dependent "
+                f"work (set_x + sigma_rest, {self.t_rest:.1f} s, timed whole) plus {nchunks_timed} of the "
+                f"{self.nchunks} ladder chunks of {self.CHUNK} a values (timed, scaled to all chunks); T-dependent "
+                f"set-up ({self.setup:.1f} s) excluded")
+
+
+def cpu_small(cfg="C1"):
+    """The oracle's whole sigma at a small workload, all threads and one thread."""
+    import torch
+    from oracle import ccsd, sampled
+    from oracle.integrals import as_t
+    from paper_2604_12914_gb300.inputs import make_config, random_amplitudes
+    s = make_config(cfg, seed=1)
+    eps, L = as_t(s.eps), as_t(s.L)
+    E = sampled.EntrySigma(eps, L, torch.zeros(s.o, s.v, dtype=torch.complex128),
+                           ccsd.first_order_t2_from_L(eps, L, s.o))
+    E.Wovvo_full()
+    E.Wovoo_full()
+    x1, x2 = map(as_t, random_amplitudes(s.o, s.v, seed=5))
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, whole sigma (oracle.sampled.sigma_blocked)"}
+    nt = torch.get_num_threads()
+    for label, threads in (("all_threads", nt), ("one_thread", 1)):
+        torch.set_num_threads(threads)
+        E.set_x(x1, x2)
+        E.sigma_blocked()
+        t0 = time.perf_counter()
+        E.set_x(x1, x2)
+        E.sigma_blocked()
+        el = time.perf_counter() - t0
+        out[label] = {"threads": threads, "seconds": el, "sigma_vectors_per_s": 1.0 / el}
+    torch.set_num_threads(nt)
+    return out
 
 
 def run_reference(args):
@@ -225,21 +287,22 @@ def run_reference(args):
         return
     from paper_2604_12914_gb300.inputs import CONFIGS
     c = CONFIGS[args.config]
-    S = OracleSample(args.config, 2)
-    per = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
-    vals = []
-    last = None
+    T = OracleTiming(args.config, 2)
+    T.rest()
+    times = []
     for k in range(args.warmup + args.steps):
-        last = S.sample(per)
+        t = T.chunk()
         if k >= args.warmup:
-            vals.append(last["value"])
-    v = sum(vals) / len(vals)
+            times.append(t)
+    v = 1.0 / T.sigma_time(times)
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "sigma-vectors/s",
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "c128", "data": "synthetic (seeded; T1=0, first-order T2)",
            "config": {"workload": f"{args.config} o={c['o']} v={c['v']} naux={c['naux']} single-RHS sigma"},
-           "cpu_baseline": {**last, "value": v},
+           "cpu_baseline": {"value": v, "unit": "sigma-vectors/s", "cores": T.threads, "kind": "oracle",
+                            "host": host_cpu(),
+                            "sample": T.describe(args.steps) + "; each timed step is one ladder chunk"},
            "e2e": {"value": v, "unit": "sigma-vectors/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
            "gpu_launches": 0}
     print(json.dumps(out), flush=True)
@@ -250,13 +313,13 @@ def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428),
     on the same synthetic system and to the same relative residual tol; returns both times
     and max |delta alpha| (a.u.)."""
     import numpy as np
+    import torch
     from paper_2604_12914_gb300 import binding
     from paper_2604_12914_gb300.inputs import make_config
     s = make_config(cfg, scale=scale)
     out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
            "components": list(comps), "omegas": list(omegas), "tol": tol}
     res = {}
-    import torch
     for tag, prec in (("fp64", "fp64"), ("mixed", prec_mixed)):
         stream = torch.cuda.Stream()
         ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec, stream=stream.cuda_stream)
@@ -282,9 +345,12 @@ def time_to_alpha(cfg, scale, prec_mixed, comps=(0, 1, 2), omegas=(0.0, 0.0428),
 
 def time_to_alpha_large(cfg, scale, comps=(2,), omegas=(0.0,), tol=1e-6):
     """Wall time of cc_lr_solve on the large workload with tensor-core arithmetic throughout
-    the solve: TF32 corrections, 3xTF32 refinement residuals and F X stencils, FP64 vectors,
-    Krylov subspace and alpha contractions.  (One FP64 sigma at this size takes about a minute on
-    this GPU, so the FP64 path is not run here.)"""
+    the solve (TF32 corrections, 3xTF32 refinement residuals and F X stencils; FP64 vectors,
+    Krylov subspace and alpha contractions), then alpha again by the left-hand route
+    (cc_lr_solve_left): the two routes agree to the solves' accuracy, so |alpha_left -
+    alpha_right| is an a-posteriori estimate of the error.  (One FP64 sigma at this size takes
+    tens of seconds on this GPU; the FP64 path's solve is not run here.)"""
+    import numpy as np
     from paper_2604_12914_gb300 import binding
     from paper_2604_12914_gb300.inputs import make_config
     s = make_config(cfg, scale=scale)
@@ -295,6 +361,10 @@ def time_to_alpha_large(cfg, scale, comps=(2,), omegas=(0.0,), tol=1e-6):
     t0 = time.perf_counter()
     al, st = ctx.cc_lr_solve(list(omegas), comps, tol=tol, allow_noconv=True)
     el = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    alL, stL = ctx.cc_lr_solve_left(list(omegas), comps, tol=tol, allow_noconv=True)
+    elL = time.perf_counter() - t0
+    mem = ctx.cc_lr_memory()
     ctx.close()
     return {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
             "components": list(comps), "omegas": list(omegas), "tol": tol,
@@ -304,7 +374,72 @@ def time_to_alpha_large(cfg, scale, comps=(2,), omegas=(0.0,), tol=1e-6):
             "converged": st["converged"], "max_rel_residual": st["max_rel_residual"],
             "seconds_solve_lambda_alpha": [st["time_solve_ms"] / 1e3, st["time_lambda_ms"] / 1e3,
                                            st["time_alpha_ms"] / 1e3],
-            "alpha": [[float(al[w, a, a].real) for a in range(len(comps))] for w in range(len(omegas))]}
+            "alpha": [[float(al[w, a, a].real) for a in range(len(comps))] for w in range(len(omegas))],
+            "left_route": {"seconds": elL, "converged": stL["converged"],
+                           "alpha": [[float(alL[w, a, a].real) for a in range(len(comps))] for w in range(len(omegas))],
+                           "max_abs_left_minus_right_au": float(np.abs(alL - al).max())},
+            "device_memory_peak_gb": mem[1] / 1e9}
+
+
+def packed_batch(cfg, nrhs, precs, reps=2):
+    """sigma-vectors/s of an nrhs batch in the packed unique-amplitude layout at workload cfg
+    (lean memory: the FP64 state is released), with the context's device memory."""
+    import torch
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import make_config
+    s = make_config(cfg)
+    t0 = time.perf_counter()
+    stream = torch.cuda.current_stream()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=precs[0], stream=stream.cuda_stream)
+    ctx.cc_lr_set_refinement("3xtf32")          # no FP64 product: its set is released
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, {nrhs} RHS in one batched product (packed layout)",
+           "init_seconds": time.perf_counter() - t0, "nrhs": nrhs}
+    del s
+    g = torch.Generator(device="cuda")
+    g.manual_seed(11)
+    x = torch.randn(nrhs, ctx.n_packed(), dtype=torch.complex128, device="cuda", generator=g)
+    y = torch.empty_like(x)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for p in precs:
+        ctx.cc_lr_set_precision(p)
+        ctx.sigma_packed(x, y, nrhs=nrhs)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(reps):
+            ctx.sigma_packed(x, y, nrhs=nrhs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        tm = ctx.cc_lr_last_timings()
+        out[p] = {"ms_per_batch": ms, "sigma_vectors_per_s": nrhs / (ms / 1e3), "ladder_ms": float(tm[0]),
+                  "formation_ms": float(tm[3]), "ladder_group_size": ctx.cc_lr_ladder_tuning(p)[0]}
+    used, peak, _ = ctx.cc_lr_memory()
+    out["device_memory_gb"] = {"held": used / 1e9, "peak": peak / 1e9,
+                               "caller_vectors": 2 * x.numel() * 16 / 1e9}
+    ctx.close()
+    return out
+
+
+def cublas_tf32_tflops():
+    """cuBLAS TF32 GEMM 8192^3 (torch.matmul on FP32 with TF32 allowed), best of 5, CUDA events."""
+    import torch
+    n = 8192
+    a = torch.randn(n, n, device="cuda")
+    b = torch.randn(n, n, device="cuda")
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    best = 1e30
+    for _ in range(6):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    del a, b
+    torch.cuda.empty_cache()
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 def run_cclr(args):
@@ -312,14 +447,23 @@ def run_cclr(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cpu = None
+    cpu_c1 = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = OracleSample(args.config, 2).sample(args.cpu_seconds)   # before any GPU call
+        # before any GPU call: the oracle on the host cores
+        T = OracleTiming(args.config, 2)
+        T.rest()
+        ch = [T.chunk() for _ in range(max(1, args.cpu_ladder_chunks))]
+        cpu = {"value": 1.0 / T.sigma_time(ch), "unit": "sigma-vectors/s", "cores": T.threads, "kind": "oracle",
+               "host": host_cpu(), "sample": T.describe(len(ch)),
+               "seconds_per_sigma": T.sigma_time(ch), "seconds_rest": T.t_rest, "seconds_per_ladder_chunk": ch}
+        del T
+        cpu_c1 = cpu_small("C1")
 
     import numpy as np
     import torch
     import torch.distributed as dist
     from paper_2604_12914_gb300 import binding
-    from paper_2604_12914_gb300.inputs import CONFIGS, make_config, random_amplitudes
+    from paper_2604_12914_gb300.inputs import make_config, random_amplitudes
 
     torch.cuda.set_device(local)
     if world > 1:
@@ -377,6 +521,7 @@ def run_cclr(args):
     barrier()
     e2e = replica_throughput(world, args.steps, reduce_max(e0.elapsed_time(e1)))
     bytes_io = (x1p.numel() + x2p.numel()) * 16
+    del x1p, x2p, s1p, s2p
 
     # batched: several right-hand sides share each formed <ab||ef>~ block
     batched = None
@@ -428,6 +573,35 @@ def run_cclr(args):
     alg = algorithmic(o, v, naux)
     lad_ms = sum(lad) / len(lad)
     form_ms = sum(form) / len(form)
+    tga = ctx.cc_lr_ladder_tuning(args.prec)[0] if args.prec in ("tf32", "3xtf32", "bf16x3") else None
+
+    # every precision mode on the same workload and context
+    precisions = None
+    if not args.no_precisions:
+        precisions = {}
+        for p in ("3xtf32", "bf16x3", "fp32", "fp64"):
+            if p == args.prec:
+                continue
+            ctx.cc_lr_set_precision(p)
+            ctx.sigma_into(x1, x2, s1, s2)
+            barrier()
+            k = 1 if p == "fp64" else 3
+            lp = []
+            e0.record(stream)
+            for _ in range(k):
+                ctx.sigma_into(x1, x2, s1, s2)
+                lp.append(float(ctx.cc_lr_last_timings()[0]))
+            e1.record(stream)
+            barrier()
+            msp = e0.elapsed_time(e1) / k
+            bnd, pk, how = ladder_peak(p)
+            precisions[p] = {"sigma_vectors_per_s": 1e3 / msp, "ms_per_sigma": msp, "ladder_ms": sum(lp) / len(lp),
+                             "whole_sigma_rate_tflops": alg["total_cmac"] * 8 / (msp * 1e-3) / 1e12,
+                             "unit_peak_tflops": pk, "unit": bnd, "peak_source": how, "steps": k}
+        ctx.cc_lr_set_precision(args.prec)
+    ctx.close()
+    del x1, x2, s1, s2
+
     bound, peak, how = ladder_peak(args.prec)
     lad_achieved = alg["ladder_cmac"] * 8 / (lad_ms * 1e-3) / 1e12
     # the dominant kernel: the tensor-core GEMMs that form <ab|ef>~ (CUDA events around each)
@@ -435,41 +609,66 @@ def run_cclr(args):
     if form_ms > 0:
         kernel = "tc_gemm_kernel: pp-ladder formation <ab|ef>~ = sum_P L~_ae L~_bf (all groups of one sigma)"
         achieved = alg["form_cmac"] * 8 / (form_ms * 1e-3) / 1e12
-        ga = ctx.cc_lr_ladder_tuning(args.prec)[0]
-        traffic = FORMATION_BYTES_PER_FLOP * formation_flops_executed(v, naux, ga)
+        if args.prec == "tf32" and tga:
+            traffic = FORMATION_BYTES_PER_FLOP * formation_flops_executed(v, naux, tga)
     else:
         kernel = "pp-ladder (formation + contraction)"
         achieved = lad_achieved
-    ctx.close()
+    ms_step = ms_max / args.steps
+
+    hbm = None
+    if rank == 0 and not args.no_hbm:
+        d, howp = peaks()
+        hbm = {"peak_gbs": d["hbm_gbs"], "peak_source": f"{howp} copy bandwidth", "kernels": {}}
+        for k, (msk, byt) in binding.cc_lr_bench_hbm(o, v, reps=5).items():
+            gbs = byt / (msk * 1e-3) / 1e9
+            hbm["kernels"][k] = {"ms": msk, "algorithmic_gb": byt / 1e9, "achieved_gbs": gbs,
+                                 "frac": gbs / d["hbm_gbs"]}
+    tf32_cublas = cublas_tf32_tflops() if rank == 0 else None
+
     tta = None
     tta_large = None
     if rank == 0 and not args.no_alpha:
         tta = time_to_alpha(args.alpha_config, args.alpha_scale, "tf32" if args.prec in ("tf32", "fp64") else args.prec)
         if not args.no_alpha_large:
             tta_large = time_to_alpha_large(args.alpha_large_config, args.alpha_large_scale)
+    c3 = c5 = None
+    if rank == 0 and not args.no_c3:
+        c3 = packed_batch("C3", 21, ["tf32", "3xtf32"])
+    if rank == 0 and not args.no_c5:
+        c5 = packed_batch("C5", 1, ["tf32", "bf16x3"])
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": {"tf32": "c64-tf32", "3xtf32": "c64-3xtf32", "fp32": "c64", "fp64": "c128"}[args.prec],
+            "dtype": {"tf32": "c64-tf32", "3xtf32": "c64-3xtf32", "bf16x3": "c64-bf16x3", "fp32": "c64",
+                      "fp64": "c128"}[args.prec],
             "data": "synthetic (seeded; T1=0, first-order T2, random X)",
             "config": {"workload": f"{args.config} o={o} v={v} naux={naux} single-RHS sigma",
                        "precision_mode": args.prec, "parallelism": f"replicas x{world}",
-                       "l2": "inputs larger than L2 (X2 c128 %.2f GB, L~vv %.2f GB)" % (x2.numel() * 16 / 1e9, naux * v * v * 16 / 1e9)},
+                       "l2": "inputs larger than L2 (X2 c128 %.2f GB, L~vv %.2f GB)" % (o * o * v * v * 16 / 1e9, naux * v * v * 16 / 1e9)},
             "roofline": {"kernel": kernel, "bound": bound,
                          "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "peak_source": how, "traffic": traffic,
                          "traffic_source": "ncu dram bytes per FLOP of one formation launch, scaled to the "
                                            "FLOP of one sigma's formation launches" if traffic else None,
                          "kernel_ms": form_ms if form_ms > 0 else lad_ms,
-                         "ladder_ms": lad_ms, "ladder_share": lad_ms / (ms_max / args.steps),
-                         "ladder_achieved": lad_achieved, "ladder_frac": lad_achieved / peak},
+                         "ladder_ms": lad_ms, "ladder_share": lad_ms / ms_step,
+                         "ladder_achieved": lad_achieved, "ladder_frac": lad_achieved / peak,
+                         "whole_sigma_achieved": alg["total_cmac"] * 8 / (ms_step * 1e-3) / 1e12,
+                         "whole_sigma_frac": alg["total_cmac"] * 8 / (ms_step * 1e-3) / 1e12 / peak,
+                         "tf32_cublas_measured_tflops": tf32_cublas,
+                         "frac_of_cublas_tf32": achieved / tf32_cublas if tf32_cublas else None},
             "clocks": clk,
             "e2e": {"value": e2e, "unit": "sigma-vectors/s", "h2d_bytes_per_step": bytes_io,
                     "d2h_bytes_per_step": bytes_io},
             "gpu_launches": int(launches),
         }
+        if precisions is not None:
+            out["precisions"] = precisions
+        if hbm is not None:
+            out["hbm_kernels"] = hbm
         if tta is not None:
             out["time_to_alpha"] = tta
         if tta_large is not None:
@@ -478,8 +677,13 @@ def run_cclr(args):
             out["batched"] = batched
         if ablation is not None:
             out["ablation_stored_ladder"] = ablation
+        if c3 is not None:
+            out["c3_batched"] = c3
+        if c5 is not None:
+            out["c5"] = c5
         if cpu is not None:
             out["cpu_baseline"] = cpu
+            out["cpu_c1_whole_sigma"] = cpu_c1
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()

@@ -103,6 +103,14 @@ cclr_status cc_lr_sigma(cclr_ctx *ctx, int nrhs, const double *x1, const double 
 cclr_status cc_lr_sigma_T(cclr_ctx *ctx, int nrhs, const double *y1, const double *y2,
                           double *s1, double *s2);
 
+/* sigma (transpose = 0) or sigma^T (transpose = 1) of nrhs vectors in the packed
+ * unique-amplitude layout the solvers use: each vector is n1 + n2p complex numbers,
+ * singles [o][v] then doubles [(i<j)][(a<b)] (pairs numbered row by row), so a doubles
+ * block is a quarter of the full tensor; the bilinear product of two vectors is the plain
+ * sum over entries.  x and s are device arrays of nrhs vectors each (the batch forms every
+ * <ab||ef>~ block once for all of them); host arrays return CCLR_EINVAL. */
+cclr_status cc_lr_sigma_packed(cclr_ctx *ctx, int nrhs, int transpose, const double *x, double *s);
+
 /* Right-hand side xi^B = <nu|e^{-T} mu^B e^{T}|Phi_0> (Sec. 2.2) for component
  * comp (0 = x, 1 = y, 2 = z). */
 cclr_status cc_lr_xi(cclr_ctx *ctx, int comp, double *xi1, double *xi2);
@@ -130,6 +138,18 @@ cclr_status cc_lr_solve(cclr_ctx *ctx, int nomega, const double *omegas, int nco
 cclr_status cc_lr_solve_left(cclr_ctx *ctx, int nomega, const double *omegas, int ncomp,
                              const int *comps, double tol, int diis_depth, double *alpha,
                              cclr_stats *stats);
+
+/* alpha to an absolute tolerance tol_alpha (a.u.) instead of a residual target: the left-hand
+ * route and the X-only route are evaluated from the same X and F X (dot products only), their
+ * largest difference over the entries is the a-posteriori error estimate written to
+ * *alpha_err, and the solves are tightened, warm-started from the previous solutions, until it
+ * is below tol_alpha.  alpha holds the left-hand route's values.  The ground-state Lambda, which
+ * both routes share, is solved near the arithmetic's residual floor (5e-7 relative with 3xTF32
+ * refinement).  Returns CCLR_ENOCONV (alpha and *alpha_err filled) when the floor is reached
+ * with the estimate still above tol_alpha. */
+cclr_status cc_lr_solve_alpha_tol(cclr_ctx *ctx, int nomega, const double *omegas, int ncomp,
+                                  const int *comps, double tol_alpha, int diis_depth, double *alpha,
+                                  double *alpha_err, cclr_stats *stats);
 
 /* eta^A = <(1 + Lambda)|[A-bar, tau_nu]|Phi_0> (Sec. 2.2) for component comp as a vector:
  * eta1 [o][v], eta2 [o][o][v][v] (full antisymmetric).  Formed as dE_A/dT + lambda A[mu^A], with
@@ -208,6 +228,19 @@ cclr_status cc_lr_set_refinement(cclr_ctx *ctx, int prec);
  * each linear solve (default 300; 0 keeps the current value); a solve that reaches it
  * returns CCLR_ENOCONV with its best iterate. */
 cclr_status cc_lr_set_solver(cclr_ctx *ctx, int method, int subspace, int max_iterations);
+
+/* Tensor-core GEMM tile autotuner (on by default): the first eager use of each GEMM shape
+ * (operand type, M, N, K, output layout) on a device times a handful of launch configurations
+ * -- tile width, K splits, raster band -- around the rules' choice on the real operands (an
+ * accumulated output is tuned into a scratch block) and keeps the fastest for that shape and
+ * device; later products, and other contexts on the device, launch it.  on = 0: untuned shapes
+ * keep the rules. */
+cclr_status cc_lr_set_autotune(cclr_ctx *ctx, int on);
+
+/* The tuned GEMM shapes of the current device: writes *n (the number of shapes) and the first
+ * min(*n, cap) rows of 10 doubles (operand type 0 TF32 / 1 BF16, M, N, K (real elements), tile
+ * width, K splits, raster band, best milliseconds, the rules' milliseconds, candidates timed). */
+cclr_status cc_lr_gemm_tuning(cclr_ctx *ctx, int cap, int *n, double *rec);
 
 /* Device memory held by the context now (*in_use), the most it has held (*peak), and its
  * budget (*budget, 0 = none), in bytes.  Host-side bookkeeping only (no device call). */

@@ -20,8 +20,25 @@ int cc_lr_selftest_gemm(int M, int N, int K, int mode, unsigned seed, double *er
  * GEMM, ms[1] = the corresponding TFLOP/s at 8 real flops per complex multiply-add. */
 int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms);
 
-/* Size in bytes of the fixed device array that cc_lr_selftest_gemm_noalloc works in (32 MiB,
- * one copy per device). */
+/* Times the HBM-bound kernels of the solver and the sigma program at o occupied and v virtual
+ * spinors on device buffers of those sizes (contents: zeros; the time does not depend on them):
+ * reps launches each, CUDA events.  Writes for k = 0..min(n, 8)-1 the pair
+ * (out[2k] = milliseconds per launch, out[2k+1] = algorithmic bytes per launch), in the order
+ *   0 antisym_apply    complex64 S += P(ab) Rab + P(ij) Rij + P(ij)P(ab) R4 (3 reads, S read+write)
+ *   1 antisym_project  complex64 in-place projection of S (read + write)
+ *   2 unpack_doubles   packed complex128 -> full complex64 (packed read, full write)
+ *   3 pack_doubles     full complex64 -> packed complex128 (the i<j, a<b entries read, packed write)
+ *   4 vec_precond      packed complex128 r / (D - w) (r and D read, result written)
+ *   5 vec_dot          packed complex128 Hermitian dot, FP64 accumulation (two reads)
+ *   6 vec_axpy         packed complex128 y += a x (x, y read, y written)
+ *   7 unpack_sig       pp-ladder result scattered to the four antisymmetric images (complex64)
+ * Returns 0 on success, else a cclr_status code. */
+int cc_lr_bench_hbm(int o, int v, int reps, double *out, int n);
+
+/* Size in bytes of the fixed device array that cc_lr_selftest_gemm_noalloc works in (32 MiB).
+ * The array is part of the library's device code: loading the library reserves it on every
+ * device the process uses, whether or not the entry point is ever called, and it is not part
+ * of any context's HBM budget (cc_lr_memory does not count it). */
 #define CCLR_SELFTEST_NOALLOC_SCRATCH_BYTES 33554432ull
 
 /* cc_lr_selftest_gemm without any device allocation.  The paper has no counterpart: this

@@ -92,6 +92,8 @@ class EntrySigma:
         return self.Woooo[:, :, i, j]
 
     def Wovvo_bj(self, b, j):      # Wovvo[m, b, e, j] over (m, e)
+        if getattr(self, "_wovvo", None) is not None:      # the whole block, when formed
+            return self._wovvo[:, b, :, j]
         w = ein("Pme,P->me", self.Lov, self.Lvo[:, b, j]) - ein("Pm,Pe->me", self.Loo[:, :, j], self.Lvv[:, b, :])
         return w - (self.oovv_me @ self.t2[j, :, :, b].reshape(-1)).reshape(self.no, self.nv)
 
@@ -186,6 +188,8 @@ class EntrySigma:
         """Wovoo[m, b, i, j] for every (b, i, j) (the terms of Wovoo_bij); the <mb|ef>~ t_ij^ef
         part is formed in chunks of b from L~ (no tensor with three virtual indices is held
         whole)."""
+        if getattr(self, "_wovoo", None) is not None:
+            return self._wovoo
         t2 = self.t2
         w = (ein("Pmi,Pbj->mbij", self.Loo, self.Lvo) - ein("Pmj,Pbi->mbij", self.Loo, self.Lvo)
              - ein("me,ijbe->mbij", self.fov, t2)
@@ -194,6 +198,7 @@ class EntrySigma:
             b1 = min(self.nv, b0 + b_chunk)
             G = ein("Pme,Pbf->mbef", self.Lov, self.Lvv[:, b0:b1])    # <mb|ef>~ for the chunk
             w[:, b0:b1] += ein("mbef,ijef->mbij", G, t2)
+        self._wovoo = w
         return w
 
     def wx_all(self):

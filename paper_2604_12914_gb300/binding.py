@@ -21,11 +21,11 @@ CCLR_FP64, CCLR_C64_TF32, CCLR_C64_3XTF32, CCLR_C64_FP32, CCLR_BF16X3 = range(5)
 PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp32": CCLR_C64_FP32,
         "bf16x3": CCLR_BF16X3}
 
-EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
-           "cc_lr_solve_damped", "cc_lr_solve_left", "cc_lr_eta",
+EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_sigma_packed", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
+           "cc_lr_solve_damped", "cc_lr_solve_left", "cc_lr_solve_alpha_tol", "cc_lr_eta",
            "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
            "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_ladder_storage", "cc_lr_set_solver",
-           "cc_lr_last_timings", "cc_lr_memory",
+           "cc_lr_last_timings", "cc_lr_memory", "cc_lr_set_autotune", "cc_lr_gemm_tuning",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
 
 
@@ -61,12 +61,14 @@ def load(path: str = LIB_PATH):
         "cc_lr_init": [ctypes.POINTER(ctypes.c_void_p), I, I, I, P, P, P, P, P, P, P, I, S, I, P],
         "cc_lr_sigma": [P, I, P, P, P, P],
         "cc_lr_sigma_T": [P, I, P, P, P, P],
+        "cc_lr_sigma_packed": [P, I, I, P, P],
         "cc_lr_xi": [P, I, P, P],
         "cc_lr_solve_x": [P, D, I, D, I, P, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve_damped": [P, I, P, D, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_solve_left": [P, I, P, I, P, D, I, P, ctypes.POINTER(cclr_stats)],
         "cc_lr_eta": [P, I, D, P, P],
+        "cc_lr_solve_alpha_tol": [P, I, P, I, P, D, I, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(cclr_stats)],
         "cc_lr_lambda": [P, D, P, P],
         "cc_lr_get_t": [P, P, P],
         "cc_lr_set_precision": [P, I],
@@ -78,6 +80,8 @@ def load(path: str = LIB_PATH):
         "cc_lr_ladder_tuning": [P, I, ctypes.POINTER(ctypes.c_int), I, P, P, ctypes.POINTER(ctypes.c_int)],
         "cc_lr_last_timings": [P, P, I],
         "cc_lr_memory": [P, ctypes.POINTER(S), ctypes.POINTER(S), ctypes.POINTER(S)],
+        "cc_lr_set_autotune": [P, I],
+        "cc_lr_gemm_tuning": [P, I, ctypes.POINTER(ctypes.c_int), P],
         "cc_lr_free": [P],
         "cc_lr_strerror": [I],
         "cc_lr_last_error": [],
@@ -85,6 +89,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_selftest_gemm": [I, I, I, I, ctypes.c_uint, P],
         "cc_lr_selftest_gemm_noalloc": [I, I, I, I, ctypes.c_uint, P],
         "cc_lr_bench_gemm": [I, I, I, I, I, P],
+        "cc_lr_bench_hbm": [I, I, I, P, I],
         "cc_lr_selftest_timeout": [I, ctypes.POINTER(ctypes.c_int)],
     }
     for name, args in sig.items():
@@ -186,6 +191,15 @@ class Context:
         fn = load().cc_lr_sigma_T if transpose else load().cc_lr_sigma
         _check(fn(self._h, nrhs, _ptr(x1), _ptr(x2), _ptr(s1), _ptr(s2)))
 
+    def n_packed(self):
+        """Length of one packed unique-amplitude vector: o v + o(o-1)/2 v(v-1)/2."""
+        o, v = self.o, self.v
+        return o * v + (o * (o - 1) // 2) * (v * (v - 1) // 2)
+
+    def sigma_packed(self, x, s, nrhs=1, transpose=False):
+        """sigma (or sigma^T) of nrhs packed vectors, device arrays [nrhs][n_packed] complex128."""
+        _check(load().cc_lr_sigma_packed(self._h, nrhs, 1 if transpose else 0, _ptr(x), _ptr(s)))
+
     def cc_lr_sigma_T(self, y1, y2):
         return self.cc_lr_sigma(y1, y2, transpose=True)
 
@@ -235,6 +249,21 @@ class Context:
         d = st.as_dict()
         d["status"] = status
         return out, d
+
+    def cc_lr_solve_alpha_tol(self, omegas, comps=(0, 1, 2), tol_alpha=1e-5, diis_depth=8, allow_noconv=False):
+        """(alpha[w][a][b], a-posteriori |delta alpha| estimate, stats): solves tightened until the
+        left- and right-route alphas agree within tol_alpha (a.u.)."""
+        om = np.ascontiguousarray(omegas, dtype=np.float64)
+        cp = np.ascontiguousarray(comps, dtype=np.int32)
+        out = np.zeros((len(om), len(cp), len(cp)), dtype=np.complex128)
+        err = ctypes.c_double(0.0)
+        st = cclr_stats()
+        status = _check(load().cc_lr_solve_alpha_tol(self._h, len(om), _ptr(om), len(cp), _ptr(cp), float(tol_alpha),
+                                                     diis_depth, _ptr(out), ctypes.byref(err), ctypes.byref(st)),
+                        allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        d = st.as_dict()
+        d["status"] = status
+        return out, err.value, d
 
     def cc_lr_eta(self, comp, tol=1e-10):
         o, v = self.o, self.v
@@ -292,6 +321,17 @@ class Context:
         m = {"gmres": 1, "diis": 0, "block": 2}[method] if isinstance(method, str) else int(method)
         _check(load().cc_lr_set_solver(self._h, m, int(subspace), int(max_iterations)))
 
+    def cc_lr_set_autotune(self, on=True):
+        _check(load().cc_lr_set_autotune(self._h, 1 if on else 0))
+
+    def cc_lr_gemm_tuning(self, cap=256):
+        """List of dicts: the tuned GEMM shapes of this device and their chosen configuration."""
+        n = ctypes.c_int(0)
+        rec = np.zeros((cap, 10), dtype=np.float64)
+        _check(load().cc_lr_gemm_tuning(self._h, cap, ctypes.byref(n), _ptr(rec)))
+        keys = ["kind", "M", "N", "K", "BN", "splits", "band", "ms_best", "ms_rule", "tried"]
+        return [dict(zip(keys, map(float, rec[k]))) for k in range(min(n.value, cap))]
+
     def cc_lr_memory(self):
         """(bytes held, peak bytes held, budget) of this context's device memory."""
         a, b, c = ctypes.c_size_t(0), ctypes.c_size_t(0), ctypes.c_size_t(0)
@@ -324,6 +364,17 @@ def cc_lr_bench_gemm(M, N, K, mode, reps=5):
     out = np.zeros(2, dtype=np.float64)
     _check(load().cc_lr_bench_gemm(M, N, K, mode, reps, _ptr(out)))
     return float(out[0]), float(out[1])
+
+
+HBM_KERNELS = ["antisym_apply", "antisym_project", "unpack_doubles", "pack_doubles", "vec_precond", "vec_dot",
+               "vec_axpy", "unpack_sig"]
+
+
+def cc_lr_bench_hbm(o, v, reps=5):
+    """{kernel: (ms per launch, algorithmic bytes per launch)} of the HBM-bound kernels at o, v."""
+    out = np.zeros(16, dtype=np.float64)
+    _check(load().cc_lr_bench_hbm(o, v, reps, _ptr(out), 8))
+    return {k: (float(out[2 * i]), float(out[2 * i + 1])) for i, k in enumerate(HBM_KERNELS)}
 
 
 def cc_lr_selftest_timeout(timeout_us=1000):

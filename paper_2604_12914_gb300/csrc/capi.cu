@@ -167,9 +167,10 @@ struct cclr_ctx {
   // normed and applied in FP64; each correction (Op - omega) d = r is solved by DIIS with
   // the tensor-core sigma (TF32: two digits per correction, 3xTF32: five).
   int refinements = 0;
+  // warm: x holds a start vector (its residual is formed first) instead of zero
   double solve(int dir, zd omega, const void *b, void *x, double tol, int depth, int maxit,
-               int *its) {
-    if (M->prec == CCLR_FP64) return solve_diis(dir, omega, b, x, tol, depth, maxit, its);
+               int *its, bool warm = false) {
+    if (M->prec == CCLR_FP64) return solve_diis(dir, omega, b, x, tol, depth, maxit, its, warm);
     const int lo = M->prec;
     const double inner_tol = lo == CCLR_C64_TF32 ? 1e-2 : 1e-5;
     // each correction gets a bounded number of DIIS steps: near its precision floor the
@@ -181,13 +182,13 @@ struct cclr_ctx {
     alloc_vec(d);
     alloc_vec(xb);
     const double bn = std::max(norm(b), 1e-300);
-    CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
+    if (!warm) CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
     copy(b, r.b.p);
     double rel = 1.0, rel_prev = 1e300;
     int used = 0;
     bool stalled = false;
     for (int outer = 0; outer < 40 && used < maxit; ++outer) {
-      if (outer > 0) {
+      if (outer > 0 || warm) {
         M->prec = hi_prec;
         op(dir, x, s.b.p);
         M->prec = lo;
@@ -510,11 +511,11 @@ struct cclr_ctx {
   // residuals (accurate precision) and corrections (working precision) are both batched.
   void solve_block(int dir, const std::vector<zd> &om, const std::vector<const void *> &b,
                    const std::vector<void *> &x, double tol, int maxit, std::vector<int> &its,
-                   std::vector<double> &rel) {
+                   std::vector<double> &rel, bool warm = false) {
     const int nr = (int)b.size();
     const int m = block_restart(nr);
     if (M->prec == CCLR_FP64) {
-      gmres_block(dir, om, b, x, std::vector<double>(nr, tol), m, maxit, its, rel, false);
+      gmres_block(dir, om, b, x, std::vector<double>(nr, tol), m, maxit, its, rel, warm);
       return;
     }
     const int lo = M->prec;
@@ -528,7 +529,7 @@ struct cclr_ctx {
     for (int r = 0; r < nr; ++r) {
       alloc_vec(sv[r]); alloc_vec(rv[r]); alloc_vec(dv[r]); alloc_vec(xb[r]);
       bn[r] = std::max(norm(b[r]), 1e-300);
-      CCLR_CUDA(cudaMemsetAsync(x[r], 0, (size_t)ntot() * 16, st));
+      if (!warm) CCLR_CUDA(cudaMemsetAsync(x[r], 0, (size_t)ntot() * 16, st));
       copy(b[r], rv[r].b.p);
     }
     for (int outer = 0; outer < 40; ++outer) {
@@ -536,7 +537,7 @@ struct cclr_ctx {
       for (int r = 0; r < nr; ++r)
         if (state[r] == 0) act.push_back(r);
       if (act.empty()) break;
-      if (outer > 0) {
+      if (outer > 0 || warm) {
         std::vector<const void *> in;
         std::vector<void *> out;
         for (int r : act) { in.push_back(x[r]); out.push_back(sv[r].b.p); }
@@ -992,6 +993,30 @@ cclr_status cc_lr_sigma_T(cclr_ctx *c, int nrhs, const double *y1, const double 
   return sigma_common(c, -1, nrhs, y1, y2, s1, s2);
 }
 
+cclr_status cc_lr_sigma_packed(cclr_ctx *c, int nrhs, int transpose, const double *x, double *s) {
+  if (!c || nrhs < 0 || (transpose != 0 && transpose != 1) || (nrhs > 0 && (!x || !s)))
+    return (cclr_status)fail(CCLR_EINVAL, "bad sigma_packed arguments");
+  return (cclr_status)guarded_ctx(c, [&] {
+    const int64_t n = c->ntot();
+    std::vector<const void *> xs(nrhs);
+    std::vector<void *> ss(nrhs);
+    for (int r = 0; r < nrhs; ++r) {
+      xs[r] = x + (size_t)r * n * 2;
+      ss[r] = s + (size_t)r * n * 2;
+    }
+    // all right-hand sides in one batched product (device pointers of the current device; host
+    // arrays are refused: the packed entry point stages nothing)
+    for (int r = 0; r < nrhs; ++r) {
+      cudaPointerAttributes a{};
+      CCLR_CUDA(cudaPointerGetAttributes(&a, xs[r]));
+      CCLR_REQUIRE(a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged,
+                   "cc_lr_sigma_packed needs device arrays");
+    }
+    if (nrhs > 0) c->op_batch(transpose ? -1 : +1, nrhs, xs.data(), ss.data());
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+  });
+}
+
 cclr_status cc_lr_xi(cclr_ctx *c, int comp, double *xi1, double *xi2) {
   if (!c || comp < 0 || comp > 2 || !xi1 || !xi2) return (cclr_status)fail(CCLR_EINVAL, "bad xi arguments");
   return (cclr_status)guarded_ctx(c, [&] {
@@ -1164,11 +1189,12 @@ static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, do
 
 // Right (X) solves of every component at the shifts in sh, in one block or one by one.
 static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const std::vector<const void *> &bs,
-                        const std::vector<void *> &xs, double tol, int diis_depth, cclr_stats &loc) {
+                        const std::vector<void *> &xs, double tol, int diis_depth, cclr_stats &loc,
+                        bool warm = false) {
   if (c->method == 2) {
     std::vector<int> its;
     std::vector<double> rels;
-    c->solve_block(dir, sh, bs, xs, tol, c->maxit, its, rels);
+    c->solve_block(dir, sh, bs, xs, tol, c->maxit, its, rels, warm);
     for (size_t k = 0; k < its.size(); ++k) {
       loc.iterations += its[k];
       loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
@@ -1178,7 +1204,7 @@ static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const s
   }
   for (size_t k = 0; k < bs.size(); ++k) {
     int its = 0;
-    const double rel = c->solve(dir, sh[k], bs[k], xs[k], tol, diis_depth, c->maxit, &its);
+    const double rel = c->solve(dir, sh[k], bs[k], xs[k], tol, diis_depth, c->maxit, &its, warm);
     loc.iterations += its;
     loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
     if (!(rel < tol)) loc.converged = 0;
@@ -1187,9 +1213,15 @@ static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const s
 
 // alpha by the left-hand route (Sec. 2.2): X^B(w) from (A - w) X = -xi^B, Y^B(w) from
 // Y (A + w) = -(eta^B + F X^B(w)), and g(A,B;w) = Y^B(w) . xi^A + eta^A . X^B(w);
-// <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)], alpha = -<<A;B>>.
+// <<A;B>>_w = 1/2 [g(A,B;w) + conj g(A,B;-w)], alpha = -<<A;B>>.  The same X and F X give the
+// X-only route g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w) with dot products
+// only; both routes converge to one alpha, so their largest difference is an a-posteriori
+// estimate of the error (*est).  tol_alpha > 0: the solves are tightened (warm-started from the
+// previous solutions) until that estimate is below tol_alpha or the residual target reaches
+// tol_floor.
 static cclr_status solve_alpha_left(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
-                                    double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+                                    double tol, int diis_depth, double *alpha, cclr_stats *stats,
+                                    double tol_alpha = 0.0, double *est = nullptr) {
   if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0))
     return (cclr_status)fail(CCLR_EINVAL, "bad solve_left arguments");
   for (int k = 0; k < ncomp; ++k)
@@ -1197,9 +1229,15 @@ static cclr_status solve_alpha_left(cclr_ctx *c, int nomega, const double *omega
   cclr_stats loc;
   std::memset(&loc, 0, sizeof(loc));
   loc.converged = 1;
+  double est_all = 0.0;
+  bool alpha_met = true;
   int st = guarded_ctx(c, [&] {
     const int calls0 = c->sigma_calls;
-    c->ensure_lambda(tol, diis_depth, &loc);
+    // residual floor of the arithmetic: FP64, or the accurate products of the mixed modes
+    const double tol_floor = c->M->prec == CCLR_FP64 || c->hi_prec == CCLR_FP64 ? 1e-12 : 8e-7;
+    // Lambda enters both routes alike (the estimate does not see its error): with a tol_alpha
+    // target it is solved near the floor
+    c->ensure_lambda(tol_alpha > 0.0 ? std::max(1.5 * tol_floor, 1e-10) : tol, diis_depth, &loc);
     std::vector<AVec> XI(ncomp), RB(ncomp);
     for (int a = 0; a < ncomp; ++a) {
       c->alloc_vec(XI[a]);
@@ -1213,67 +1251,107 @@ static cclr_status solve_alpha_left(cclr_ctx *c, int nomega, const double *omega
       if (omegas[w] != 0.0) shifts.push_back(zd(-omegas[w]));
       const int ns = (int)shifts.size();
       auto slot = [&](int k) { return (k == 1 && ns == 2) ? 1 : 0; };  // k = 0: +w, 1: -w
-      std::vector<AVec> X((size_t)ncomp * ns), Y((size_t)ncomp * ns);
-      auto t0 = std::chrono::steady_clock::now();
-      std::vector<zd> sh;
-      std::vector<const void *> bs;
-      std::vector<void *> xs;
-      for (int b = 0; b < ncomp; ++b)
-        for (int q = 0; q < ns; ++q) {
-          c->alloc_vec(X[(size_t)b * ns + q]);
-          sh.push_back(shifts[q]);
-          bs.push_back(RB[b].b.p);
-          xs.push_back(X[(size_t)b * ns + q].b.p);
+      std::vector<AVec> X((size_t)ncomp * ns), Y((size_t)ncomp * ns), LB((size_t)ncomp * ns), FXv((size_t)ncomp * ns);
+      double tw = tol;
+      bool warm = false;
+      for (int level = 0;; ++level) {
+        auto t0 = std::chrono::steady_clock::now();
+        std::vector<zd> sh;
+        std::vector<const void *> bs;
+        std::vector<void *> xs;
+        for (int b = 0; b < ncomp; ++b)
+          for (int q = 0; q < ns; ++q) {
+            c->alloc_vec(X[(size_t)b * ns + q]);
+            sh.push_back(shifts[q]);
+            bs.push_back(RB[b].b.p);
+            xs.push_back(X[(size_t)b * ns + q].b.p);
+          }
+        cclr_stats lvl;
+        std::memset(&lvl, 0, sizeof(lvl));
+        lvl.converged = 1;
+        solve_right(c, +1, sh, bs, xs, tw, diis_depth, lvl, warm);
+        auto t1 = std::chrono::steady_clock::now();
+        // F X^B(s), and the left right-hand sides -(eta^B + F X^B(s)); Y^B(s) with the shift -s
+        std::vector<zd> lsh;
+        std::vector<const void *> lbs;
+        std::vector<void *> ys;
+        for (int b = 0; b < ncomp; ++b)
+          for (int q = 0; q < ns; ++q) {
+            const size_t id = (size_t)b * ns + q;
+            c->alloc_vec(FXv[id]);
+            c->fx(X[id].b.p, FXv[id].b.p);
+            c->alloc_vec(LB[id]);
+            c->copy(FXv[id].b.p, LB[id].b.p);
+            c->axpy(zd(1), c->eta_vec(comps[b]), LB[id].b.p);
+            c->scal(zd(-1), LB[id].b.p);
+            c->alloc_vec(Y[id]);
+            lsh.push_back(-shifts[q]);
+            lbs.push_back(LB[id].b.p);
+            ys.push_back(Y[id].b.p);
+          }
+        auto t2 = std::chrono::steady_clock::now();
+        solve_right(c, -1, lsh, lbs, ys, tw, diis_depth, lvl, warm);
+        auto t3 = std::chrono::steady_clock::now();
+        double e = 0.0;
+        for (int a = 0; a < ncomp; ++a)
+          for (int b = 0; b < ncomp; ++b) {
+            // k = 0: +w, 1: -w
+            auto gL = [&](int k) {
+              const size_t id = (size_t)b * ns + slot(k);
+              return c->dot(Y[id].b.p, XI[a].b.p, 0) + c->eta_dot(comps[a], X[id].b.p);
+            };
+            auto gR = [&](int k) {
+              const size_t xb = (size_t)b * ns + slot(k), xa = (size_t)a * ns + slot(1 - k);
+              return c->eta_dot(comps[a], X[xb].b.p) + c->eta_dot(comps[b], X[xa].b.p) +
+                     c->dot(FXv[xa].b.p, X[xb].b.p, 0);
+            };
+            const zd al = -0.5 * (gL(0) + std::conj(gL(1)));
+            const zd ar = -0.5 * (gR(0) + std::conj(gR(1)));
+            e = std::max(e, std::abs(al - ar));
+            const size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
+            alpha[k] = al.real();
+            alpha[k + 1] = al.imag();
+          }
+        auto t4 = std::chrono::steady_clock::now();
+        loc.iterations += lvl.iterations;
+        loc.time_solve_ms += std::chrono::duration<double, std::milli>((t1 - t0) + (t3 - t2)).count();
+        loc.time_alpha_ms += std::chrono::duration<double, std::milli>((t2 - t1) + (t4 - t3)).count();
+        if (cclr_ctx::verbose()) std::fprintf(stderr, "cclr alpha level %d tol %.2e estimate %.3e\n", level, tw, e);
+        const bool last = tol_alpha <= 0.0 || e < tol_alpha || tw <= tol_floor || level >= 8;
+        if (last) {
+          loc.max_rel_residual = std::max(loc.max_rel_residual, lvl.max_rel_residual);
+          if (!lvl.converged) loc.converged = 0;
+          est_all = std::max(est_all, e);
+          if (tol_alpha > 0.0 && !(e < tol_alpha)) alpha_met = false;
+          break;
         }
-      solve_right(c, +1, sh, bs, xs, tol, diis_depth, loc);
-      auto t1 = std::chrono::steady_clock::now();
-      // left right-hand sides -(eta^B + F X^B(s)), then Y^B(s) with the shift -s
-      std::vector<AVec> LB((size_t)ncomp * ns);
-      std::vector<zd> lsh;
-      std::vector<const void *> lbs;
-      std::vector<void *> ys;
-      for (int b = 0; b < ncomp; ++b)
-        for (int q = 0; q < ns; ++q) {
-          AVec &r = LB[(size_t)b * ns + q];
-          c->alloc_vec(r);
-          c->fx(X[(size_t)b * ns + q].b.p, r.b.p);
-          c->axpy(zd(1), c->eta_vec(comps[b]), r.b.p);
-          c->scal(zd(-1), r.b.p);
-          c->alloc_vec(Y[(size_t)b * ns + q]);
-          lsh.push_back(-shifts[q]);
-          lbs.push_back(r.b.p);
-          ys.push_back(Y[(size_t)b * ns + q].b.p);
-        }
-      auto t2 = std::chrono::steady_clock::now();
-      solve_right(c, -1, lsh, lbs, ys, tol, diis_depth, loc);
-      auto t3 = std::chrono::steady_clock::now();
-      for (int a = 0; a < ncomp; ++a)
-        for (int b = 0; b < ncomp; ++b) {
-          auto g = [&](int k) {
-            const size_t id = (size_t)b * ns + slot(k);
-            return c->dot(Y[id].b.p, XI[a].b.p, 0) + c->eta_dot(comps[a], X[id].b.p);
-          };
-          const zd al = -0.5 * (g(0) + std::conj(g(1)));
-          const size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
-          alpha[k] = al.real();
-          alpha[k + 1] = al.imag();
-        }
-      auto t4 = std::chrono::steady_clock::now();
-      loc.time_solve_ms += std::chrono::duration<double, std::milli>((t1 - t0) + (t3 - t2)).count();
-      loc.time_alpha_ms += std::chrono::duration<double, std::milli>((t2 - t1) + (t4 - t3)).count();
+        // tighten by the estimate's distance from the target (first-order error in the residual)
+        tw = std::max(tol_floor, tw * std::min(0.3, std::max(0.01, 0.3 * tol_alpha / e)));
+        warm = true;
+      }
     }
     loc.sigma_calls = c->sigma_calls - calls0;
     loc.refinements = c->refinements;
     c->release_scratch();
   });
   if (stats) *stats = loc;
+  if (est) *est = est_all;
   if (st != CCLR_OK) return (cclr_status)st;
-  return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve_left: tolerance not met");
+  if (!alpha_met) return (cclr_status)fail(CCLR_ENOCONV, "solve_alpha_tol: estimate " + std::to_string(est_all) + " above tol_alpha");
+  return loc.converged || tol_alpha > 0.0 ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve_left: tolerance not met");
 }
 
 cclr_status cc_lr_solve_left(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
                              double tol, int diis_depth, double *alpha, cclr_stats *stats) {
   return solve_alpha_left(c, nomega, omegas, ncomp, comps, tol, diis_depth, alpha, stats);
+}
+
+cclr_status cc_lr_solve_alpha_tol(cclr_ctx *c, int nomega, const double *omegas, int ncomp, const int *comps,
+                                  double tol_alpha, int diis_depth, double *alpha, double *alpha_err,
+                                  cclr_stats *stats) {
+  if (!(tol_alpha > 0) || !alpha_err) return (cclr_status)fail(CCLR_EINVAL, "tol_alpha must be > 0 and alpha_err given");
+  // the first residual target: loose (the estimate drives it down from there)
+  return solve_alpha_left(c, nomega, omegas, ncomp, comps, 1e-4, diis_depth, alpha, stats, tol_alpha, alpha_err);
 }
 
 cclr_status cc_lr_eta(cclr_ctx *c, int comp, double tol, double *eta1, double *eta2) {
@@ -1385,6 +1463,17 @@ cclr_status cc_lr_set_solver(cclr_ctx *c, int method, int subspace, int max_iter
   return CCLR_OK;
 }
 
+cclr_status cc_lr_set_autotune(cclr_ctx *c, int on) {
+  if (!c || (on != 0 && on != 1)) return (cclr_status)fail(CCLR_EINVAL, "autotune must be 0 or 1");
+  c->M->autotune = on != 0;
+  return CCLR_OK;
+}
+
+cclr_status cc_lr_gemm_tuning(cclr_ctx *c, int cap, int *n, double *rec) {
+  if (!c || !n || cap < 0 || (cap > 0 && !rec)) return (cclr_status)fail(CCLR_EINVAL, "bad gemm_tuning arguments");
+  return (cclr_status)guarded_ctx(c, [&] { *n = tc_tuning_table(cap, rec); });
+}
+
 cclr_status cc_lr_memory(cclr_ctx *c, size_t *in_use, size_t *peak, size_t *budget) {
   if (!c || !in_use || !peak || !budget) return (cclr_status)fail(CCLR_EINVAL, "bad memory arguments");
   *in_use = c->acct.used;
@@ -1463,6 +1552,54 @@ int cc_lr_bench_gemm(int M, int N, int K, int mode, int reps, double *ms) {
     ms[0] = t / reps;
     ms[1] = 8.0 * M * (double)N * K / (ms[0] * 1e-3) / 1e12;
     if (tc_error(st)) throw Error(CCLR_ETIMEOUT, "tensor-core kernel gave up on a bounded wait");
+    CCLR_CUDA(cudaEventDestroy(e0));
+    CCLR_CUDA(cudaEventDestroy(e1));
+    CCLR_CUDA(cudaStreamDestroy(st));
+  });
+}
+
+int cc_lr_bench_hbm(int o, int v, int reps, double *out, int n) {
+  if (o < 2 || v < 2 || reps < 1 || !out || n < 0) return fail(CCLR_EINVAL, "bad bench_hbm arguments");
+  return guarded([&] {
+    cudaStream_t st;
+    CCLR_CUDA(cudaStreamCreate(&st));
+    const int64_t nf = (int64_t)o * o * v * v, n1 = (int64_t)o * v;
+    const int64_t np = (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2), nt = n1 + np;
+    DevBuf S((size_t)nf * 8), R1((size_t)nf * 8), R2((size_t)nf * 8), R3((size_t)nf * 8);
+    DevBuf P((size_t)nt * 16), Q((size_t)nt * 16), D((size_t)nt * 8), dots(sizeof(double2) * 576);
+    for (DevBuf *b : {&S, &R1, &R2, &R3, &P, &Q, &D, &dots}) CCLR_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st));
+    double2 *part = dots.as<double2>(), *res = part + 512;
+    cudaEvent_t e0, e1;
+    CCLR_CUDA(cudaEventCreate(&e0));
+    CCLR_CUDA(cudaEventCreate(&e1));
+    auto timeit = [&](auto &&fn) {
+      fn();
+      CCLR_CUDA(cudaEventRecord(e0, st));
+      for (int r = 0; r < reps; ++r) fn();
+      CCLR_CUDA(cudaEventRecord(e1, st));
+      CCLR_CUDA(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CCLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+      return (double)ms / reps;
+    };
+    double res_[16];
+    res_[0] = timeit([&] { antisym_apply(C64, o, v, +1, S.p, R1.p, R2.p, R3.p, st); });
+    res_[1] = 5.0 * nf * 8;
+    res_[2] = timeit([&] { antisym_project(C64, o, v, S.p, st); });
+    res_[3] = 2.0 * nf * 8;
+    res_[4] = timeit([&] { unpack_doubles(C128, C64, o, v, P.p, S.p, zc(1), false, st); });
+    res_[5] = 16.0 * np + 8.0 * nf;
+    res_[6] = timeit([&] { pack_doubles(C64, C128, o, v, S.p, P.p, st); });
+    res_[7] = 8.0 * np + 16.0 * np;
+    res_[8] = timeit([&] { vec_precond(C128, nt, D.as<double>(), 0.0, 0.0, P.p, Q.p, st); });
+    res_[9] = 40.0 * nt;
+    res_[10] = timeit([&] { vec_dot(C128, nt, P.p, Q.p, 1, part, res, 0, st); });
+    res_[11] = 32.0 * nt;
+    res_[12] = timeit([&] { vec_axpy(C128, nt, zc(0.5), P.p, Q.p, st); });
+    res_[13] = 48.0 * nt;
+    res_[14] = timeit([&] { ladder_unpack_sig_bench(o, v, R1.p, S.p, st); });
+    res_[15] = 8.0 * np + 4 * 2 * 8.0 * np;
+    for (int k = 0; k < 2 * std::min(n, 8); ++k) out[k] = res_[k];
     CCLR_CUDA(cudaEventDestroy(e0));
     CCLR_CUDA(cudaEventDestroy(e1));
     CCLR_CUDA(cudaStreamDestroy(st));

@@ -122,6 +122,25 @@ int64_t pair_start(int v, int a) { return (int64_t)a * v - (int64_t)a * (a + 1) 
 
 }  // namespace
 
+void ladder_unpack_sig_bench(int o, int v, const void *S, void *out, cudaStream_t st) {
+  static thread_local DevBuf opairs, vpairs;
+  static thread_local int po = -1, pv = -1;
+  const int64_t Po = (int64_t)o * (o - 1) / 2, Pv = (int64_t)v * (v - 1) / 2;
+  if (po != o || pv != v) {
+    auto op = pairs(o), vp = pairs(v);
+    opairs.alloc(op.size() * sizeof(int2));
+    vpairs.alloc(vp.size() * sizeof(int2));
+    CCLR_CUDA(cudaMemcpy(opairs.p, op.data(), op.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    CCLR_CUDA(cudaMemcpy(vpairs.p, vp.data(), vp.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    po = o;
+    pv = v;
+  }
+  unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>((const float2 *)S, Po, o, v, opairs.as<int2>(), vpairs.as<int2>(), Po, Pv,
+                                               1.f, 0.f, (float2 *)out);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
 void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind) {
   cudaStream_t st = E.st;
   wall_ready_ = false;  // a stored block belongs to the previous L~_vv

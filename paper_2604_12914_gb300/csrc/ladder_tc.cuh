@@ -12,6 +12,11 @@
 
 namespace cclr {
 
+// Times nothing itself: runs the ladder's result scatter (unpack_sig) once on a packed result S
+// [(a<b)][(i<j)] (complex64) into out [o][o][v][v] (complex64), with its own pair tables (for the
+// HBM kernel benchmark).
+void ladder_unpack_sig_bench(int o, int v, const void *S, void *out, cudaStream_t st);
+
 class LadderTC {
  public:
   LadderTC() = default;

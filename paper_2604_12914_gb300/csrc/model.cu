@@ -10,6 +10,9 @@
 //                               + P(ij) <mn||ie>~ t_jn^be,
 // and the vvvv / vovv / vvvo elements are never stored: they enter sigma through L~_vv
 // (the "higher-rank integrals evaluated on the fly" of Sec. 3).
+#include <cstdio>
+#include <cstdlib>
+
 #include "model.cuh"
 #include "tc_gemm.cuh"
 
@@ -335,11 +338,18 @@ void Model::release_fp64() {
   lcc.release();
 }
 
-// The working intermediates are built in FP64; the complex64 modes read a rounded copy.
+// The FP64 mode reads intermediates built in FP64.  The complex64 modes read the rounding of
+// those when they exist, else a set built in FP32 on the CUDA cores (this GPU's FP64 rate makes
+// the FP64 build of the o^3 v^3 and o v^3 naux terms take minutes at o=56, v=480).
 const CstSet &Model::cst_for(int p) {
-  if (!c128.valid) build_set(t1.p, t2.p, c128, C128);
-  if (p == 0) return c128;
-  if (!c64.valid) round_set(c128, c64);
+  if (p == 0) {
+    if (!c128.valid) build_set(t1.p, t2.p, c128, C128);
+    return c128;
+  }
+  if (!c64.valid) {
+    if (c128.valid) round_set(c128, c64);
+    else build_set(t1.p, t2.p, c64, C64);
+  }
   return c64;
 }
 
@@ -465,9 +475,18 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
       E.zero(V(r, 3));
     }
     if (lad) run_ladder(+1, lad->alpha, lad->in, lad->out);
+    // CCLR_OPTIME=1 prints the device time of every operation of the first RHS (diagnostics)
+    static const bool optime = std::getenv("CCLR_OPTIME") && std::getenv("CCLR_OPTIME")[0] == '1';
+    cudaEvent_t oe0 = nullptr, oe1 = nullptr;
+    if (optime && timed) {
+      CCLR_CUDA(cudaEventCreate(&oe0));
+      CCLR_CUDA(cudaEventCreate(&oe1));
+    }
     for (int r = 0; r < nr; ++r)
-      for (const Op &op : prog.ops) {
+      for (size_t oi = 0; oi < prog.ops.size(); ++oi) {
+        const Op &op = prog.ops[oi];
         if (op.kind == OP_LADDER || (op.kind == OP_CONTRACT && C.zero[op.cst])) continue;
+        if (oe0 && r == 0) CCLR_CUDA(cudaEventRecord(oe0, st));
         switch (op.kind) {
           case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.in), op.mi, V(r, op.out), op.mo); break;
           case OP_PERM: E.permute(op.alpha, V(r, op.in), op.mi, V(r, op.out), op.mo, true); break;
@@ -478,7 +497,19 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
           case OP_PROJECT: antisym_project(dt, o, v, ptr[r][op.out], st); break;
           default: break;
         }
+        if (oe0 && r == 0) {
+          CCLR_CUDA(cudaEventRecord(oe1, st));
+          CCLR_CUDA(cudaEventSynchronize(oe1));
+          float ms = 0.f;
+          CCLR_CUDA(cudaEventElapsedTime(&ms, oe0, oe1));
+          std::fprintf(stderr, "cclr op %zu kind %d cst %d %s,%s->%s dt %d tc %d: %.3f ms\n", oi, (int)op.kind, op.cst,
+                       op.mc.c_str(), op.mi.c_str(), op.mo.c_str(), dt, E.tc_mode, ms);
+        }
       }
+    if (oe0) {
+      cudaEventDestroy(oe0);
+      cudaEventDestroy(oe1);
+    }
   } else {
     // bars: s1-bar = y1 (the x1 argument), s2-bar = y2 / 4 (unique-amplitude weight), held in
     // the s2 output until the end; x1-bar accumulates in the s1 output and x2-bar in a per-RHS
@@ -616,8 +647,15 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
     }
   }
   float lad_ms = 0.f, form_ms = 0.f;
-  CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
-  apply_body(dir, C, nr, x1, x2, s1, s2, true, lad_ms, form_ms);
+  tc_set_autotune(autotune && E.tc_mode != 0);
+  try {
+    CCLR_CUDA(cudaEventRecord(tm.ev[0], st));
+    apply_body(dir, C, nr, x1, x2, s1, s2, true, lad_ms, form_ms);
+  } catch (...) {
+    tc_set_autotune(false);
+    throw;
+  }
+  tc_set_autotune(false);
   CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
   CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
   float tot = 0.f;

@@ -104,6 +104,7 @@ class Model {
   // precision, buffer addresses) repeat those of an earlier eager call, with no memory freed
   // or constants rebuilt since, is captured once and then replayed by cudaGraphLaunch.
   bool graphs = false;
+  bool autotune = true;  // tensor-core GEMM shapes tuned on their first (eager) use
   std::vector<GraphEntry> gcache;
   std::vector<GraphEntry> warm;  // recent eager calls (key, epoch after the call); no exec
   int graph_launches = 0, graph_captures = 0;

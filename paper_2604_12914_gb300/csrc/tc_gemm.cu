@@ -12,8 +12,12 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
+#include "engine.cuh"
 #include "tc_gemm.cuh"
 
 namespace cclr {
@@ -595,18 +599,35 @@ void tc_prep_b(const void *B, int64_t sbk, int64_t sbn, int64_t K, int64_t N, in
   tc_prep_b2(B, view1(sbk), view1(sbn), K, N, seg, kind, dst, ldd, st);
 }
 
+// Launch configuration: tile width BN, K splits and raster band (0 = the rule's choice).
+struct TcCfg {
+  int BN = 0, splits = 0, band = 0;
+};
+
+struct TuneKey {
+  int dev, kind, transposed;
+  int64_t M, N, K;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(dev, kind, transposed, M, N, K) < std::tie(o.dev, o.kind, o.transposed, o.M, o.N, o.K);
+  }
+};
+struct TuneRec {
+  TcCfg cfg, rule;
+  float ms_best = 0.f, ms_rule = 0.f;
+  int tried = 0;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneRec> g_tune;
+thread_local bool g_tune_on = false;
+
 // a_cols: operand elements A actually holds per row (<= Kreal; the rest reads as zero).
-// lda, ldb, Kreal in elements of the operand type.
-static void tc_gemm_core(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal,
-                         int64_t Kreal, int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
-                         int max_kb_per_split, int *err, cudaStream_t st, int64_t a_cols = -1) {
-  if (M <= 0 || Nreal <= 0) return;
+// lda, ldb, Kreal in elements of the operand type.  cfg overrides the rules; *used receives the
+// configuration launched.
+static void tc_launch(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal, int64_t Kreal,
+                      int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, int max_kb_per_split,
+                      int *err, cudaStream_t st, int64_t a_cols, TcCfg cfg, TcCfg *used) {
   const int64_t es = tc_esize(kind), BK = BKB / es;
-  CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
-  CCLR_REQUIRE((lda * es) % 16 == 0 && (ldb * es) % 16 == 0, "tc_gemm: row pitches must be multiples of 16 bytes");
-  CCLR_REQUIRE(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, "tc_gemm: operands must be 16-byte aligned");
-  CCLR_REQUIRE(M < (1ll << 31) && Nreal < (1ll << 31) && Kreal < (1ll << 31), "tc_gemm: dimension too large");
-  const int BN = pick_bn(Nreal);
+  const int BN = cfg.BN > 0 ? cfg.BN : pick_bn(Nreal);
   const CUtensorMap ma = make_map(A, M, a_cols < 0 ? Kreal : a_cols, lda, BM, kind);
   const CUtensorMap mb = make_map(B, Nreal, Kreal, ldb, BN, kind);
   TcParams p;
@@ -617,14 +638,16 @@ static void tc_gemm_core(const void *A, int64_t lda, const void *B, int64_t ldb,
   p.nMt = (int)((M + BM - 1) / BM);
   p.nNt = (int)((Nreal + BN - 1) / BN);
   // band of M tiles whose A rows (about 32 MB) stay in L2 while N sweeps
-  p.band = (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * es + 1)));
+  p.band = cfg.band > 0 ? std::min(cfg.band, p.nMt)
+                        : (int)std::max<int64_t>(1, std::min<int64_t>(p.nMt, (32ll << 20) / (BM * Kreal * es + 1)));
   const int nk = (int)((Kreal + BK - 1) / BK);
   const int64_t tiles = (int64_t)p.nMt * p.nNt;
   const int nsm = num_sms();
   // split K when the tile list cannot fill the GPU (two units per SM), at least 16 K blocks
   // per split
   int splits = 1;
-  if (tiles < 2 * nsm && nk >= 32)
+  if (cfg.splits > 0) splits = std::min(cfg.splits, nk);
+  else if (tiles < 2 * nsm && nk >= 32)
     splits = (int)std::max<int64_t>(1, std::min<int64_t>((2 * nsm + tiles - 1) / tiles, nk / 16));
   // bound the length of each accumulation chain (accuracy of the split-precision passes)
   if (max_kb_per_split > 0) splits = std::max(splits, (nk + max_kb_per_split - 1) / max_kb_per_split);
@@ -661,6 +684,124 @@ static void tc_gemm_core(const void *A, int64_t lda, const void *B, int64_t ldb,
   else tc_gemm_kernel<TC_TF32><<<grid, 320, smem, st>>>(ma, mb, p);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
+  if (used) {
+    used->BN = BN;
+    used->splits = splits;
+    used->band = p.band;
+  }
+}
+
+// Candidate configurations around the rule's choice: other tile widths for wide outputs, more or
+// fewer K splits where the tile list is short, and the two extreme raster bands.
+static std::vector<TcCfg> candidates(const TcCfg &rule, int64_t M, int64_t Nreal, int64_t Kreal, int kind,
+                                     bool allow_split) {
+  std::vector<TcCfg> c{rule};
+  auto add = [&](TcCfg x) {
+    for (const auto &y : c)
+      if (y.BN == x.BN && y.splits == x.splits && y.band == x.band) return;
+    c.push_back(x);
+  };
+  if (Nreal > 256)
+    for (int bn : {128, 192, 256}) { TcCfg x = rule; x.BN = bn; add(x); }
+  const int64_t nk = (Kreal + BKB / tc_esize(kind) - 1) / (BKB / tc_esize(kind));
+  if (!allow_split) {
+  } else if (rule.splits > 1) {
+    TcCfg x = rule; x.splits = std::max(1, rule.splits / 2); add(x);
+    x.splits = (int)std::min<int64_t>(nk, 2 * rule.splits); add(x);
+  } else if (nk >= 16) {
+    TcCfg x = rule; x.splits = 2; add(x);
+  }
+  const int nMt = (int)((M + BM - 1) / BM);
+  if (nMt > 1) {
+    TcCfg x = rule; x.band = 1; add(x);
+    x.band = nMt; add(x);
+  }
+  return c;
+}
+
+static void tc_gemm_core(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal,
+                         int64_t Kreal, int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate,
+                         int max_kb_per_split, int *err, cudaStream_t st, int64_t a_cols = -1) {
+  if (M <= 0 || Nreal <= 0) return;
+  const int64_t es = tc_esize(kind);
+  CCLR_REQUIRE(Nreal % 2 == 0, "tc_gemm: real N must be even (complex pairs)");
+  CCLR_REQUIRE((lda * es) % 16 == 0 && (ldb * es) % 16 == 0, "tc_gemm: row pitches must be multiples of 16 bytes");
+  CCLR_REQUIRE(((uintptr_t)A % 16) == 0 && ((uintptr_t)B % 16) == 0, "tc_gemm: operands must be 16-byte aligned");
+  CCLR_REQUIRE(M < (1ll << 31) && Nreal < (1ll << 31) && Kreal < (1ll << 31), "tc_gemm: dimension too large");
+  const int transposed = (cv.sin == 1 && (cv.din == TC_ONE_LEVEL || cv.din >= 8)) ? 1 : 0;
+  const TuneKey key{current_device(), kind, transposed, M, Nreal, Kreal};
+  TcCfg cfg;
+  bool have = false;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      cfg = it->second.cfg;
+      have = true;
+    }
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CCLR_CUDA(cudaStreamIsCapturing(st, &cap));
+  // Autotuning (first use of a shape while tuning is on, never inside a capture): every candidate
+  // is timed with CUDA events on the real operands.  Outputs that are overwritten are tuned in
+  // place (the launch below rewrites them); accumulated ones into a scratch block of the same
+  // shape when it fits in 512 MB, else the rule stands.
+  if (!have && g_tune_on && cap == cudaStreamCaptureStatusNone) {
+    const size_t cbytes = (size_t)M * Nreal * 4;
+    DevBuf scratch;
+    float *Ct = C;
+    View2 trv = rv, tcv = cv;
+    bool ok = true;
+    if (accumulate) {
+      if (cbytes <= (512ull << 20)) {
+        scratch.alloc(cbytes);
+        Ct = scratch.as<float>();
+        trv = view1(Nreal / 2);
+        tcv = view1(1);
+      } else {
+        ok = false;
+      }
+    }
+    TuneRec rec;
+    if (ok) {
+      TcCfg rule;
+      tc_launch(A, lda, B, ldb, M, Nreal, Kreal, kind, Ct, trv, tcv, alpha, false, max_kb_per_split, err, st, a_cols,
+                TcCfg(), &rule);
+      rec.rule = rule;
+      cudaEvent_t e0, e1;
+      CCLR_CUDA(cudaEventCreate(&e0));
+      CCLR_CUDA(cudaEventCreate(&e1));
+      float best = 1e30f;
+      // K splits need an accumulating or plain output (split partial tiles are added atomically)
+      const bool plain = trv.din == TC_ONE_LEVEL && tcv.din == TC_ONE_LEVEL && tcv.sin == 1;
+      for (const TcCfg &cand : candidates(rule, M, Nreal, Kreal, kind, accumulate || plain)) {
+        TcCfg used;
+        CCLR_CUDA(cudaEventRecord(e0, st));
+        tc_launch(A, lda, B, ldb, M, Nreal, Kreal, kind, Ct, trv, tcv, alpha, false, max_kb_per_split, err, st, a_cols,
+                  cand, &used);
+        CCLR_CUDA(cudaEventRecord(e1, st));
+        CCLR_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CCLR_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (rec.tried == 0) rec.ms_rule = ms;  // the first candidate is the rule's configuration
+        ++rec.tried;
+        if (ms < best) {
+          best = ms;
+          rec.cfg = used;
+        }
+      }
+      rec.ms_best = best;
+      CCLR_CUDA(cudaEventDestroy(e0));
+      CCLR_CUDA(cudaEventDestroy(e1));
+    } else {
+      rec.cfg = TcCfg();
+    }
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = rec;
+    cfg = rec.cfg;
+  }
+  tc_launch(A, lda, B, ldb, M, Nreal, Kreal, kind, C, rv, cv, alpha, accumulate, max_kb_per_split, err, st, a_cols, cfg,
+            nullptr);
 }
 
 void tc_gemm(const float *A, int64_t lda, const float *B, int64_t ldb, int64_t M, int64_t Nreal,
@@ -723,6 +864,27 @@ int tc_selftest_timeout(int timeout_us, cudaStream_t st) {
   count_launch();
   CCLR_CUDA(cudaGetLastError());
   return tc_error(st);
+}
+
+void tc_set_autotune(bool on) { g_tune_on = on; }
+
+int tc_tuning_table(int cap, double *rec) {
+  const int dev = current_device();
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  int n = 0;
+  for (const auto &kv : g_tune) {
+    if (kv.first.dev != dev) continue;
+    if (n < cap && rec) {
+      double *r = rec + 10 * n;
+      const TuneKey &k = kv.first;
+      const TuneRec &t = kv.second;
+      r[0] = k.kind; r[1] = (double)k.M; r[2] = (double)k.N; r[3] = (double)k.K;
+      r[4] = t.cfg.BN; r[5] = t.cfg.splits; r[6] = t.cfg.band;
+      r[7] = t.ms_best; r[8] = t.ms_rule; r[9] = t.tried;
+    }
+    ++n;
+  }
+  return n;
 }
 
 int tc_error(cudaStream_t st) {

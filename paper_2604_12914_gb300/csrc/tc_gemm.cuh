@@ -148,6 +148,15 @@ void tc_gemm_seg_flagged(const float *A, int64_t lda, const float *B, int64_t ld
 void tc_gemm_seg_v(const void *A, int64_t lda, const void *B, int64_t ldb, int64_t M, int64_t Nreal, int64_t Kseg,
                    int seg, int kind, float *C, View2 rv, View2 cv, zc alpha, bool accumulate, cudaStream_t st);
 
+// Tile autotuner: while on (per host thread), the first use of a GEMM shape (operand kind, M,
+// real N, real K, epilogue layout) on a device times a handful of launch configurations (tile
+// width, K splits, raster band) around the rules' choice and caches the fastest for that shape
+// and device; later uses launch the cached configuration.  Never tunes inside a stream capture.
+void tc_set_autotune(bool on);
+// Rows of 10 doubles per tuned shape of the current device (kind, M, N, K, BN, splits, band,
+// best ms, the rule's ms, candidates timed), up to cap rows; returns the number of shapes.
+int tc_tuning_table(int cap, double *rec);
+
 // Reads (and clears) the device-side error flag of the tensor-core kernels: 0 = fine,
 // 1 = a bounded wait gave up.
 int tc_error(cudaStream_t st);

@@ -118,3 +118,21 @@ def test_c4_lambda_and_alpha_from_both_sides(c4sys):
     assert st_r["converged"] == 1 and st_l["converged"] == 1
     assert d < 1e-4
     ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol_alpha", [("fp64", 1e-8), ("tf32", 1e-5)])
+def test_alpha_to_absolute_tolerance(prec, tol_alpha):
+    """cc_lr_solve_alpha_tol: solves tightened until the left- and right-route alphas agree within
+    tol_alpha; the result then agrees with the oracle's alpha (which shares no code) within the
+    1e-4 a.u. target, and the estimate is below tol_alpha."""
+    s, P = _converged_small()
+    ctx = gpu_context(s, t1=P.t1.numpy(), t2=P.t2.numpy(), prec=prec)
+    if prec != "fp64":
+        ctx.cc_lr_set_refinement("3xtf32")
+    al, est, st = ctx.cc_lr_solve_alpha_tol([0.0428], (0, 1, 2), tol_alpha=tol_alpha)
+    ref = R.alpha(P, [as_t(m) for m in s.mu], 0.0428).numpy()
+    err = np.abs(al[0] - ref).max()
+    print(f"{prec}: tol_alpha {tol_alpha:.0e}: estimate {est:.2e}, |alpha - oracle| {err:.2e}, {st}")
+    assert est < tol_alpha
+    assert err < (1e-6 * np.abs(ref).max() if prec == "fp64" else 1e-4)
+    ctx.close()

@@ -410,3 +410,56 @@ def test_damped_alpha_two_electrons_equals_sum_over_states():
                         for a in range(3)])
         assert np.abs(al[0] - sos).max() < 1e-7 * np.abs(sos).max()
     ctx.close()
+
+
+def test_gemm_autotuner_caches_shapes_and_keeps_results():
+    """The tile autotuner: the first tensor-core sigma tunes every GEMM shape it meets (rows in
+    cc_lr_gemm_tuning with the candidates timed, the best no slower than the rules' choice), and
+    the tuned launches give the same sigma as the rules' configuration (autotune off)."""
+    s = make_config("C1")
+    x1, x2 = random_amplitudes(s.o, s.v, seed=3)
+    from paper_2604_12914_gb300 import binding
+    ref = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec="3xtf32")
+    ref.cc_lr_set_autotune(False)
+    n_before = len(ref.cc_lr_gemm_tuning())
+    r1, r2 = ref.cc_lr_sigma(x1, x2)
+    ref.close()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec="3xtf32")
+    g1, g2 = ctx.cc_lr_sigma(x1, x2)
+    tab = ctx.cc_lr_gemm_tuning()
+    assert len(tab) > n_before
+    for row in tab:
+        if row["tried"] > 0:
+            assert row["ms_best"] <= row["ms_rule"] * 1.0001
+    h1, h2 = ctx.cc_lr_sigma(x1, x2)         # tuned shapes: cached configuration
+    assert rel_err(g1, g2, r1, r2) < 1e-6
+    assert rel_err(h1, h2, r1, r2) < 1e-6
+    print(f"{len(tab)} tuned shapes; e.g. {tab[:3]}")
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("tf32", 1e-6)])
+def test_packed_sigma_entry_point_matches_full_layout(prec, tol):
+    """cc_lr_sigma_packed (unique amplitudes i<j, a<b, device arrays) equals cc_lr_sigma in the full
+    layout, for a batch of right-hand sides and for the transpose."""
+    o, v, naux, seed, scale, t1s = CASES[2]
+    s = make_system(o, v, naux, seed=seed, scale=scale)
+    t1, t2 = _amps(s, seed + 100, t1s)
+    ctx = gpu_context(s, t1=t1, t2=t2, prec=prec)
+    x1, x2 = random_amplitudes(o, v, seed=5, nvec=3)
+    oi, oj = np.triu_indices(o, 1)
+    vi, vj = np.triu_indices(v, 1)
+
+    def pack(a1, a2):
+        return np.concatenate([a1.reshape(-1), a2[oi, oj][:, vi, vj].reshape(-1)])
+
+    xp = torch.tensor(np.stack([pack(x1[r], x2[r]) for r in range(3)]), device="cuda")
+    for transpose in (False, True):
+        g1, g2 = ctx.cc_lr_sigma(x1, x2, transpose=transpose)
+        sp = torch.empty_like(xp)
+        ctx.sigma_packed(xp, sp, nrhs=3, transpose=transpose)
+        got = sp.cpu().numpy()
+        for r in range(3):
+            ref = pack(g1[r], g2[r])
+            assert np.abs(got[r] - ref).max() < tol * np.abs(ref).max()
+    ctx.close()
