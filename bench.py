@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--no-hbm", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--solve-large", default="",
+                    help="only run a large mixed-precision solve and print its JSON: "
+                         "'C3' (3 components x {0, +-0.02, +-0.0428, +-0.0656} = 21 systems in one block) "
+                         "or 'C5' (zz at omega = 0 by both routes, alpha tolerance, 180 GB budget)")
+    ap.add_argument("--solve-scale", type=float, default=0.0)
     ap.add_argument("--alpha-large-config", default="C2")
     ap.add_argument("--alpha-large-scale", type=float, default=0.05)
     return ap.parse_args()
@@ -420,6 +425,46 @@ def packed_batch(cfg, nrhs, precs, reps=2):
     return out
 
 
+def solve_large(cfg, scale):
+    """A mixed-precision solve at a large workload (TF32 corrections, 3xTF32 refinement, FP64
+    vectors) with its wall time, iterations and device memory: at o=40 v=320 the 21 systems of 3
+    components x {0, +-0.02, +-0.0428, +-0.0656} in one block (every iteration applies the operator
+    to all unconverged systems in batched products); at o=56 v=480 the zz component at omega = 0 to
+    an absolute alpha tolerance of 1e-4 a.u. (left- and right-route alphas), under a 180 GB budget."""
+    import numpy as np
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import make_config
+    c5 = cfg == "C5"
+    scale = scale or (0.035 if c5 else 0.045)
+    s = make_config(cfg, scale=scale)
+    budget = int(180e9) if c5 else 0
+    t0 = time.perf_counter()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec="tf32", hbm_budget=budget)
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
+           "init_seconds": time.perf_counter() - t0, "budget_gb": budget / 1e9 if budget else None}
+    del s
+    ctx.cc_lr_set_refinement("3xtf32")
+    t0 = time.perf_counter()
+    if c5:
+        ctx.cc_lr_set_solver("gmres", 20, 200)
+        al, est, st = ctx.cc_lr_solve_alpha_tol([0.0], (2,), tol_alpha=1e-4, allow_noconv=True)
+        out.update({"what": "alpha_zz(0) to |alpha_left - alpha_right| < 1e-4 a.u.",
+                    "alpha_zz": [float(al[0, 0, 0].real), float(al[0, 0, 0].imag)], "estimate_au": est})
+    else:
+        ctx.cc_lr_set_solver("block", 20, 300)
+        omegas = [0.0, 0.02, 0.0428, 0.0656]
+        al, st = ctx.cc_lr_solve(omegas, (0, 1, 2), tol=1e-5, allow_noconv=True)
+        out.update({"what": "3 components x 7 shifts = 21 systems in one block, relative residual 1e-5",
+                    "alpha_diag": [[float(al[w, a, a].real) for a in range(3)] for w in range(len(omegas))],
+                    "max_abs_imag_diag": float(np.abs(np.imag(np.diagonal(al, axis1=1, axis2=2))).max())})
+    out["seconds"] = time.perf_counter() - t0
+    out["stats"] = st
+    used, peak, _ = ctx.cc_lr_memory()
+    out["device_memory_gb"] = {"held": used / 1e9, "peak": peak / 1e9}
+    ctx.close()
+    return out
+
+
 def cublas_tf32_tflops():
     """cuBLAS TF32 GEMM 8192^3 (torch.matmul on FP32 with TF32 allowed), best of 5, CUDA events."""
     import torch
@@ -691,7 +736,9 @@ def run_cclr(args):
 
 if __name__ == "__main__":
     a = parse()
-    if a.impl == "reference":
+    if a.solve_large:
+        print(json.dumps({"solve_large": solve_large(a.solve_large, a.solve_scale)}), flush=True)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_cclr(a)

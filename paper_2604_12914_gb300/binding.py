@@ -324,9 +324,11 @@ class Context:
     def cc_lr_set_autotune(self, on=True):
         _check(load().cc_lr_set_autotune(self._h, 1 if on else 0))
 
-    def cc_lr_gemm_tuning(self, cap=256):
-        """List of dicts: the tuned GEMM shapes of this device and their chosen configuration."""
+    def cc_lr_gemm_tuning(self):
+        """List of dicts: every tuned GEMM shape of this device and its chosen configuration."""
         n = ctypes.c_int(0)
+        _check(load().cc_lr_gemm_tuning(self._h, 0, ctypes.byref(n), None))
+        cap = max(1, n.value)
         rec = np.zeros((cap, 10), dtype=np.float64)
         _check(load().cc_lr_gemm_tuning(self._h, cap, ctypes.byref(n), _ptr(rec)))
         keys = ["kind", "M", "N", "K", "BN", "splits", "band", "ms_best", "ms_rule", "tried"]

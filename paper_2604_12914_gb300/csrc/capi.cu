@@ -1,5 +1,6 @@
 // C ABI of libcclr (declared in include/cclr.h): context life cycle, sigma / sigma^T, the
 // preconditioned DIIS linear solver in FP64, the ground-state Lambda, and alpha(omega).
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -112,9 +113,30 @@ struct cclr_ctx {
     for (int r = 0; r < nr; ++r)
       if (!xf[r].p) { xf[r].alloc((size_t)nfull() * dt_size(dt)); sf[r].alloc((size_t)nfull() * dt_size(dt)); }
   }
+  // right-hand sides per batched product: the per-RHS full-layout staging (and, in the
+  // transpose, x2-bar) and the ladder's packed operands must fit in a third of what is free
+  int batch_cap(int dir, int dt, int nr) {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
+      (void)cudaGetLastError();
+      return nr;
+    }
+    if (acct.budget) free_b = std::min(free_b, acct.budget > acct.used ? acct.budget - acct.used : (size_t)0);
+    const double per = (double)nfull() * dt_size(dt) * (dir < 0 ? 3 : 2) + (double)n2p * 8 * 4;
+    const int fit = (int)(free_b / 3.0 / per);
+    return std::max(1, std::min(nr, fit));
+  }
   void op_batch(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set = nullptr) {
-    sigma_calls += nr;
     if (set == nullptr) set = &M->cst_for(M->prec);
+    const int cap = batch_cap(dir, set->dt, nr);
+    if (cap < nr) {  // several batched products, each sharing its formed blocks
+      for (int r0 = 0; r0 < nr; r0 += cap) op_batch_chunk(dir, std::min(cap, nr - r0), xs + r0, ss + r0, set);
+      return;
+    }
+    op_batch_chunk(dir, nr, xs, ss, set);
+  }
+  void op_batch_chunk(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set) {
+    sigma_calls += nr;
     const int dt = set->dt;
     const size_t es = dt_size(dt);
     stage_full(dt, nr);
@@ -246,10 +268,17 @@ struct cclr_ctx {
   // preconditioner P = (D - omega)^-1 (diagonal of A), modified Gram-Schmidt in the
   // weighted Hermitian inner product (singles 1, doubles 1/4), Givens rotations and the
   // small least-squares problem on the host in FP64.
-  std::vector<AVec> kv;  // Krylov basis (kept between calls)
+  std::vector<AVec> kv;  // Krylov basis (kept between calls unless the context is budgeted)
   double solve_gmres(int dir, zd omega, const void *b, void *x, double tol, int m, int maxit,
                      int *its, bool warm) {
     m = std::max(2, std::min(m, 100));
+    if (acct.budget) m = std::min(m, block_restart(1, 0.2));
+    struct Release {
+      cclr_ctx *c;
+      ~Release() {
+        if (c->M->lean) c->kv.clear();
+      }
+    } rel_guard{this};
     if ((int)kv.size() < m + 1) kv.resize(m + 1);
     for (int k = 0; k <= m; ++k) alloc_vec(kv[k]);
     AVec z, w;
@@ -513,7 +542,7 @@ struct cclr_ctx {
                    const std::vector<void *> &x, double tol, int maxit, std::vector<int> &its,
                    std::vector<double> &rel, bool warm = false) {
     const int nr = (int)b.size();
-    const int m = block_restart(nr);
+    const int m = block_restart(nr, M->lean ? 0.2 : 0.5);
     if (M->prec == CCLR_FP64) {
       gmres_block(dir, om, b, x, std::vector<double>(nr, tol), m, maxit, its, rel, warm);
       return;
@@ -615,7 +644,7 @@ struct cclr_ctx {
 
   // restart length of the block solver: the Krylov bases of all systems must fit in half of
   // the free device memory (and of what the context's budget leaves)
-  int block_restart(int nr) {
+  int block_restart(int nr, double frac = 0.5) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       (void)cudaGetLastError();
@@ -623,7 +652,7 @@ struct cclr_ctx {
     }
     if (acct.budget) free_b = std::min(free_b, acct.budget > acct.used ? acct.budget - acct.used : (size_t)0);
     const double vec = (double)ntot() * 16;
-    const int fit = (int)(0.5 * (double)free_b / (vec * std::max(1, nr))) - 4;
+    const int fit = (int)(frac * (double)free_b / (vec * std::max(1, nr))) - 4;
     return std::max(2, std::min(krylov, fit));
   }
 
@@ -862,6 +891,11 @@ struct cclr_ctx {
     }
     // d eta0 / dT along X: sum_jb <ij||ab> X_jb (singles only)
     packed_doubles_dot_singles(o, v, M->oovv_packed(), x, out, zc(1), st);
+    if (M->lean) {  // the stencil's set is rebuilt for every X: not kept in a budgeted context
+      M->release_set(shift64);
+      M->release_set(shift);
+      fullB.b.release();
+    }
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
 };
@@ -929,6 +963,7 @@ cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps
     CCLR_CUDA(cudaGetDevice(&dev));
     c->M.reset(new Model(o, v, naux, c->st));
     c->M->prec = prec;
+    c->M->lean = hbm_budget_bytes > 0;
     c->M->upload_inputs(eps, L, mu, t1, t2, device_ptrs);
     c->M->cst_for(prec);      // intermediates in the working precision
     c->M->build_diagonal();
@@ -1074,119 +1109,6 @@ cclr_status cc_lr_lambda(cclr_ctx *c, double tol, double *lam1, double *lam2) {
   });
 }
 
-// alpha at z = omega + i gamma for every omega (gamma = 0: the undamped response):
-//   g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w),
-//   <<A;B>>_z = 1/2 [g(A,B;z) + conj g(A,B;-z*)],  alpha = -<<A;B>>,
-// so X^C is needed at the shifts z, -z, z*, -z* (two of them when gamma = 0, one at z = 0).
-static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, double gamma, int ncomp,
-                               const int *comps, double tol, int diis_depth, double *alpha, cclr_stats *stats) {
-  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0) || !(gamma >= 0))
-    return (cclr_status)fail(CCLR_EINVAL, "bad solve arguments");
-  for (int k = 0; k < ncomp; ++k)
-    if (comps[k] < 0 || comps[k] > 2) return (cclr_status)fail(CCLR_EINVAL, "component out of range");
-  cclr_stats loc;
-  std::memset(&loc, 0, sizeof(loc));
-  loc.converged = 1;
-  int st = guarded_ctx(c, [&] {
-    int calls0 = c->sigma_calls;
-    c->ensure_lambda(tol, diis_depth, &loc);
-    for (int w = 0; w < nomega; ++w) {
-      const zd z(omegas[w], gamma);
-      // distinct shifts among z, -z, z*, -z*; slot[k] = index of the shift used for the k-th
-      const zd want[4] = {z, -z, std::conj(z), -std::conj(z)};
-      std::vector<zd> shifts;
-      int slot[4];
-      for (int k = 0; k < 4; ++k) {
-        int f = -1;
-        for (size_t q = 0; q < shifts.size(); ++q)
-          if (shifts[q] == want[k]) f = (int)q;
-        if (f < 0) {
-          f = (int)shifts.size();
-          shifts.push_back(want[k]);
-        }
-        slot[k] = f;
-      }
-      const int ns = (int)shifts.size();
-      std::vector<AVec> X((size_t)ncomp * ns);
-      auto Xs = [&](int a, int k) -> AVec & { return X[(size_t)a * ns + slot[k]]; };
-      auto t0 = std::chrono::steady_clock::now();
-      std::vector<AVec> B(ncomp);
-      for (int a = 0; a < ncomp; ++a) {
-        c->alloc_vec(B[a]);
-        c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, B[a].b.p);
-        c->scal(zd(-1), B[a].b.p);
-        for (int q = 0; q < ns; ++q) c->alloc_vec(X[(size_t)a * ns + q]);
-      }
-      if (c->method == 2) {
-        // every component and shift in one block: the operator is applied to all at once
-        std::vector<zd> oms;
-        std::vector<const void *> bs;
-        std::vector<void *> xs;
-        for (int a = 0; a < ncomp; ++a)
-          for (int q = 0; q < ns; ++q) {
-            oms.push_back(shifts[q]);
-            bs.push_back(B[a].b.p);
-            xs.push_back(X[(size_t)a * ns + q].b.p);
-          }
-        std::vector<int> its;
-        std::vector<double> rels;
-        c->solve_block(+1, oms, bs, xs, tol, c->maxit, its, rels);
-        for (size_t k = 0; k < its.size(); ++k) {
-          loc.iterations += its[k];
-          loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
-          if (!(rels[k] < tol)) loc.converged = 0;
-        }
-      } else {
-        for (int a = 0; a < ncomp; ++a)
-          for (int q = 0; q < ns; ++q) {
-            int its = 0;
-            double rel = c->solve(+1, shifts[q], B[a].b.p, X[(size_t)a * ns + q].b.p, tol, diis_depth, c->maxit, &its);
-            loc.iterations += its;
-            loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
-            if (!(rel < tol)) loc.converged = 0;
-          }
-      }
-      auto t1 = std::chrono::steady_clock::now();
-      loc.time_solve_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
-      // eta^A . X^B at every shift, and F X^A at -z (for g(z)) and z* (for g(-z*))
-      std::vector<zd> ED((size_t)ncomp * ncomp * ns);
-      for (int a = 0; a < ncomp; ++a)
-        for (int b = 0; b < ncomp; ++b)
-          for (int q = 0; q < ns; ++q)
-            ED[((size_t)a * ncomp + b) * ns + q] = c->eta_dot(comps[a], X[(size_t)b * ns + q].b.p);
-      auto EDs = [&](int a, int b, int k) { return ED[((size_t)a * ncomp + b) * ns + slot[k]]; };
-      std::vector<AVec> FX((size_t)ncomp * ns);
-      std::vector<char> have((size_t)ncomp * ns, 0);
-      auto FXs = [&](int a, int k) -> AVec & {
-        const size_t id = (size_t)a * ns + slot[k];
-        if (!have[id]) {
-          c->alloc_vec(FX[id]);
-          c->fx(X[id].b.p, FX[id].b.p);
-          have[id] = 1;
-        }
-        return FX[id];
-      };
-      for (int a = 0; a < ncomp; ++a)
-        for (int b = 0; b < ncomp; ++b) {
-          // k: 0 = z, 1 = -z, 2 = z*, 3 = -z*
-          zd gp = EDs(a, b, 0) + EDs(b, a, 1) + c->dot(FXs(a, 1).b.p, Xs(b, 0).b.p, 0);
-          zd gm = EDs(a, b, 3) + EDs(b, a, 2) + c->dot(FXs(a, 2).b.p, Xs(b, 3).b.p, 0);
-          zd al = -0.5 * (gp + std::conj(gm));
-          size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
-          alpha[k] = al.real();
-          alpha[k + 1] = al.imag();
-        }
-      loc.time_alpha_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
-    }
-    loc.sigma_calls = c->sigma_calls - calls0;
-    loc.refinements = c->refinements;
-    c->release_scratch();
-  });
-  if (stats) *stats = loc;
-  if (st != CCLR_OK) return (cclr_status)st;
-  return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve: tolerance not met");
-}
-
 // Right (X) solves of every component at the shifts in sh, in one block or one by one.
 static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const std::vector<const void *> &bs,
                         const std::vector<void *> &xs, double tol, int diis_depth, cclr_stats &loc,
@@ -1209,6 +1131,107 @@ static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const s
     loc.max_rel_residual = std::max(loc.max_rel_residual, rel);
     if (!(rel < tol)) loc.converged = 0;
   }
+}
+
+// alpha at z = omega + i gamma for every omega (gamma = 0: the undamped response):
+//   g(A,B;w) = eta^A X^B(w) + eta^B X^A(-w) + (F X^A(-w)) X^B(w),
+//   <<A;B>>_z = 1/2 [g(A,B;z) + conj g(A,B;-z*)],  alpha = -<<A;B>>,
+// so X^C is needed at the shifts z, -z, z*, -z* (two of them when gamma = 0, one at z = 0).
+static cclr_status solve_alpha(cclr_ctx *c, int nomega, const double *omegas, double gamma, int ncomp,
+                               const int *comps, double tol, int diis_depth, double *alpha, cclr_stats *stats) {
+  if (!c || nomega < 1 || !omegas || ncomp < 1 || ncomp > 3 || !comps || !alpha || !(tol > 0) || !(gamma >= 0))
+    return (cclr_status)fail(CCLR_EINVAL, "bad solve arguments");
+  for (int k = 0; k < ncomp; ++k)
+    if (comps[k] < 0 || comps[k] > 2) return (cclr_status)fail(CCLR_EINVAL, "component out of range");
+  cclr_stats loc;
+  std::memset(&loc, 0, sizeof(loc));
+  loc.converged = 1;
+  int st = guarded_ctx(c, [&] {
+    int calls0 = c->sigma_calls;
+    c->ensure_lambda(tol, diis_depth, &loc);
+    // the distinct shifts over every frequency (z, -z, z*, -z* of each); slot[w][k] = the index of
+    // the shift the k-th of them uses at frequency w
+    std::vector<zd> shifts;
+    std::vector<std::array<int, 4>> slot(nomega);
+    for (int w = 0; w < nomega; ++w) {
+      const zd z(omegas[w], gamma);
+      const zd want[4] = {z, -z, std::conj(z), -std::conj(z)};
+      for (int k = 0; k < 4; ++k) {
+        int f = -1;
+        for (size_t q = 0; q < shifts.size(); ++q)
+          if (shifts[q] == want[k]) f = (int)q;
+        if (f < 0) {
+          f = (int)shifts.size();
+          shifts.push_back(want[k]);
+        }
+        slot[w][k] = f;
+      }
+    }
+    const int ns = (int)shifts.size();
+    std::vector<AVec> X((size_t)ncomp * ns);
+    auto t0 = std::chrono::steady_clock::now();
+    std::vector<AVec> B(ncomp);
+    for (int a = 0; a < ncomp; ++a) {
+      c->alloc_vec(B[a]);
+      c->xi_vec(comps[a], c->M->t1.p, c->M->t2.p, B[a].b.p);
+      c->scal(zd(-1), B[a].b.p);
+      for (int q = 0; q < ns; ++q) c->alloc_vec(X[(size_t)a * ns + q]);
+    }
+    {
+      // every component and shift of every frequency: one block (method 2: the operator is applied
+      // to all unconverged systems at once) or one solve after another
+      std::vector<zd> oms;
+      std::vector<const void *> bs;
+      std::vector<void *> xs;
+      for (int a = 0; a < ncomp; ++a)
+        for (int q = 0; q < ns; ++q) {
+          oms.push_back(shifts[q]);
+          bs.push_back(B[a].b.p);
+          xs.push_back(X[(size_t)a * ns + q].b.p);
+        }
+      solve_right(c, +1, oms, bs, xs, tol, diis_depth, loc);
+    }
+    auto t1 = std::chrono::steady_clock::now();
+    loc.time_solve_ms += std::chrono::duration<double, std::milli>(t1 - t0).count();
+    // eta^A . X^B at every shift, and F X^A where a frequency needs it (-z for g(z), z* for g(-z*))
+    std::vector<zd> ED((size_t)ncomp * ncomp * ns);
+    for (int a = 0; a < ncomp; ++a)
+      for (int b = 0; b < ncomp; ++b)
+        for (int q = 0; q < ns; ++q)
+          ED[((size_t)a * ncomp + b) * ns + q] = c->eta_dot(comps[a], X[(size_t)b * ns + q].b.p);
+    std::vector<AVec> FX((size_t)ncomp * ns);
+    std::vector<char> have((size_t)ncomp * ns, 0);
+    auto FXq = [&](int a, int q) -> AVec & {
+      const size_t id = (size_t)a * ns + q;
+      if (!have[id]) {
+        c->alloc_vec(FX[id]);
+        c->fx(X[id].b.p, FX[id].b.p);
+        have[id] = 1;
+      }
+      return FX[id];
+    };
+    for (int w = 0; w < nomega; ++w) {
+      auto Xs = [&](int a, int k) -> AVec & { return X[(size_t)a * ns + slot[w][k]]; };
+      auto EDs = [&](int a, int b, int k) { return ED[((size_t)a * ncomp + b) * ns + slot[w][k]]; };
+      for (int a = 0; a < ncomp; ++a)
+        for (int b = 0; b < ncomp; ++b) {
+          // k: 0 = z, 1 = -z, 2 = z*, 3 = -z*
+          zd gp = EDs(a, b, 0) + EDs(b, a, 1) + c->dot(FXq(a, slot[w][1]).b.p, Xs(b, 0).b.p, 0);
+          zd gm = EDs(a, b, 3) + EDs(b, a, 2) + c->dot(FXq(a, slot[w][2]).b.p, Xs(b, 3).b.p, 0);
+          zd al = -0.5 * (gp + std::conj(gm));
+          size_t k = (((size_t)w * ncomp + a) * ncomp + b) * 2;
+          alpha[k] = al.real();
+          alpha[k + 1] = al.imag();
+        }
+    }
+    loc.time_alpha_ms += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t1).count();
+    loc.sigma_calls = c->sigma_calls - calls0;
+    loc.refinements = c->refinements;
+    c->release_scratch();
+  });
+  if (stats) *stats = loc;
+  if (st != CCLR_OK) return (cclr_status)st;
+  return loc.converged ? CCLR_OK : (cclr_status)fail(CCLR_ENOCONV, "solve: tolerance not met");
 }
 
 // alpha by the left-hand route (Sec. 2.2): X^B(w) from (A - w) X = -xi^B, Y^B(w) from
@@ -1444,11 +1467,13 @@ cclr_status cc_lr_set_refinement(cclr_ctx *c, int prec) {
       if (c->M->prec != CCLR_FP64) {
         c->M->oovv_packed();  // formed from the complex128 set while it exists
         // no FP64 product remains in this configuration: its set and buffers are freed (an FP64
-        // product requested later rebuilds them)
+        // product requested later rebuilds them; in a budgeted context the FP64 inputs go too,
+        // and FP64 products are refused afterwards)
         c->M->release_fp64();
         c->xfs[C128].clear();
         c->sfs[C128].clear();
         c->M->release_set(c->shift);
+        if (c->M->lean) c->M->release_fp64_inputs();
       }
     }
   });

@@ -245,6 +245,49 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
     return;
   }
 
+  // An output mode that keeps the M or N group from being one strided index in both of its
+  // operands is peeled off as a batch index (stride 0 in the operand that lacks it), so that
+  // no operand is permuted; batch modes proper take precedence.
+  if (bat.empty()) {
+    auto merges = [&](const std::string &mm, const std::string &nn) {
+      int64_t z, t;
+      return group_view(A, ma, mm, z, t) && group_view(A, ma, Km, z, t) && group_view(B, mb, Km, z, t) &&
+             group_view(B, mb, nn, z, t) && group_view(C, mc, mm, z, t) && group_view(C, mc, nn, z, t);
+    };
+    if (!merges(Mm, Nm)) {
+      for (int side = 0; side < 2; ++side) {
+        const std::string &grp = side == 0 ? Nm : Mm;
+        for (size_t k = 0; k < grp.size() && grp.size() >= 2; ++k) {
+          std::string rest = grp;
+          const char pm = rest[k];
+          rest.erase(k, 1);
+          if (!(side == 0 ? merges(Mm, rest) : merges(rest, Nm))) continue;
+          GemmArgs g;
+          g.alr = alpha.re; g.ali = alpha.im;
+          const int pc = mode_pos(mc, pm);
+          g.batch = C.dim[pc];
+          g.sCb = C.str[pc];
+          if (side == 0) { g.sAb = 0; g.sBb = B.str[mode_pos(mb, pm)]; }
+          else { g.sBb = 0; g.sAb = A.str[mode_pos(ma, pm)]; }
+          const std::string &mm = side == 0 ? Mm : rest, &nn = side == 0 ? rest : Nm;
+          int64_t z;
+          group_view(A, ma, mm, z, g.sAm); group_view(A, ma, Km, z, g.sAk);
+          group_view(B, mb, Km, z, g.sBk); group_view(B, mb, nn, z, g.sBn);
+          group_view(C, mc, mm, z, g.sCm); group_view(C, mc, nn, z, g.sCn);
+          g.M = prod_dims(C, mc, mm); g.N = prod_dims(C, mc, nn); g.K = K;
+          if (!(g.M == 1 || K == 1 || g.sAm == 1 || g.sAk == 1) || !(K == 1 || g.N == 1 || g.sBk == 1 || g.sBn == 1))
+            continue;
+          g.A = A.p; g.B = B.p; g.C = C.p; g.overwrite = 0;
+          if (trace_on())
+            std::fprintf(stderr, "cclr contract simt %s,%s->%s batch over %c (%lld) M=%lld N=%lld K=%lld dt=%d\n",
+                         ma.c_str(), mb.c_str(), mc.c_str(), pm, (long long)g.batch, (long long)g.M, (long long)g.N,
+                         (long long)K, dt);
+          launch_gemm(g, dt, st);
+          return;
+        }
+      }
+    }
+  }
   GemmArgs g;
   g.M = M; g.N = N; g.K = K; g.batch = nb;
   g.alr = alpha.re; g.ali = alpha.im;

@@ -66,6 +66,8 @@ class Engine {
   int64_t tc_calls = 0;
   // Workspace slot s of at least `bytes` bytes (grown on demand, reused across calls).
   void *ws(int slot, size_t bytes);
+  // frees the workspace slots (they grow again on demand)
+  void release_ws() { slots_.clear(); }
   // C[mc] += alpha * sum A[ma] B[mb] over the modes not in mc (einsum semantics; every
   // mode must appear in exactly two operands or in all three).
   void contract(zc alpha, const Tens &A, const std::string &ma, const Tens &B,

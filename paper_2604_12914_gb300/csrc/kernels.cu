@@ -414,16 +414,189 @@ __global__ void antisym_project_kernel(int o, int v, typename cpx<T>::t *S) {
   }
 }
 
+// ---- tiled forms: one block per orbit {(i,j), (j,i)} x {(A,B), (B,A)} of 32 x 32 (a,b) tiles,
+// i <= j and A <= B, so that every element is read and written once and the transposed images
+// go through shared memory (coalesced in both orientations).
+
+// the k-th pair (p <= q) of n values, row by row
+__device__ __forceinline__ void tri_pair(int64_t k, int n, int &p, int &q) {
+  int r = 0;
+  while (k >= n - r) {
+    k -= n - r;
+    ++r;
+  }
+  p = r;
+  q = r + (int)k;
+}
+
+template <typename T> __device__ __forceinline__ typename cpx<T>::t cz() {
+  typename cpx<T>::t z;
+  z.x = 0;
+  z.y = 0;
+  return z;
+}
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) { a.x *= s; a.y *= s; return a; }
+
+// S <- 1/4 (S - S(ij) - S(ab) + S(ij)(ab)) in place (zero where i = j or a = b)
+template <typename T>
+__global__ void __launch_bounds__(256) antisym_project_tiled(int o, int v, typename cpx<T>::t *S) {
+  using C = typename cpx<T>::t;
+  __shared__ C P[32][33], Q[32][33];
+  const int nt = (v + 31) / 32;
+  const int64_t ntp = (int64_t)nt * (nt + 1) / 2;
+  int i, j, tA, tB;
+  tri_pair(blockIdx.x / ntp, o, i, j);
+  tri_pair(blockIdx.x % ntp, nt, tA, tB);
+  const int a0 = tA * 32, b0 = tB * 32, tx = threadIdx.x;
+  const int64_t vv = (int64_t)v * v;
+  C *Sij = S + ((int64_t)i * o + j) * vv, *Sji = S + ((int64_t)j * o + i) * vv;
+  if (i == j) {
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      if (a0 + r < v && b0 + tx < v) Sij[(int64_t)(a0 + r) * v + b0 + tx] = cz<T>();
+      if (b0 + r < v && a0 + tx < v) Sij[(int64_t)(b0 + r) * v + a0 + tx] = cz<T>();
+    }
+    return;
+  }
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    int a = a0 + r, b = b0 + tx;
+    P[r][tx] = (a < v && b < v) ? csub(Sij[(int64_t)a * v + b], Sji[(int64_t)a * v + b]) : cz<T>();
+    b = b0 + r;
+    a = a0 + tx;
+    Q[r][tx] = (a < v && b < v) ? csub(Sij[(int64_t)b * v + a], Sji[(int64_t)b * v + a]) : cz<T>();
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int a = a0 + r, b = b0 + tx;
+    if (a < v && b < v) {
+      C q = a == b ? cz<T>() : cscale(csub(P[r][tx], Q[tx][r]), (T)0.25);
+      Sij[(int64_t)a * v + b] = q;
+      Sji[(int64_t)a * v + b] = cscale(q, (T)-1);
+    }
+  }
+  if (tA != tB)
+    for (int r = threadIdx.y; r < 32; r += 8) {
+      const int b = b0 + r, a = a0 + tx;
+      if (a < v && b < v) {
+        C q = cscale(csub(Q[r][tx], P[tx][r]), (T)0.25);
+        Sij[(int64_t)b * v + a] = q;
+        Sji[(int64_t)b * v + a] = cscale(q, (T)-1);
+      }
+    }
+}
+
+// S += P(ab) Rab + P(ij) Rij + P(ij)P(ab) R4 over one orbit.  With, at (a,b),
+//   al_ij = Rab_ij - Rab_ij^T, al_ji likewise, be = Rij_ij - Rij_ji, ga = R4_ij - R4_ji - (R4_ij - R4_ji)^T
+// and beT = (Rij_ij - Rij_ji) at (b,a):
+//   S_ij(a,b) += al_ij + be + ga,  S_ji(a,b) += al_ji - be - ga,
+//   S_ij(b,a) += -al_ij - ga + beT, S_ji(b,a) += -al_ji + ga - beT.
+template <typename T>
+__global__ void __launch_bounds__(256) antisym_apply_tiled(int o, int v, typename cpx<T>::t *S,
+                                                           const typename cpx<T>::t *Rab,
+                                                           const typename cpx<T>::t *Rij,
+                                                           const typename cpx<T>::t *R4) {
+  using C = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smem_as[];
+  C(*T1)[33] = reinterpret_cast<C(*)[33]>(smem_as);   // Rab_ij at (b,a), later U1
+  C(*T2)[33] = T1 + 32;                               // Rab_ji at (b,a), later U2
+  C(*T3)[33] = T1 + 64;                               // (R4_ij - R4_ji) at (b,a)
+  C(*T4)[33] = T1 + 96;                               // (Rij_ij - Rij_ji) at (b,a)
+  const int nt = (v + 31) / 32;
+  const int64_t ntp = (int64_t)nt * (nt + 1) / 2;
+  int i, j, tA, tB;
+  tri_pair(blockIdx.x / ntp, o, i, j);
+  tri_pair(blockIdx.x % ntp, nt, tA, tB);
+  const int a0 = tA * 32, b0 = tB * 32, tx = threadIdx.x;
+  const int64_t vv = (int64_t)v * v, oij = ((int64_t)i * o + j) * vv, oji = ((int64_t)j * o + i) * vv;
+  const bool same = i == j;
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int b = b0 + r, a = a0 + tx;
+    const bool in = a < v && b < v;
+    const int64_t e = (int64_t)b * v + a;
+    T1[r][tx] = in ? Rab[oij + e] : cz<T>();
+    T2[r][tx] = in ? Rab[oji + e] : cz<T>();
+    T3[r][tx] = in ? csub(R4[oij + e], R4[oji + e]) : cz<T>();
+    T4[r][tx] = in ? csub(Rij[oij + e], Rij[oji + e]) : cz<T>();
+  }
+  __syncthreads();
+  C u1[4], u2[4];
+  for (int k = 0, r = threadIdx.y; r < 32; r += 8, ++k) {
+    const int a = a0 + r, b = b0 + tx;
+    u1[k] = cz<T>();
+    u2[k] = cz<T>();
+    if (!(a < v && b < v)) continue;
+    const int64_t e = (int64_t)a * v + b;
+    const C al_ij = csub(Rab[oij + e], T1[tx][r]);
+    const C al_ji = csub(Rab[oji + e], T2[tx][r]);
+    const C be = csub(Rij[oij + e], Rij[oji + e]);
+    const C ga = csub(csub(R4[oij + e], R4[oji + e]), T3[tx][r]);
+    if (same) {
+      S[oij + e] = cadd(S[oij + e], al_ij);
+    } else {
+      S[oij + e] = cadd(S[oij + e], cadd(al_ij, cadd(be, ga)));
+      S[oji + e] = cadd(S[oji + e], csub(al_ji, cadd(be, ga)));
+    }
+    u1[k] = cscale(cadd(al_ij, ga), (T)-1);
+    u2[k] = csub(ga, al_ji);
+  }
+  if (tA == tB) return;  // the tile holds both (a,b) and (b,a): done
+  __syncthreads();
+  for (int k = 0, r = threadIdx.y; r < 32; r += 8, ++k) {
+    T1[r][tx] = u1[k];
+    T2[r][tx] = u2[k];
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < 32; r += 8) {
+    const int b = b0 + r, a = a0 + tx;
+    if (!(a < v && b < v)) continue;
+    const int64_t e = (int64_t)b * v + a;
+    if (same) {
+      S[oij + e] = cadd(S[oij + e], T1[tx][r]);  // -al_ij at (a,b) (ga = 0 when i = j)
+    } else {
+      S[oij + e] = cadd(S[oij + e], cadd(T1[tx][r], T4[r][tx]));
+      S[oji + e] = cadd(S[oji + e], csub(T2[tx][r], T4[r][tx]));
+    }
+  }
+}
+
+static int64_t orbit_blocks(int o, int v) {
+  const int64_t nt = (v + 31) / 32;
+  return (int64_t)o * (o + 1) / 2 * (nt * (nt + 1) / 2);
+}
+
 void antisym_project(int dt, int o, int v, void *S, cudaStream_t st) {
-  const int64_t n = (int64_t)o * o * v * v;
-  const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
-  if (dt == C128) antisym_project_kernel<double><<<g, 256, 0, st>>>(o, v, (double2 *)S);
-  else antisym_project_kernel<float><<<g, 256, 0, st>>>(o, v, (float2 *)S);
+  const int64_t nb = orbit_blocks(o, v);
+  CCLR_REQUIRE(nb < (1ll << 31), "antisym_project: too many tiles");
+  if (dt == C128) antisym_project_tiled<double><<<(unsigned)nb, dim3(32, 8), 0, st>>>(o, v, (double2 *)S);
+  else antisym_project_tiled<float><<<(unsigned)nb, dim3(32, 8), 0, st>>>(o, v, (float2 *)S);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }
 
 void antisym_apply(int dt, int o, int v, int dir, void *S, void *Rab, void *Rij, void *R4, cudaStream_t st) {
+  if (dir > 0) {
+    const int64_t nb = orbit_blocks(o, v);
+    CCLR_REQUIRE(nb < (1ll << 31), "antisym_apply: too many tiles");
+    const size_t smem = (size_t)4 * 32 * 33 * (dt == C128 ? 16 : 8);
+    static std::atomic<unsigned long long> attr_set{0};  // one bit per device
+    int dev = 0;
+    CCLR_CUDA(cudaGetDevice(&dev));
+    if (dev < 64 && !(attr_set.load() & (1ull << dev))) {  // the complex128 tiles take 67 KB of shared memory
+      CCLR_CUDA(cudaFuncSetAttribute(antisym_apply_tiled<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)((size_t)4 * 32 * 33 * 16)));
+      attr_set |= 1ull << dev;
+    }
+    if (dt == C128)
+      antisym_apply_tiled<double><<<(unsigned)nb, dim3(32, 8), smem, st>>>(o, v, (double2 *)S, (const double2 *)Rab,
+                                                                          (const double2 *)Rij, (const double2 *)R4);
+    else
+      antisym_apply_tiled<float><<<(unsigned)nb, dim3(32, 8), smem, st>>>(o, v, (float2 *)S, (const float2 *)Rab,
+                                                                         (const float2 *)Rij, (const float2 *)R4);
+    count_launch();
+    CCLR_CUDA(cudaGetLastError());
+    return;
+  }
   const int64_t n = (int64_t)o * o * v * v;
   const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 152 * 32));
   if (dt == C128)

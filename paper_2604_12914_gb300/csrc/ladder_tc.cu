@@ -7,17 +7,18 @@
 namespace cclr {
 namespace {
 
-// Packed X as the contraction B operand: B(k = (e<f), n = (i<j)) = X[i,j,e,f].
+// Packed X as the contraction B operand over the pairs q0 .. q0 + nq - 1:
+// B(k = (e<f) - q0, n = (i<j)) = X[i,j,e,f].
 template <int KIND>
 __global__ void pack_x_b(const float2 *X, int o, int v, const int2 *op, const int2 *vp, int64_t Po,
-                         int64_t Pv, int64_t Kp, int seg, typename TcElem<KIND>::T *dst, int64_t ldd) {
+                         int64_t q0, int64_t nq, int64_t Kp, int seg, typename TcElem<KIND>::T *dst, int64_t ldd) {
   const int64_t total = Po * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t n = e / Kp, k = e % Kp;
     float2 val = make_float2(0.f, 0.f);
-    if (k < Pv) {
-      const int2 ij = op[n], ef = vp[k];
+    if (k < nq) {
+      const int2 ij = op[n], ef = vp[q0 + k];
       val = X[(((int64_t)ij.x * o + ij.y) * v + ef.x) * v + ef.y];
     }
     tc_put_b<KIND>(dst + (2 * n) * ldd, dst + (2 * n + 1) * ldd, k, Kp, seg, val);
@@ -46,22 +47,23 @@ __global__ void pack_y_a(const float2 *Y, int o, int v, const int2 *op, const in
 }
 
 // Antisymmetrised packed block of the group, from W[(b - a0) v + f][(a - a0) v + e] = <ab|ef>~:
-//   <ab||ef>~ = W[(b-a0)v+f][(a-a0)v+e] - W[(b-a0)v+e][(a-a0)v+f],  a in group, b > a, e < f.
-// mode 0: A operand rows r = (a,b) pair - p0, K = (e<f)      (forward contraction)
-// mode 1: B operand rows 2(e<f), 2(e<f)+1, K = r              (transpose contraction)
+//   <ab||ef>~ = W[(b-a0)v+f][(a-a0)v+e] - W[(b-a0)v+e][(a-a0)v+f],  a in group, b > a, e < f,
+// for the (e<f) pairs q0 .. q0 + nq - 1 (q below is the pair's offset from q0).
+// mode 0: A operand rows r = (a,b) pair - p0, K = q          (forward contraction)
+// mode 1: B operand rows 2q, 2q+1, K = r                      (transpose contraction)
 template <int KIND>
 __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *vp, int64_t p0,
-                       int64_t np, int64_t Pv, int64_t Kp, int seg, int mode, typename TcElem<KIND>::T *dst,
+                       int64_t np, int64_t q0, int64_t nq, int64_t Kp, int seg, int mode, typename TcElem<KIND>::T *dst,
                        int64_t ldd) {
-  const int64_t total = mode == 0 ? np * Kp : Pv * Kp;
+  const int64_t total = mode == 0 ? np * Kp : nq * Kp;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t r, q;  // r: (a,b) pair within the group; q: (e<f) pair
+    int64_t r, q;  // r: (a,b) pair within the group; q: (e<f) pair offset
     if (mode == 0) { r = e / Kp; q = e % Kp; } else { q = e / Kp; r = e % Kp; }
-    const bool inside = mode == 0 ? (q < Pv) : (r < np);
+    const bool inside = mode == 0 ? (q < nq) : (r < np);
     float2 val = make_float2(0.f, 0.f);
     if (inside) {
-      const int2 ab = vp[p0 + r], ef = vp[q];
+      const int2 ab = vp[p0 + r], ef = vp[q0 + q];
       const int64_t rb = (int64_t)(ab.y - a0) * v, ca = (int64_t)(ab.x - a0) * v;
       const float2 w1 = W[(rb + ef.y) * ldw + ca + ef.x];
       const float2 w2 = W[(rb + ef.x) * ldw + ca + ef.y];
@@ -141,7 +143,7 @@ void ladder_unpack_sig_bench(int o, int v, const void *S, void *out, cudaStream_
   CCLR_CUDA(cudaGetLastError());
 }
 
-void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind) {
+void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind, bool lean) {
   cudaStream_t st = E.st;
   wall_ready_ = false;  // a stored block belongs to the previous L~_vv
   o_ = o; v_ = v; naux_ = naux; seg_ = seg; kind_ = kind;
@@ -160,7 +162,15 @@ void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int s
   if (!op.empty()) CCLR_CUDA(cudaMemcpyAsync(opairs.p, op.data(), op.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   if (!vp.empty()) CCLR_CUDA(cudaMemcpyAsync(vpairs.p, vp.data(), vp.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
   CCLR_CUDA(cudaStreamSynchronize(st));
-  if (!tuned_) tune(E);
+  if (lean) {
+    ga_ = 1;
+    for (int cand : {2, 4, 8, 16, 32, 64})
+      if ((double)v * v * std::min(cand, v) * v * 8 <= 4e9) ga_ = std::min(cand, v);
+    tuned_ = true;
+    tune_log.clear();
+  } else if (!tuned_) {
+    tune(E);
+  }
 }
 
 void LadderTC::tune(Engine &E) {
@@ -212,49 +222,59 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   if (Po == 0 || Pv == 0 || nrhs < 1) return;
   const int64_t vv = (int64_t)v * v, es = tc_esize(kind);
   const int64_t ldL = 2 * tc_kpad(naux_) * seg;
-  const int64_t KpPv = tc_kpad(Pv), ldPv = 2 * KpPv * seg;
   const int ga = std::min(ga_, v);
   const int64_t NR = (int64_t)nrhs;
+  const bool use_wall = store_ && dir > 0;
   // buffers sized for the first (largest) group
   const int64_t maxpairs = pair_start(v, ga);
+  const int64_t kpg = tc_kpad(maxpairs);
+  // the (e<f) pairs in chunks of QC, so that a packed block (rows of the group's pairs, or
+  // rows of the chunk's pairs in the transpose) stays within 2 GiB; the stored ablation keeps one
+  const int64_t cap = 2ll << 30;
+  int64_t QC = use_wall ? Pv : std::max<int64_t>(64, cap / (4 * std::max<int64_t>(kpg, 1) * seg * es) / 8 * 8);
+  QC = std::min(QC, Pv);
+  const int64_t nch = (Pv + QC - 1) / QC, Kc = tc_kpad(QC), ldc = 2 * Kc * seg;
   if (W.bytes < (size_t)vv * ga * v * 8) W.alloc((size_t)vv * ga * v * 8);
   if (LB.bytes < (size_t)2 * ga * v * ldL * es) LB.alloc((size_t)2 * ga * v * ldL * es);
-  const int64_t kpg = tc_kpad(maxpairs);
-  const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldPv * es : (size_t)2 * Pv * (2 * kpg * seg) * es;
+  const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldc * es : (size_t)2 * QC * (2 * kpg * seg) * es;
   if (Wp.bytes < wp_bytes) Wp.alloc(wp_bytes);
-  const size_t xp_bytes = dir > 0 ? (size_t)2 * Po * NR * ldPv * es : (size_t)Po * NR * (2 * kpg * seg) * es;
+  const size_t xp_bytes = dir > 0 ? (size_t)nch * 2 * Po * NR * ldc * es : (size_t)Po * NR * (2 * kpg * seg) * es;
   if (Xp.bytes < xp_bytes) Xp.alloc(xp_bytes);
   if (sig.bytes < (size_t)Po * Pv * NR * 8) sig.alloc((size_t)Po * Pv * NR * 8);
   const int2 *op = opairs.as<int2>(), *vp = vpairs.as<int2>();
   char *LAb = (char *)LA.p, *LBb = (char *)LB.p, *Wpb = (char *)Wp.p, *Xpb = (char *)Xp.p;
+  const size_t xchunk = (size_t)2 * Po * NR * ldc * es;  // bytes of one chunk of packed X
   nform_ = 0;
   if (dir > 0) {
-    for (int64_t r = 0; r < NR; ++r) {
-      void *dst = Xpb + 2 * Po * r * ldPv * es;
-      if (kind == TC_BF16)
-        pack_x_b<TC_BF16><<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
-                                                              (__nv_bfloat16 *)dst, ldPv);
-      else
-        pack_x_b<TC_TF32><<<grid1d(Po * KpPv), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, Pv, KpPv, seg,
-                                                              (float *)dst, ldPv);
-      count_launch();
+    for (int64_t c = 0; c < nch; ++c) {
+      const int64_t q0 = c * QC, nq = std::min(QC, Pv - q0);
+      for (int64_t r = 0; r < NR; ++r) {
+        void *dst = Xpb + c * xchunk + 2 * Po * r * ldc * es;
+        if (kind == TC_BF16)
+          pack_x_b<TC_BF16><<<grid1d(Po * Kc), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, q0, nq, Kc, seg,
+                                                              (__nv_bfloat16 *)dst, ldc);
+        else
+          pack_x_b<TC_TF32><<<grid1d(Po * Kc), 256, 0, st>>>((const float2 *)in[r], o, v, op, vp, Po, q0, nq, Kc, seg,
+                                                              (float *)dst, ldc);
+        count_launch();
+      }
     }
   } else {
     CCLR_CUDA(cudaMemsetAsync(sig.p, 0, (size_t)Po * Pv * NR * 8, st));
   }
-  const bool use_wall = store_ && dir > 0;
   if (use_wall && !wall_ready_) {
-    const size_t wall_bytes = (size_t)Pv * ldPv * es;
+    const size_t wall_bytes = (size_t)Pv * ldc * es;
     if (Wall.bytes != wall_bytes) Wall.alloc(wall_bytes);
   }
   // pack_w launch into dst (rows of ldd elements of the mode's operand type)
-  auto packw = [&](int a0, int64_t p0, int64_t np, int64_t cols, int64_t Kp, int mode, void *dst, int64_t ldd) {
-    const int64_t total = mode == 0 ? np * Kp : Pv * Kp;
+  auto packw = [&](int a0, int64_t p0, int64_t np, int64_t q0, int64_t nq, int64_t cols, int64_t Kp, int mode,
+                   void *dst, int64_t ldd) {
+    const int64_t total = mode == 0 ? np * Kp : nq * Kp;
     if (kind == TC_BF16)
-      pack_w<TC_BF16><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, Kp, seg, mode,
+      pack_w<TC_BF16><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, q0, nq, Kp, seg, mode,
                                                      (__nv_bfloat16 *)dst, ldd);
     else
-      pack_w<TC_TF32><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, Pv, Kp, seg, mode,
+      pack_w<TC_TF32><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, q0, nq, Kp, seg, mode,
                                                      (float *)dst, ldd);
     count_launch();
   };
@@ -277,15 +297,18 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_ + 1], st));
     ++nform_;
     if (use_wall) {  // pack the group's rows into the stored block; contract once afterwards
-      packw(a0, p0, np, cols, KpPv, 0, (char *)Wall.p + p0 * ldPv * es, ldPv);
+      packw(a0, p0, np, 0, Pv, cols, Kc, 0, (char *)Wall.p + p0 * ldc * es, ldc);
     } else if (dir > 0) {
-      packw(a0, p0, np, cols, KpPv, 0, Wpb, ldPv);
-      // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f]  for the group's pairs, all RHS
-      tc_gemm_seg(Wpb, ldPv, Xpb, ldPv, np, 2 * Po * NR, ldPv / seg, seg, kind,
-                  sig.as<float>() + 2 * p0 * Po * NR, 2 * Po * NR, zc(1.0), false, st);
+      // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f] for the group's pairs, all RHS, summed
+      // over the chunks of (e<f)
+      for (int64_t c = 0; c < nch; ++c) {
+        const int64_t q0 = c * QC, nq = std::min(QC, Pv - q0);
+        packw(a0, p0, np, q0, nq, cols, Kc, 0, Wpb, ldc);
+        tc_gemm_seg(Wpb, ldc, Xpb + c * xchunk, ldc, np, 2 * Po * NR, ldc / seg, seg, kind,
+                    sig.as<float>() + 2 * p0 * Po * NR, 2 * Po * NR, zc(1.0), c > 0, st);
+      }
     } else {
       const int64_t kg = tc_kpad(np), ldg = 2 * kg * seg;
-      packw(a0, p0, np, cols, kg, 1, Wpb, ldg);
       for (int64_t r = 0; r < NR; ++r) {
         void *dst = Xpb + Po * r * ldg * es;
         if (kind == TC_BF16)
@@ -296,16 +319,20 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
                                                               (float *)dst, ldg);
         count_launch();
       }
-      // Z[(r, ij)][(ef)] += sum_{(ab) in group} Y'_r[(ij)][(ab)] <ab||ef>~
-      tc_gemm_seg(Xpb, ldg, Wpb, ldg, Po * NR, 2 * Pv, ldg / seg, seg, kind, sig.as<float>(), 2 * Pv, zc(1.0), true,
-                  st);
+      // Z[(r, ij)][(ef)] += sum_{(ab) in group} Y'_r[(ij)][(ab)] <ab||ef>~, a chunk of (e<f) at a time
+      for (int64_t c = 0; c < nch; ++c) {
+        const int64_t q0 = c * QC, nq = std::min(QC, Pv - q0);
+        packw(a0, p0, np, q0, nq, cols, kg, 1, Wpb, ldg);
+        tc_gemm_seg(Xpb, ldg, Wpb, ldg, Po * NR, 2 * nq, ldg / seg, seg, kind, sig.as<float>() + 2 * q0, 2 * Pv,
+                    zc(1.0), true, st);
+      }
     }
     CCLR_CUDA(cudaGetLastError());
   }
   if (use_wall) {
     wall_ready_ = true;
-    // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f] for every pair at once
-    tc_gemm_seg(Wall.p, ldPv, Xpb, ldPv, Pv, 2 * Po * NR, ldPv / seg, seg, kind, sig.as<float>(), 2 * Po * NR, zc(1.0),
+    // sigT[(ab)][(r, ij)] = sum_{e<f} <ab||ef>~ X_r[i,j,e,f] for every pair at once (one chunk)
+    tc_gemm_seg(Wall.p, ldc, Xpb, ldc, Pv, 2 * Po * NR, ldc / seg, seg, kind, sig.as<float>(), 2 * Po * NR, zc(1.0),
                 false, st);
     CCLR_CUDA(cudaGetLastError());
   }

@@ -28,7 +28,8 @@ class LadderTC {
   }
   // Lvv: complex64 [naux][v][v] (T1-dressed).  seg = 1 (one pass) or 3 (split); kind = TC_TF32
   // or TC_BF16 (operand type of the tensor-core GEMMs).
-  void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind);
+  // lean: skip the group-size tuner and take the largest candidate whose block fits in 4 GB
+  void prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int seg, int kind, bool lean = false);
   bool ready(int seg, int kind) const { return seg_ == seg && kind_ == kind && LA.p != nullptr; }
   // dir +1: out[r] += alpha * ladder(in[r]);  dir -1: out[r] += alpha * ladder^T(in[r]),
   // r = 0..nrhs-1, all complex64 [o][o][v][v].  Each <ab||ef>~ group block is formed once
@@ -50,6 +51,10 @@ class LadderTC {
     if (!on) { Wall.release(); wall_ready_ = false; }
   }
   bool stored() const { return store_; }
+  // frees the per-product buffers and the prepared operands (prepare() is needed again)
+  void release() {
+    W.release(); Wp.release(); Xp.release(); sig.release(); LB.release(); LA.release();
+  }
   size_t stored_bytes() const { return Wall.bytes; }
   std::vector<std::pair<int, float>> tune_log;
 

@@ -241,6 +241,7 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
     CCLR_CUDA(cudaStreamSynchronize(st));
   }
   E.tc_mode = tc_saved;
+  if (lean) E.release_ws();  // the builds' permuted operands are not needed by the products
   for (int k = 0; k < 3; ++k)  // a ladder prepared from this buffer is stale
     if (ltc_src[k] == out.t[K_LVV].p) ltc_src[k] = nullptr;
   bump_state_epoch();  // and so is any captured program that read the set
@@ -338,12 +339,24 @@ void Model::release_fp64() {
   lcc.release();
 }
 
+void Model::release_fp64_inputs() {
+  ensure_src64();
+  oovv_packed();
+  Loo0.release(); Lov0.release(); Lvo0.release(); Lvv0.release();
+  fp64_gone = true;
+}
+
 // The FP64 mode reads intermediates built in FP64.  The complex64 modes read the rounding of
 // those when they exist, else a set built in FP32 on the CUDA cores (this GPU's FP64 rate makes
 // the FP64 build of the o^3 v^3 and o v^3 naux terms take minutes at o=56, v=480).
 const CstSet &Model::cst_for(int p) {
   if (p == 0) {
-    if (!c128.valid) build_set(t1.p, t2.p, c128, C128);
+    if (!c128.valid) {
+      if (fp64_gone)
+        throw Error(6, "FP64 products are unavailable: this budgeted context freed its FP64 inputs when 3xTF32 "
+                       "refinement was set");
+      build_set(t1.p, t2.p, c128, C128);
+    }
     return c128;
   }
   if (!c64.valid) {
@@ -414,8 +427,14 @@ void Model::ladder(int dir, const CstSet &C, zc alpha, const std::vector<Tens> &
   const int nr = (int)in.size();
   if (dt == C64 && E.tc_mode) {
     const int k = E.tc_mode - 1, seg = E.tc_mode == 1 ? 1 : 3, kind = E.tc_mode == 3 ? TC_BF16 : TC_TF32;
+    if (lean)  // a budgeted context keeps one tensor-core ladder's buffers at a time
+      for (int q = 0; q < 3; ++q)
+        if (q != k && ltc_src[q]) {
+          ltc[q].release();
+          ltc_src[q] = nullptr;
+        }
     if (!ltc[k].ready(seg, kind) || ltc_src[k] != C.t[K_LVV].p) {
-      ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg, kind);
+      ltc[k].prepare(E, C.t[K_LVV], o, v, naux, seg, kind, lean);
       ltc_src[k] = C.t[K_LVV].p;
     }
     std::vector<const void *> ip(nr);
@@ -656,6 +675,7 @@ void Model::apply_batch(int dir, const CstSet &C, int nr, const void *const *x1,
     throw;
   }
   tc_set_autotune(false);
+  if (lean) E.release_ws();  // a budgeted context does not keep the product's staging
   CCLR_CUDA(cudaEventRecord(tm.ev[3], st));
   CCLR_CUDA(cudaEventSynchronize(tm.ev[3]));
   float tot = 0.f;

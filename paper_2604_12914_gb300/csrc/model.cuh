@@ -105,6 +105,7 @@ class Model {
   // or constants rebuilt since, is captured once and then replayed by cudaGraphLaunch.
   bool graphs = false;
   bool autotune = true;  // tensor-core GEMM shapes tuned on their first (eager) use
+  bool lean = false;     // budgeted context: transient buffers are freed after use
   std::vector<GraphEntry> gcache;
   std::vector<GraphEntry> warm;  // recent eager calls (key, epoch after the call); no exec
   int graph_launches = 0, graph_captures = 0;
@@ -128,6 +129,10 @@ class Model {
   // frees everything the FP64 products hold (the complex128 set, temporaries and the CUDA-core
   // ladder's blocks); an FP64 product afterwards rebuilds them
   void release_fp64();
+  // lean memory (a context with an HBM budget): also frees the undressed complex128 Cholesky
+  // blocks once their complex64 copies exist; FP64 products are refused afterwards
+  bool fp64_gone = false;
+  void release_fp64_inputs();
 
   // sigma (dir = +1) or sigma^T (dir = -1) on device buffers of the given dtype.
   void apply(int dir, const CstSet &C, const void *x1, const void *x2, void *s1, void *s2);

@@ -102,8 +102,9 @@ inline View2 view1(int64_t stride) {
   return v;
 }
 
-// Complex K padded so that every operand row is a whole number of 16-byte units.
-inline int64_t tc_kpad(int64_t K) { return (K + 1) / 2 * 2; }
+// Complex K padded so that every operand row is a whole number of 16-byte units for every
+// operand type and split (2 K seg elements of 2 or 4 bytes: K a multiple of 4).
+inline int64_t tc_kpad(int64_t K) { return (K + 3) / 4 * 4; }
 
 // seg = 1 (one pass) or 3 (split); kind = TC_TF32 or TC_BF16.  dst rows have ldd elements of
 // the operand type (>= 2*tc_kpad(K)*seg).
