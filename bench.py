@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-hbm", action="store_true")
     ap.add_argument("--no-c3", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--no-ccsd", action="store_true")
+    ap.add_argument("--ccsd-config", default="C2")
+    ap.add_argument("--ccsd-prec", default="3xtf32")
     ap.add_argument("--solve-large", default="",
                     help="only run a large mixed-precision solve and print its JSON: "
                          "'C3' (3 components x {0, +-0.02, +-0.0428, +-0.0656} = 21 systems in one block) "
@@ -465,6 +468,39 @@ def solve_large(cfg, scale):
     return out
 
 
+def ground_state(cfg, scale, prec, tol):
+    """Ground-state CCSD on the device: Omega(T) = 0 from the first-order guess by quasi-Newton
+    steps with DIIS, each residual from two intermediate builds and two sigma products (exact
+    two-point Gauss-Legendre rule); wall time, residuals formed, energy, and the FP64 residual
+    norm of the final amplitudes (an independent check that the mixed-precision solve met its
+    tolerance)."""
+    import numpy as np
+    from paper_2604_12914_gb300 import binding
+    from paper_2604_12914_gb300.inputs import make_config
+    s = make_config(cfg, scale=scale)
+    t0 = time.perf_counter()
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=prec)
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, Cholesky vectors scaled by {scale}",
+           "init_seconds": time.perf_counter() - t0, "residual_products": prec, "tol": tol}
+    t0 = time.perf_counter()
+    e, rn, its = ctx.cc_lr_ccsd(tol=tol, max_iterations=80, allow_noconv=True)
+    el = time.perf_counter() - t0
+    out.update({"seconds": el, "residuals": its, "seconds_per_residual": el / max(its, 1),
+                "residual_norm": rn, "converged": rn < tol, "energy": [e.real, e.imag]})
+    t1, t2 = ctx.cc_lr_get_t()
+    t0 = time.perf_counter()
+    r1, r2, e64 = ctx.cc_lr_ccsd_residual(t1, t2, prec="fp64")
+    out["fp64_residual_seconds"] = time.perf_counter() - t0
+    iu = np.triu_indices(s.o, 1)
+    ju = np.triu_indices(s.v, 1)
+    out["fp64_residual_norm"] = float(np.sqrt(np.sum(np.abs(r1) ** 2) +
+                                              np.sum(np.abs(r2[iu][:, ju[0], ju[1]]) ** 2)))
+    used, peak, _ = ctx.cc_lr_memory()
+    out["device_memory_peak_gb"] = peak / 1e9
+    ctx.close()
+    return out
+
+
 def cublas_tf32_tflops():
     """cuBLAS TF32 GEMM 8192^3 (torch.matmul on FP32 with TF32 allowed), best of 5, CUDA events."""
     import torch
@@ -682,6 +718,9 @@ def run_cclr(args):
         c3 = packed_batch("C3", 21, ["tf32", "3xtf32"])
     if rank == 0 and not args.no_c5:
         c5 = packed_batch("C5", 1, ["tf32", "bf16x3"])
+    gs = None
+    if rank == 0 and not args.no_ccsd:
+        gs = ground_state(args.ccsd_config, 0.05, args.ccsd_prec, 1e-5)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,
@@ -726,6 +765,8 @@ def run_cclr(args):
             out["c3_batched"] = c3
         if c5 is not None:
             out["c5"] = c5
+        if gs is not None:
+            out["ground_state_ccsd"] = gs
         if cpu is not None:
             out["cpu_baseline"] = cpu
             out["cpu_c1_whole_sigma"] = cpu_c1

@@ -170,6 +170,37 @@ cclr_status cc_lr_solve_damped(cclr_ctx *ctx, int nomega, const double *omegas, 
 /* Ground-state Lambda (solved if needed) copied out: lam1 [o][v], lam2 [o][o][v][v]. */
 cclr_status cc_lr_lambda(cclr_ctx *ctx, double tol, double *lam1, double *lam2);
 
+/* Ground-state CCSD on the device (Sec. 2.2): the amplitude equations
+ * Omega_mu(T) = <mu|e^{-T} H e^{T}|Phi_0> = 0 and the correlation energy
+ * E(T) = <Phi_0|e^{-T} H e^{T}|Phi_0> - E_ref = sum_ia f_ia t_ia + 1/4 sum <ij||ab> t_ijab
+ * + 1/2 sum <ij||ab> t_ia t_jb (f = diag(eps), so f_ia = 0).
+ * The residual is formed from the Jacobian products the context already runs: Omega(sT) is a
+ * polynomial of degree four in s with d/ds Omega(sT) = A(sT) T, so
+ * Omega(T) = Omega(0) + 1/2 [A(s1 T) T + A(s2 T) T], s1,2 = 1/2 -+ 1/(2 sqrt 3), exactly
+ * (two-point Gauss-Legendre quadrature of a cubic), with Omega(0) = <mu|H|Phi_0> (zero singles,
+ * <ab||ij> doubles).  Each residual costs two builds of the intermediates and two sigma
+ * products.
+ * prec: the arithmetic of those products (a cclr_prec; -1 = the context's precision).  FP64
+ * gives the exact residual; the tensor-core modes give it to their product accuracy.
+ *
+ * cc_lr_ccsd_residual: Omega(T) and E(T) at the given amplitudes (t1 [o][v], t2 [o][o][v][v]
+ * antisymmetric in (i,j) and (a,b); r1, r2 the same shapes; energy NULL or 2 doubles, complex).
+ * The context's own amplitudes and intermediates are unchanged.
+ *
+ * cc_lr_ccsd: solves Omega(T) = 0 starting from the context's amplitudes by quasi-Newton steps
+ * T <- T - Omega(T) / D (D the orbital-energy differences) with Pulay (DIIS) extrapolation over
+ * the last diis_depth steps (2..16), until the norm of the residual over unique amplitudes
+ * (singles, i<j a<b doubles) is below tol, or max_iterations residuals were formed.  The context
+ * then holds the final T and rebuilds or resets everything that depends on it (intermediates,
+ * preconditioner, Lambda, eta).  energy (NULL or 2 doubles): E at the final T; res_norm: the last
+ * residual norm; iterations: residuals formed.  CCLR_ENOCONV if the tolerance was not met (the
+ * context then holds the last iterate).  CCLR_EUNSUPPORTED for FP64 products in a budgeted
+ * context that released its FP64 inputs. */
+cclr_status cc_lr_ccsd_residual(cclr_ctx *ctx, int prec, const double *t1, const double *t2,
+                                double *r1, double *r2, double *energy);
+cclr_status cc_lr_ccsd(cclr_ctx *ctx, int prec, double tol, int max_iterations, int diis_depth,
+                       double *energy, double *res_norm, int *iterations);
+
 /* The amplitudes the context holds (useful when t2 was NULL at init). */
 cclr_status cc_lr_get_t(cclr_ctx *ctx, double *t1, double *t2);
 

@@ -23,7 +23,7 @@ PREC = {"fp64": CCLR_FP64, "tf32": CCLR_C64_TF32, "3xtf32": CCLR_C64_3XTF32, "fp
 
 EXPORTS = ["cc_lr_init", "cc_lr_sigma", "cc_lr_sigma_T", "cc_lr_sigma_packed", "cc_lr_xi", "cc_lr_solve_x", "cc_lr_solve",
            "cc_lr_solve_damped", "cc_lr_solve_left", "cc_lr_solve_alpha_tol", "cc_lr_eta",
-           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
+           "cc_lr_lambda", "cc_lr_get_t", "cc_lr_ccsd_residual", "cc_lr_ccsd", "cc_lr_set_precision", "cc_lr_set_refinement", "cc_lr_set_graphs",
            "cc_lr_graph_stats", "cc_lr_ladder_tuning", "cc_lr_set_ladder_storage", "cc_lr_set_solver",
            "cc_lr_last_timings", "cc_lr_memory", "cc_lr_set_autotune", "cc_lr_gemm_tuning",
            "cc_lr_free", "cc_lr_strerror", "cc_lr_last_error", "cc_lr_launch_count"]
@@ -71,6 +71,8 @@ def load(path: str = LIB_PATH):
         "cc_lr_solve_alpha_tol": [P, I, P, I, P, D, I, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(cclr_stats)],
         "cc_lr_lambda": [P, D, P, P],
         "cc_lr_get_t": [P, P, P],
+        "cc_lr_ccsd_residual": [P, I, P, P, P, P, P],
+        "cc_lr_ccsd": [P, I, D, I, I, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
         "cc_lr_set_precision": [P, I],
         "cc_lr_set_solver": [P, I, I, I],
         "cc_lr_set_refinement": [P, I],
@@ -285,6 +287,28 @@ class Context:
         t2 = self._out((o, o, v, v))
         _check(load().cc_lr_get_t(self._h, _ptr(t1), _ptr(t2)))
         return t1, t2
+
+    def cc_lr_ccsd_residual(self, t1, t2, prec=-1):
+        """Omega(T) (r1, r2) and the correlation energy E(T) at the given amplitudes."""
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        t1, t2 = self._in(t1), self._in(t2)
+        r1 = self._out(tuple(t1.shape))
+        r2 = self._out(tuple(t2.shape))
+        e = np.zeros(2)
+        _check(load().cc_lr_ccsd_residual(self._h, p, _ptr(t1), _ptr(t2), _ptr(r1), _ptr(r2), e.ctypes.data))
+        return r1, r2, complex(e[0], e[1])
+
+    def cc_lr_ccsd(self, tol=1e-9, max_iterations=60, diis_depth=8, prec=-1, allow_noconv=False):
+        """Solve the ground-state CCSD equations from the context's amplitudes; the context then
+        holds the converged T.  Returns (energy, residual norm, iterations)."""
+        p = PREC[prec] if isinstance(prec, str) else int(prec)
+        e = np.zeros(2)
+        rn = ctypes.c_double(0.0)
+        its = ctypes.c_int(0)
+        _check(load().cc_lr_ccsd(self._h, p, float(tol), int(max_iterations), int(diis_depth), e.ctypes.data,
+                                 ctypes.byref(rn), ctypes.byref(its)),
+               allow=(CCLR_ENOCONV,) if allow_noconv else ())
+        return complex(e[0], e[1]), rn.value, its.value
 
     def cc_lr_set_precision(self, prec):
         p = PREC[prec] if isinstance(prec, str) else int(prec)

@@ -757,6 +757,161 @@ struct cclr_ctx {
     pack_from(fullA.b.p, C128, out);
   }
 
+  // ---- ground-state CCSD: the amplitude equations Omega(T) = 0 and the energy (Sec. 2.2) ----
+  CstSet gs;  // intermediates at s T, s a quadrature node of the residual (scratch)
+
+  // the arithmetic of a ground-state product: a cclr_prec, or -1 for the context's own
+  int gs_prec(int p) const {
+    if (p < 0) p = M->prec;
+    if (p > 4) throw Error(CCLR_EINVAL, "unknown precision mode");
+    if (p == CCLR_FP64 && M->fp64_gone)
+      throw Error(CCLR_EUNSUPPORTED, "FP64 products are unavailable: this budgeted context freed its FP64 inputs");
+    return p;
+  }
+
+  // Omega(T), packed, at the packed amplitudes tp, with the sigma products in precision p.
+  // CCSD is at most quartic in T, so Omega(sT) is a polynomial of degree four in s, and its
+  // derivative d/ds Omega(sT) = A(sT) T is the Jacobian product of the sigma program with the
+  // intermediates built at sT.  Hence Omega(T) = Omega(0) + int_0^1 A(sT) T ds, and the
+  // two-point Gauss-Legendre rule on [0, 1] (nodes 1/2 -+ 1/(2 sqrt 3), weights 1/2) integrates
+  // the cubic integrand exactly.  Omega(0) = <mu|H|Phi_0> is f_ai (zero for the canonical Fock
+  // matrix diag(eps)) and <ab||ij>, the complex conjugate of <ij||ab> for Hermitian L^P.
+  void ccsd_residual(int p, const void *tp, void *r) {
+    alloc_full(fullA);
+    alloc_full(fullB);
+    AVec sv;
+    alloc_vec(sv);
+    unpack_to(tp, fullA.b.p, C128);
+    CCLR_CUDA(cudaMemsetAsync(r, 0, (size_t)n1 * 16, st));
+    vec_conj(n2p, M->oovv_packed(), (char *)r + n1 * 16, st);
+    const Tens TA = make_tens(fullA.b.p, C128, {nfull()}), TB = make_tens(fullB.b.p, C128, {nfull()});
+    const double h = 0.5 / std::sqrt(3.0);
+    const int saved = M->prec;
+    try {
+      for (double s : {0.5 - h, 0.5 + h}) {
+        M->E.permute(zc(s), TA, "a", TB, "a", false);
+        M->build_set(fullB.p1(), fullB.p2(n1), gs, p == CCLR_FP64 ? C128 : C64);
+        M->prec = p;
+        op(+1, tp, sv.b.p, &gs);
+        M->prec = saved;
+        axpy(zd(0.5), sv.b.p, r);
+      }
+    } catch (...) {
+      M->prec = saved;
+      throw;
+    }
+  }
+
+  // E(T) = sum_ia f_ia t_ia + 1/4 sum <ij||ab> t_ijab + 1/2 sum <ij||ab> t_ia t_jb
+  //      = sum over i<j, a<b of <ij||ab> tau_ijab (f_ia = 0), packed amplitudes tp
+  zd ccsd_energy(const void *tp) {
+    DevBuf tau((size_t)std::max<int64_t>(1, n2p) * 16);
+    tau_packed(o, v, tp, (const char *)tp + n1 * 16, tau.p, st);
+    double2 *part = M->E.dot_scratch();
+    double2 *res = M->E.dot_results();
+    vec_dot(C128, n2p, M->oovv_packed(), tau.p, 0, part, res, 0, st);
+    double2 e;
+    CCLR_CUDA(cudaMemcpyAsync(&e, res, sizeof(e), cudaMemcpyDeviceToHost, st));
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return zd(e.x, e.y);
+  }
+
+  // the context's amplitudes (M->t1, M->t2, full layouts) packed into out
+  void pack_t(void *out) {
+    CCLR_CUDA(cudaMemcpyAsync(out, M->t1.p, (size_t)n1 * 16, cudaMemcpyDeviceToDevice, st));
+    pack_doubles(C128, C128, o, v, M->t2.p, (char *)out + n1 * 16, st);
+  }
+
+  // New amplitudes (packed tp): every quantity that depends on T is rebuilt (intermediates in the
+  // working precision, the preconditioner) or dropped (Lambda, eta, the stencil and one-body sets).
+  void set_amplitudes(const void *tp) {
+    CCLR_CUDA(cudaMemcpyAsync(M->t1.p, tp, (size_t)n1 * 16, cudaMemcpyDeviceToDevice, st));
+    unpack_doubles(C128, C128, o, v, (const char *)tp + n1 * 16, M->t2.p, zc(1), false, st);
+    M->release_set(gs);
+    M->release_set(shift);
+    M->release_set(shift64);
+    for (auto &b : onebody) M->release_set(b);
+    for (int k = 0; k < 3; ++k) eta_ok[k] = false;
+    have_lambda = false;
+    M->release_set(M->c128);
+    M->release_set(M->c64);
+    M->clear_graphs();
+    M->cst_for(M->prec);
+    M->build_diagonal();
+    CCLR_CUDA(cudaStreamSynchronize(st));
+  }
+
+  // Quasi-Newton iterations T <- T - Omega(T) / D, D the orbital-energy differences (the
+  // diagonal of the T = 0 Jacobian), with Pulay extrapolation over the last `depth` steps
+  // (error vectors Omega / D).  Starts from the context's amplitudes; returns the final norm of
+  // the packed residual and leaves the final amplitudes packed in tv.
+  double ccsd_solve(int p, double tol, int maxit, int depth, AVec &tv, int *its) {
+    depth = std::max(2, std::min(depth, 16));
+    alloc_vec(tv);
+    pack_t(tv.b.p);
+    {  // D from diag(eps): Foo = diag(eps_occ), Fvv = diag(eps_vir)
+      DevBuf f((size_t)(o * o + v * v) * 16);
+      CCLR_CUDA(cudaMemsetAsync(f.p, 0, f.bytes, st));
+      void *foo = f.p, *fvv = (char *)f.p + (size_t)o * o * 16;
+      set_diag(o, M->eps.as<double>(), foo, st);
+      set_diag(v, M->eps.as<double>() + o, fvv, st);
+      build_diag(o, v, foo, fvv, M->D1.as<double>(), M->D2.as<double>(), st);
+      CCLR_CUDA(cudaStreamSynchronize(st));
+    }
+    std::vector<AVec> X(depth), Er(depth);
+    AVec r;
+    alloc_vec(r);
+    std::vector<zd> B((size_t)depth * depth);
+    int nh = 0, head = 0;
+    double rn = 1e300;
+    for (int it = 0; it < maxit; ++it) {
+      ccsd_residual(p, tv.b.p, r.b.p);
+      rn = norm(r.b.p);
+      if (its) ++*its;
+      if (verbose()) std::fprintf(stderr, "cclr ccsd it=%d |Omega|=%.3e prec=%d\n", it, rn, p);
+      if (!(rn == rn)) throw Error(3, "ground-state iteration produced a NaN residual");
+      if (rn < tol) break;
+      const int k = head;
+      head = (head + 1) % depth;
+      nh = std::min(nh + 1, depth);
+      alloc_vec(X[k]);
+      alloc_vec(Er[k]);
+      precond(zd(0), r.b.p, Er[k].b.p);  // Omega / D
+      scal(zd(-1), Er[k].b.p);           // the Jacobi step -Omega / D
+      copy(tv.b.p, X[k].b.p);
+      axpy(zd(1), Er[k].b.p, X[k].b.p);
+      for (int l = 0; l < depth; ++l) {
+        if (!(nh == depth || l < nh)) continue;
+        const zd d = dot(Er[k].b.p, Er[l].b.p, 1);
+        B[(size_t)k * depth + l] = d;
+        B[(size_t)l * depth + k] = std::conj(d);
+      }
+      if (nh < 2) {
+        copy(X[k].b.p, tv.b.p);
+        continue;
+      }
+      std::vector<int> idx;
+      for (int l = 0; l < depth; ++l)
+        if (nh == depth || l < nh) idx.push_back(l);
+      const int m = (int)idx.size();
+      double sc = 0.0;
+      for (int a : idx) sc = std::max(sc, std::abs(B[(size_t)a * depth + a]));
+      if (sc <= 0) sc = 1.0;
+      std::vector<zd> Am((size_t)(m + 1) * (m + 1)), rhs(m + 1, 0.0);
+      for (int a = 0; a < m; ++a) {
+        for (int c2 = 0; c2 < m; ++c2) Am[(size_t)a * (m + 1) + c2] = B[(size_t)idx[a] * depth + idx[c2]] / sc;
+        Am[(size_t)a * (m + 1) + m] = 1.0;
+        Am[(size_t)m * (m + 1) + a] = 1.0;
+      }
+      rhs[m] = 1.0;
+      const std::vector<zd> cf = solve_small(Am, rhs, m + 1);
+      CCLR_CUDA(cudaMemsetAsync(tv.b.p, 0, (size_t)ntot() * 16, st));
+      for (int a = 0; a < m; ++a) axpy(cf[a], X[idx[a]].b.p, tv.b.p);
+    }
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    return rn;
+  }
+
   // eta0 = dE/dT = [ sum_jb <ij||ab> t_jb ; <ij||ab> ] (canonical Fock: f_ia = 0), packed
   void eta0(void *out) {
     const void *oovv = M->oovv_packed();
@@ -964,6 +1119,9 @@ cclr_status cc_lr_init(cclr_ctx **ctx, int o, int v, int naux, const double *eps
     c->M.reset(new Model(o, v, naux, c->st));
     c->M->prec = prec;
     c->M->lean = hbm_budget_bytes > 0;
+    // prepared constant operands of the tensor-core contractions are kept (up to 8 GB) unless the
+    // context has a budget
+    c->M->E.prep_cache_cap = c->M->lean ? 0 : (size_t)8 << 30;
     c->M->upload_inputs(eps, L, mu, t1, t2, device_ptrs);
     c->M->cst_for(prec);      // intermediates in the working precision
     c->M->build_diagonal();
@@ -1397,6 +1555,57 @@ cclr_status cc_lr_solve(cclr_ctx *c, int nomega, const double *omegas, int ncomp
 cclr_status cc_lr_solve_damped(cclr_ctx *c, int nomega, const double *omegas, double gamma, int ncomp,
                                const int *comps, double tol, int diis_depth, double *alpha, cclr_stats *stats) {
   return solve_alpha(c, nomega, omegas, gamma, ncomp, comps, tol, diis_depth, alpha, stats);
+}
+
+cclr_status cc_lr_ccsd_residual(cclr_ctx *c, int prec, const double *t1, const double *t2, double *r1,
+                                double *r2, double *energy) {
+  if (!c || !t1 || !t2 || !r1 || !r2) return (cclr_status)fail(CCLR_EINVAL, "bad ccsd_residual arguments");
+  return (cclr_status)guarded_ctx(c, [&] {
+    const int p = c->gs_prec(prec);
+    c->alloc_full(c->fullB);
+    AVec tv, rv;
+    c->alloc_vec(tv);
+    c->alloc_vec(rv);
+    to_dev(c, t1, c->fullB.p1(), (size_t)c->n1 * 16);
+    to_dev(c, t2, c->fullB.p2(c->n1), (size_t)c->n2 * 16);
+    c->pack_from(c->fullB.b.p, C128, tv.b.p);
+    c->ccsd_residual(p, tv.b.p, rv.b.p);
+    if (energy) {
+      const zd e = c->ccsd_energy(tv.b.p);
+      energy[0] = e.real();
+      energy[1] = e.imag();
+    }
+    c->unpack_to(rv.b.p, c->fullA.b.p, C128);
+    from_dev(c, c->fullA.p1(), r1, (size_t)c->n1 * 16);
+    from_dev(c, c->fullA.p2(c->n1), r2, (size_t)c->n2 * 16);
+    CCLR_CUDA(cudaStreamSynchronize(c->st));
+    c->M->release_set(c->gs);
+    if (c->M->lean) c->release_scratch();
+  });
+}
+
+cclr_status cc_lr_ccsd(cclr_ctx *c, int prec, double tol, int max_iterations, int diis_depth, double *energy,
+                       double *res_norm, int *iterations) {
+  if (!c || !(tol > 0.0) || max_iterations < 1) return (cclr_status)fail(CCLR_EINVAL, "bad ccsd arguments");
+  bool conv = false;
+  int st = guarded_ctx(c, [&] {
+    const int p = c->gs_prec(prec);
+    AVec tv;
+    int its = 0;
+    const double rn = c->ccsd_solve(p, tol, max_iterations, diis_depth, tv, &its);
+    conv = rn < tol;
+    c->set_amplitudes(tv.b.p);
+    if (energy) {
+      const zd e = c->ccsd_energy(tv.b.p);
+      energy[0] = e.real();
+      energy[1] = e.imag();
+    }
+    if (res_norm) *res_norm = rn;
+    if (iterations) *iterations = its;
+    if (c->M->lean) c->release_scratch();
+  });
+  if (st == CCLR_OK && !conv) return (cclr_status)fail(CCLR_ENOCONV, "ground-state CCSD did not reach the tolerance");
+  return (cclr_status)st;
 }
 
 cclr_status cc_lr_get_t(cclr_ctx *c, double *t1, double *t2) {

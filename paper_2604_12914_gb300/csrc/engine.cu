@@ -229,6 +229,73 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
   if (K == 0) return;
   const size_t es = dt_size(dt);
 
+  // An o x o (at most 64 x 64) matrix acting on one index of a large tensor, X[p][k][q] -> Y[p][j][q]
+  // with q unit-stride in both: one pass over X and Y on the CUDA cores (memory-bound; a GEMM tile
+  // would be mostly padding in k and j and would stage X twice).
+  if (bat.empty() && Km.size() == 1 && (Mm.size() == 1 || Nm.size() == 1) && !tc_force) {
+    for (int side = 0; side < 2; ++side) {
+      const Tens &Sm = side == 0 ? A : B, &Xt = side == 0 ? B : A;
+      const std::string &ms = side == 0 ? ma : mb, &mx = side == 0 ? mb : ma;
+      const std::string &jg = side == 0 ? Mm : Nm;
+      if (jg.size() != 1 || ms.size() != 2) continue;
+      const char k = Km[0], j = jg[0];
+      const int pk = mode_pos(mx, k), pj = mode_pos(mc, j);
+      const std::string prefX = mx.substr(0, pk), sufX = mx.substr(pk + 1);
+      const std::string prefC = mc.substr(0, pj), sufC = mc.substr(pj + 1);
+      if (prefX != prefC || sufX != sufC) continue;
+      const int64_t Kd = Xt.dim[pk], Jd = C.dim[pj];
+      if (Kd > 64 || Jd > 64) continue;
+      int64_t P1, sXp, P2, sYp, Q1, sXq, Q2, sYq;
+      if (!group_view(Xt, mx, prefX, P1, sXp) || !group_view(C, mc, prefC, P2, sYp)) continue;
+      if (!group_view(Xt, mx, sufX, Q1, sXq) || !group_view(C, mc, sufC, Q2, sYq)) continue;
+      if (Q1 < 32 || (sXq != 1 && Q1 > 1) || (sYq != 1 && Q2 > 1)) continue;
+      if (trace_on())
+        std::fprintf(stderr, "cclr contract smallk %s,%s->%s P=%lld K=%lld J=%lld Q=%lld dt=%d\n", ma.c_str(),
+                     mb.c_str(), mc.c_str(), (long long)P1, (long long)Kd, (long long)Jd, (long long)Q1, dt);
+      contract_smallk(dt, P1, (int)Kd, (int)Jd, Q1, Sm.p, Sm.str[mode_pos(ms, k)], Sm.str[mode_pos(ms, j)], Xt.p, sXp,
+                      Xt.str[pk], C.p, sYp, C.str[pj], alpha, st);
+      return;
+    }
+  }
+
+  // A tensor of rank <= 4 contracted with a vector over some of its modes, y[r] = sum_c B[r, c] s[c]
+  // (the small operand has no output mode): one coalesced pass over B (memory-bound).
+  if (bat.empty() && (Mm.empty() || Nm.empty()) && !tc_force) {
+    const bool small_a = Mm.empty();
+    const Tens &Bt = small_a ? B : A, &Sv = small_a ? A : B;
+    const std::string &mbig = small_a ? mb : ma, &msm = small_a ? ma : mb;
+    bool ok = Bt.rank <= 4 && Bt.numel() >= (1 << 16);
+    int64_t expect = 1;
+    for (int q = Bt.rank - 1; q >= 0 && ok; --q) {  // contiguous row-major
+      ok = Bt.str[q] == expect || Bt.dim[q] == 1;
+      expect *= Bt.dim[q];
+    }
+    if (ok) {
+      int64_t d[4] = {1, 1, 1, 1}, ss[4] = {0, 0, 0, 0}, ys[4] = {0, 0, 0, 0};
+      int rmask = 0;
+      const int off = 4 - Bt.rank;
+      for (int q = 0; q < Bt.rank; ++q) {
+        const char mch = mbig[q];
+        d[off + q] = Bt.dim[q];
+        const int pc = mode_pos(mc, mch);
+        if (pc >= 0) {
+          rmask |= 1 << (off + q);
+          ys[off + q] = C.str[pc];
+        } else {
+          ss[off + q] = Sv.str[mode_pos(msm, mch)];
+        }
+      }
+      if (!((rmask & 4) && (rmask & 8))) {
+        if (trace_on())
+          std::fprintf(stderr, "cclr contract gemv %s,%s->%s dims %lld %lld %lld %lld rmask %d dt=%d\n", ma.c_str(),
+                       mb.c_str(), mc.c_str(), (long long)d[0], (long long)d[1], (long long)d[2], (long long)d[3],
+                       rmask, dt);
+        contract_slab_gemv(dt, d, rmask, Bt.p, Sv.p, ss, C.p, ys, alpha, st);
+        return;
+      }
+    }
+  }
+
   // complex64 on tensor cores: operands prepared straight from (two-level) strided views and
   // the result written as interleaved complex pairs into C through its own views; an operand
   // whose modes need more than two levels is first permuted into a contiguous temporary.
@@ -340,6 +407,24 @@ void Engine::contract(zc alpha, const Tens &A, const std::string &ma, const Tens
   }
 }
 
+Engine::PrepEntry *Engine::prep_find(const std::string &key) {
+  for (auto &e : prep_)
+    if (e->key == key) return e->epoch == state_epoch() ? e.get() : nullptr;
+  return nullptr;
+}
+
+Engine::PrepEntry *Engine::prep_get(const std::string &key, size_t bytes) {
+  for (auto &e : prep_)
+    if (e->key == key) return e->buf.bytes == bytes ? e.get() : nullptr;
+  if (prep_bytes_ + bytes > prep_cache_cap) return nullptr;
+  auto e = std::make_unique<PrepEntry>();
+  e->key = key;
+  e->buf.alloc(bytes);
+  prep_bytes_ += bytes;
+  prep_.push_back(std::move(e));
+  return prep_.back().get();
+}
+
 void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const Tens &B,
                          const std::string &mb, const Tens &C, const std::string &mc,
                          const std::string &bat, const std::string &Mm, const std::string &Nm,
@@ -359,19 +444,50 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
   auto coalesced = [&](const View2 &x, int64_t nx, const View2 &y, int64_t ny) {
     return runs(x, nx) || runs(y, ny);
   };
+  const int seg = tc_mode == 1 ? 1 : 3;
+  const int kind = tc_mode == 3 ? TC_BF16 : TC_TF32;
+  const int64_t ld = 2 * tc_kpad(K) * seg, tes = tc_esize(kind);
+  const int64_t per_col = 2 * ld * tes, per_row = ld * tes, capb = 2ll << 30;
+  // A constant operand (cst_hint) keeps its prepared form: "P" entries hold its permuted
+  // contiguous copy, "R" entries its prepared rows (A) or columns (B) for every batch and chunk.
+  const bool cache_a = prep_cache_cap && cst_hint && cst_hint == A.p;
+  const bool cache_b = prep_cache_cap && cst_hint && cst_hint == B.p && !cache_a;
+  std::string akey, bkey;
+  if (cache_a || cache_b) {
+    char h[96];
+    std::snprintf(h, sizeof h, "%p|%d|%d|", cache_a ? A.p : B.p, seg, kind);
+    if (cache_a) akey = std::string("A|") + h + ma + "|" + bat + "|" + Mm + "|" + Km + "|";
+    else bkey = std::string("B|") + h + mb + "|" + bat + "|" + Km + "|" + Nm + "|";
+  }
+  PrepEntry *ra = cache_a ? prep_find(akey + "R") : nullptr;  // valid prepared rows of A
+  PrepEntry *rb = cache_b ? prep_find(bkey + "R") : nullptr;  // valid prepared columns of B
   if (!(group_view(A, ma, bat, z, a0) && group_view2(A, ma, Mm, am) && group_view2(A, ma, Km, ak) &&
         coalesced(am, M, ak, K))) {
     std::string order = bat + Mm + Km;
-    Tens T = contiguous_like(ws(0, nb * M * K * es), C64, A, ma, order);
-    permute(zc(1.0), A, ma, T, order, false);
-    Ap = T.p; a0 = M * K; am = view1(K); ak = view1(1);
+    a0 = M * K; am = view1(K); ak = view1(1);
+    if (!ra) {
+      PrepEntry *pa = cache_a ? prep_find(akey + "P") : nullptr;
+      if (pa) {
+        Ap = pa->buf.p;
+      } else {
+        // (a permuted copy pays only where TF32 reads it in place; otherwise its rows are kept)
+        PrepEntry *fa = cache_a && seg == 1 ? prep_get(akey + "P", (size_t)(nb * M * K * es)) : nullptr;
+        Tens T = contiguous_like(fa ? fa->buf.p : ws(0, nb * M * K * es), C64, A, ma, order);
+        permute(zc(1.0), A, ma, T, order, false);
+        if (fa) fa->epoch = state_epoch();
+        Ap = T.p;
+      }
+    }
   }
   if (!(group_view(B, mb, bat, z, b0) && group_view2(B, mb, Km, bk) && group_view2(B, mb, Nm, bn) &&
         coalesced(bk, K, bn, N))) {
     std::string order = bat + Km + Nm;
-    Tens T = contiguous_like(ws(1, nb * K * N * es), C64, B, mb, order);
-    permute(zc(1.0), B, mb, T, order, false);
-    Bp = T.p; b0 = K * N; bk = view1(N); bn = view1(1);
+    b0 = K * N; bk = view1(N); bn = view1(1);
+    if (!rb) {  // (B is always prepared: its prepared columns are what is kept)
+      Tens T = contiguous_like(ws(1, nb * K * N * es), C64, B, mb, order);
+      permute(zc(1.0), B, mb, T, order, false);
+      Bp = T.p;
+    }
   }
   const bool direct = group_view(C, mc, bat, z, c0) && group_view2(C, mc, Mm, cm) &&
                       group_view2(C, mc, Nm, cn) && coalesced(cm, M, cn, N);
@@ -381,18 +497,14 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
     T = contiguous_like(ws(2, nb * M * N * es), C64, C, mc, order);
     c0 = M * N; cm = view1(N); cn = view1(1);
   }
-  const int seg = tc_mode == 1 ? 1 : 3;
-  const int kind = tc_mode == 3 ? TC_BF16 : TC_TF32;
-  const int64_t ld = 2 * tc_kpad(K) * seg, tes = tc_esize(kind);
   if (trace_on())
-    std::fprintf(stderr, "cclr contract tc %s,%s->%s nb=%lld M=%lld N=%lld K=%lld A[%s|%s]%s B[%s|%s]%s C[%s|%s]%s\n",
+    std::fprintf(stderr, "cclr contract tc %s,%s->%s nb=%lld M=%lld N=%lld K=%lld A[%s|%s]%s B[%s|%s]%s C[%s|%s]%s%s\n",
                  ma.c_str(), mb.c_str(), mc.c_str(), (long long)nb, (long long)M, (long long)N, (long long)K,
                  vstr(am).c_str(), vstr(ak).c_str(), Ap == A.p ? "" : "(permuted)", vstr(bk).c_str(),
                  vstr(bn).c_str(), Bp == B.p ? "" : "(permuted)", vstr(cm).c_str(), vstr(cn).c_str(),
-                 direct ? "" : "(temporary)");
+                 direct ? "" : "(temporary)", ra || rb ? " (cached operand)" : "");
   // prepared operands are bounded (2 GiB each): B in chunks of columns, A in chunks of rows,
   // each chunk starting on a whole block of a two-level view
-  const int64_t per_col = 2 * ld * tes, per_row = ld * tes, capb = 2ll << 30;
   auto unit_of = [](const View2 &x, const View2 &y) {
     int64_t u = 1;
     if (x.din != TC_ONE_LEVEL) u = std::lcm(u, x.din);
@@ -408,34 +520,46 @@ void Engine::contract_tc(zc alpha, const Tens &A, const std::string &ma, const T
     const int64_t u = unit_of(am, cm);
     if (M * per_row > capb && u < M) Mc = std::max(u, capb / per_row / u * u);
   }
-  void *Ao = nullptr;
-  void *Bo = ws(4, (size_t)(Nc * per_col));
   // TF32 reads A in place when its K index is contiguous and its rows are one strided level
-  const bool a_direct = seg == 1 && ak.sin == 1 && ak.din == TC_ONE_LEVEL && am.din == TC_ONE_LEVEL &&
+  const bool a_direct = !ra && seg == 1 && ak.sin == 1 && ak.din == TC_ONE_LEVEL && am.din == TC_ONE_LEVEL &&
                         (M == 1 || tc_a_inplace_ok(Ap, am.sin, K)) && (nb == 1 || (a0 * es) % 16 == 0);
+  // the constant's rows / columns prepared in this call for later ones (all batches and chunks)
+  PrepEntry *wa = cache_a && !ra && !a_direct ? prep_get(akey + "R", (size_t)(nb * M * per_row)) : nullptr;
+  PrepEntry *wb = cache_b && !rb ? prep_get(bkey + "R", (size_t)(nb * N * per_col)) : nullptr;
+  char *Arows = ra ? (char *)ra->buf.p : wa ? (char *)wa->buf.p : nullptr;
+  char *Bcols = rb ? (char *)rb->buf.p : wb ? (char *)wb->buf.p : nullptr;
+  void *Ao = nullptr;
+  void *Bo = Bcols ? nullptr : ws(4, (size_t)(Nc * per_col));
+  bool used_direct = false;
   for (int64_t b = 0; b < nb; ++b) {
     const void *Ab = (const char *)Ap + b * a0 * es;
     const bool ad = a_direct && tc_a_inplace_ok(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K);
-    if (!ad && !Ao) Ao = ws(3, (size_t)(Mc * per_row));
+    used_direct |= ad;
+    if (!ad && !Arows && !Ao) Ao = ws(3, (size_t)(Mc * per_row));
     float *Cb = (float *)((char *)(direct ? C.p : T.p) + b * c0 * es);
     for (int64_t n0 = 0; n0 < N; n0 += Nc) {
       const int64_t nn = std::min(Nc, N - n0);
-      tc_prep_b2((const char *)Bp + (b * b0 + v2off(bn, n0)) * es, bk, bn, K, nn, seg, kind, Bo, ld, st);
+      void *Bn = Bcols ? (void *)(Bcols + (b * N + n0) * per_col) : Bo;
+      if (!rb) tc_prep_b2((const char *)Bp + (b * b0 + v2off(bn, n0)) * es, bk, bn, K, nn, seg, kind, Bn, ld, st);
       float *Cn = Cb + 2 * v2off(cn, n0);
       if (ad) {
-        tc_gemm_a_inplace(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K, (const float *)Bo, ld, M, 2 * nn, Cn, cm, cn,
+        tc_gemm_a_inplace(Ab, M == 1 ? (K + 1) / 2 * 2 : am.sin, K, (const float *)Bn, ld, M, 2 * nn, Cn, cm, cn,
                           alpha, direct, st);
         continue;
       }
       for (int64_t m0 = 0; m0 < M; m0 += Mc) {
         const int64_t mm = std::min(Mc, M - m0);
-        if (n0 == 0 || Mc < M) tc_prep_a2((const char *)Ab + v2off(am, m0) * es, am, ak, mm, K, seg, kind, Ao, ld, st);
-        tc_gemm_seg_v(Ao, ld, Bo, ld, mm, 2 * nn, 2 * tc_kpad(K), seg, kind, Cn + 2 * v2off(cm, m0), cm, cn, alpha,
+        void *Am = Arows ? (void *)(Arows + (b * M + m0) * per_row) : Ao;
+        if (Arows ? (!ra && n0 == 0) : (n0 == 0 || Mc < M))
+          tc_prep_a2((const char *)Ab + v2off(am, m0) * es, am, ak, mm, K, seg, kind, Am, ld, st);
+        tc_gemm_seg_v(Am, ld, Bn, ld, mm, 2 * nn, 2 * tc_kpad(K), seg, kind, Cn + 2 * v2off(cm, m0), cm, cn, alpha,
                       direct, st);
       }
     }
     ++tc_calls;
   }
+  if (wa && !used_direct) wa->epoch = state_epoch();
+  if (wb) wb->epoch = state_epoch();
   if (!direct) permute(zc(1.0), T, bat + Mm + Nm, C, mc, true);
 }
 

@@ -1,6 +1,7 @@
 // Host-side tensor-contraction engine: device buffers, workspace, einsum-style
 // contractions mapped onto the strided complex GEMM, permutes and vector helpers.
 #pragma once
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -82,10 +83,33 @@ class Engine {
   void zero(const Tens &t);
   double2 *dot_scratch();  // device: partials [>=304] and results [64]
   double2 *dot_results();
+  // Constant operands: while cst_hint points at one operand of a tensor-core contraction, the
+  // prepared form of that operand (its permuted copy, or its TF32 / BF16 embedded rows or columns)
+  // is kept and reused by later contractions of the same operand with the same modes and
+  // precision, as long as state_epoch() has not moved (no device memory freed, no constants
+  // rebuilt); at most prep_cache_cap bytes (0: off).
+  const void *cst_hint = nullptr;
+  size_t prep_cache_cap = 0;
+  void clear_prep_cache() {
+    prep_.clear();
+    prep_bytes_ = 0;
+  }
+  size_t prep_cache_bytes() const { return prep_bytes_; }
 
  private:
   std::vector<DevBuf> slots_;
   DevBuf dots_;
+  struct PrepEntry {
+    std::string key;
+    DevBuf buf;
+    unsigned long long epoch = 0;  // the entry's content is valid while state_epoch() equals it
+  };
+  std::vector<std::unique_ptr<PrepEntry>> prep_;
+  size_t prep_bytes_ = 0;
+  // a valid entry, or nullptr
+  PrepEntry *prep_find(const std::string &key);
+  // the entry to (re)fill, created if needed; nullptr when it would exceed the cap
+  PrepEntry *prep_get(const std::string &key, size_t bytes);
 };
 
 }  // namespace cclr

@@ -802,6 +802,221 @@ __global__ void diag_kernel(int o, int v, const double2 *Foo, const double2 *Fvv
   }
 }
 
+// Y[p][j][q] += alpha * sum_k S(k, j) X[p][k][q] for short k and j (at most 64 each): the
+// o x o matrices acting on one occupied index of an o^2 v^2 tensor.  One block of 128 threads takes
+// 128 consecutive q of one p: S is staged in shared memory (broadcast reads), each thread copies its
+// own column X[p][.][q] into shared memory once and forms eight j at a time from it, so X is read
+// once and Y read and written once, all coalesced along q.
+template <typename T>
+__global__ void __launch_bounds__(128) smallk_kernel(int64_t P, int K, int J, int64_t Q,
+                                                     const typename cpx<T>::t *S, int64_t sSk, int64_t sSj,
+                                                     const typename cpx<T>::t *X, int64_t sXp, int64_t sXk,
+                                                     typename cpx<T>::t *Y, int64_t sYp, int64_t sYj, T ar, T ai) {
+  using C2 = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char smk_raw[];
+  C2 *Ss = (C2 *)smk_raw;     // [K][J]
+  C2 *Xs = Ss + K * J;         // [K][128], column threadIdx.x private to its thread
+  for (int e = threadIdx.x; e < K * J; e += blockDim.x) {
+    const int k = e / J, j = e % J;
+    Ss[e] = S[(int64_t)k * sSk + (int64_t)j * sSj];
+  }
+  __syncthreads();
+  const int64_t nqt = (Q + 127) / 128;
+  for (int64_t t = blockIdx.x; t < P * nqt; t += gridDim.x) {
+    const int64_t p = t / nqt, q = (t % nqt) * 128 + threadIdx.x;
+    if (q >= Q) continue;
+    const C2 *xp = X + p * sXp + q;
+    for (int k = 0; k < K; ++k) Xs[k * 128 + threadIdx.x] = xp[(int64_t)k * sXk];
+    C2 *yp = Y + p * sYp + q;
+    for (int j0 = 0; j0 < J; j0 += 8) {
+      T re[8], im[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { re[u] = 0; im[u] = 0; }
+      for (int k = 0; k < K; ++k) {
+        const C2 x = Xs[k * 128 + threadIdx.x];
+        const C2 *sr = Ss + k * J + j0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (j0 + u < J) {
+            const C2 sv = sr[u];
+            re[u] += sv.x * x.x - sv.y * x.y;
+            im[u] += sv.x * x.y + sv.y * x.x;
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j0 + u < J) {
+          C2 y = yp[(int64_t)(j0 + u) * sYj];
+          y.x += ar * re[u] - ai * im[u];
+          y.y += ar * im[u] + ai * re[u];
+          yp[(int64_t)(j0 + u) * sYj] = y;
+        }
+      }
+    }
+  }
+}
+
+void contract_smallk(int dt, int64_t P, int K, int J, int64_t Q, const void *S, int64_t sSk, int64_t sSj,
+                     const void *X, int64_t sXp, int64_t sXk, void *Y, int64_t sYp, int64_t sYj, zc alpha,
+                     cudaStream_t st) {
+  CCLR_REQUIRE(K >= 1 && K <= 64 && J >= 1 && J <= 64, "contract_smallk: k and j extents must be 1..64");
+  if (P == 0 || Q == 0) return;
+  const size_t es = dt == C128 ? 16 : 8;
+  const size_t smem = (size_t)K * J * es + (size_t)K * 128 * es;  // at most 192 KB (complex128)
+  static std::atomic<unsigned long long> attr_set{0};               // one bit per device
+  int dev = 0;
+  CCLR_CUDA(cudaGetDevice(&dev));
+  if (dev < 64 && !(attr_set.load() & (1ull << dev))) {
+    CCLR_CUDA(cudaFuncSetAttribute(smallk_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)64 * 64 * 16 + (size_t)64 * 128 * 16)));
+    CCLR_CUDA(cudaFuncSetAttribute(smallk_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)((size_t)64 * 64 * 8 + (size_t)64 * 128 * 8)));
+    attr_set |= 1ull << dev;
+  }
+  const int64_t tiles = P * ((Q + 127) / 128);
+  const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)152 * 16);
+  if (dt == C128)
+    smallk_kernel<double><<<grid, 128, smem, st>>>(P, K, J, Q, (const double2 *)S, sSk, sSj, (const double2 *)X, sXp,
+                                                   sXk, (double2 *)Y, sYp, sYj, alpha.re, alpha.im);
+  else
+    smallk_kernel<float><<<grid, 128, smem, st>>>(P, K, J, Q, (const float2 *)S, sSk, sSj, (const float2 *)X, sXp,
+                                                  sXk, (float2 *)Y, sYp, sYj, (float)alpha.re, (float)alpha.im);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+// y[r] += alpha * sum_c B[x] s[c] for a rank-4 tensor B whose modes are each either an output mode
+// (r) or a contracted mode (c), s holding only contracted modes: the matrix-vector products of an
+// o^2 v^2 tensor with an o x v vector.  One block per (x0, x1) reads the contiguous slab
+// B[x0][x1][.][.] once, sums into shared-memory partials over the slab's output index (at most one
+// of the two slab modes is an output mode), and adds them to y with atomics.
+template <typename T>
+__device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) slab_gemv_kernel(int64_t d0, int64_t d1, int64_t d2, int64_t d3,
+                                                        int rmask, const typename cpx<T>::t *B,
+                                                        const typename cpx<T>::t *S, int64_t s0, int64_t s1,
+                                                        int64_t s2, int64_t s3, typename cpx<T>::t *Y,
+                                                        int64_t y0, int64_t y1, int64_t y2, int64_t y3, T ar,
+                                                        T ai) {
+  using C2 = typename cpx<T>::t;
+  extern __shared__ __align__(16) unsigned char sg_raw[];
+  T *part = (T *)sg_raw;  // [np][2]
+  const bool r2 = rmask & 4, r3 = rmask & 8;
+  const int64_t np = r2 ? d2 : (r3 ? d3 : 1);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int64_t t = blockIdx.x; t < d0 * d1; t += gridDim.x) {
+    const int64_t x0 = t / d1, x1 = t % d1;
+    for (int64_t e = threadIdx.x; e < 2 * np; e += blockDim.x) part[e] = 0;
+    __syncthreads();
+    const C2 *slab = B + t * d2 * d3;
+    const C2 *sb = S + ((rmask & 1) ? 0 : x0 * s0) + ((rmask & 2) ? 0 : x1 * s1);
+    if (r2) {  // one warp per row x2, lanes along the contiguous contracted x3
+      for (int64_t x2 = warp; x2 < d2; x2 += nwarps) {
+        T re = 0, im = 0;
+        for (int64_t x3 = lane; x3 < d3; x3 += 32) {
+          const C2 b = slab[x2 * d3 + x3], sv = sb[x3 * s3];
+          re += b.x * sv.x - b.y * sv.y;
+          im += b.x * sv.y + b.y * sv.x;
+        }
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) { part[2 * x2] = re; part[2 * x2 + 1] = im; }
+      }
+    } else {  // thread groups over rows x2, threads along x3 (the output index, or contracted too)
+      const int64_t w3 = d3 < (int64_t)blockDim.x ? d3 : (int64_t)blockDim.x;
+      const int64_t G = blockDim.x / w3, g = threadIdx.x / w3, c = threadIdx.x % w3;
+      if (g < G) {
+        for (int64_t x3 = c; x3 < d3; x3 += w3) {
+          T re = 0, im = 0;
+          for (int64_t x2 = g; x2 < d2; x2 += G) {
+            const C2 b = slab[x2 * d3 + x3], sv = sb[(r3 ? 0 : x3 * s3) + x2 * s2];
+            re += b.x * sv.x - b.y * sv.y;
+            im += b.x * sv.y + b.y * sv.x;
+          }
+          const int64_t pi = r3 ? x3 : 0;
+          atomicAdd(&part[2 * pi], re);
+          atomicAdd(&part[2 * pi + 1], im);
+        }
+      }
+    }
+    __syncthreads();
+    const int64_t yb = ((rmask & 1) ? x0 * y0 : 0) + ((rmask & 2) ? x1 * y1 : 0);
+    for (int64_t pi = threadIdx.x; pi < np; pi += blockDim.x) {
+      const T re = part[2 * pi], im = part[2 * pi + 1];
+      T *yp = (T *)(Y + yb + (r2 ? pi * y2 : 0) + (r3 ? pi * y3 : 0));
+      atomicAdd(yp, ar * re - ai * im);
+      atomicAdd(yp + 1, ar * im + ai * re);
+    }
+    __syncthreads();
+  }
+}
+
+void contract_slab_gemv(int dt, const int64_t *d, int rmask, const void *B, const void *S, const int64_t *ss,
+                        void *Y, const int64_t *ys, zc alpha, cudaStream_t st) {
+  CCLR_REQUIRE(!((rmask & 4) && (rmask & 8)), "contract_slab_gemv: at most one slab mode may be an output mode");
+  if (d[0] * d[1] * d[2] * d[3] == 0) return;
+  const int64_t np = (rmask & 4) ? d[2] : ((rmask & 8) ? d[3] : 1);
+  const size_t smem = (size_t)np * 2 * (dt == C128 ? 8 : 4);
+  CCLR_REQUIRE(smem <= 48 * 1024, "contract_slab_gemv: slab output index too long");
+  const unsigned grid = (unsigned)std::min<int64_t>(d[0] * d[1], (int64_t)152 * 8);
+  if (dt == C128)
+    slab_gemv_kernel<double><<<grid, 256, smem, st>>>(d[0], d[1], d[2], d[3], rmask, (const double2 *)B,
+                                                      (const double2 *)S, ss[0], ss[1], ss[2], ss[3], (double2 *)Y,
+                                                      ys[0], ys[1], ys[2], ys[3], alpha.re, alpha.im);
+  else
+    slab_gemv_kernel<float><<<grid, 256, smem, st>>>(d[0], d[1], d[2], d[3], rmask, (const float2 *)B,
+                                                     (const float2 *)S, ss[0], ss[1], ss[2], ss[3], (float2 *)Y, ys[0],
+                                                     ys[1], ys[2], ys[3], (float)alpha.re, (float)alpha.im);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+// tau of the CCSD energy over the packed doubles (complex128):
+// tau[(i<j),(a<b)] = t2[(i<j),(a<b)] + t1[i,a] t1[j,b] - t1[i,b] t1[j,a].
+__global__ void tau_packed_kernel(int o, int v, const double2 *t1, const double2 *t2p, double2 *tau) {
+  const int64_t Pv = (int64_t)v * (v - 1) / 2, n = (int64_t)o * (o - 1) / 2 * Pv;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    int i, j, a, b;
+    pair_of(e / Pv, o, i, j);
+    pair_of(e % Pv, v, a, b);
+    const double2 ia = t1[(int64_t)i * v + a], jb = t1[(int64_t)j * v + b];
+    const double2 ib = t1[(int64_t)i * v + b], ja = t1[(int64_t)j * v + a];
+    double2 z = t2p[e];
+    z.x += (ia.x * jb.x - ia.y * jb.y) - (ib.x * ja.x - ib.y * ja.y);
+    z.y += (ia.x * jb.y + ia.y * jb.x) - (ib.x * ja.y + ib.y * ja.x);
+    tau[e] = z;
+  }
+}
+
+void tau_packed(int o, int v, const void *t1, const void *t2p, void *tau, cudaStream_t st) {
+  const int64_t n = (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2);
+  if (n == 0) return;
+  tau_packed_kernel<<<grid_for(n), 256, 0, st>>>(o, v, (const double2 *)t1, (const double2 *)t2p, (double2 *)tau);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
+__global__ void conj_kernel(int64_t n, const double2 *x, double2 *y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const double2 z = x[e];
+    y[e] = make_double2(z.x, -z.y);
+  }
+}
+
+void vec_conj(int64_t n, const void *x, void *y, cudaStream_t st) {
+  if (n == 0) return;
+  conj_kernel<<<grid_for(n), 256, 0, st>>>(n, (const double2 *)x, (double2 *)y);
+  count_launch();
+  CCLR_CUDA(cudaGetLastError());
+}
+
 void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, double *D2p,
                 cudaStream_t st) {
   const int64_t n = (int64_t)o * v + (int64_t)o * (o - 1) / 2 * ((int64_t)v * (v - 1) / 2);

@@ -65,6 +65,21 @@ void pack_doubles(int dt_f, int dt_p, int o, int v, const void *F, void *P, cuda
 // out1[i,a] += alpha * sum_{j,b} W[i,j,a,b] x1[j,b] for W antisymmetric in (i,j) and (a,b), given
 // packed (complex128; x1, out1 complex128 [o][v]).
 void packed_doubles_dot_singles(int o, int v, const void *Wp, const void *x1, void *out1, zc alpha, cudaStream_t st);
+// Y[p][j][q] += alpha * sum_k S[k sSk + j sSj] X[p sXp + k sXk + q] (q unit stride in X and Y,
+// Y[p sYp + j sYj + q]); k and j extents 1..64; complex128 or complex64 (dt), FP64 / FP32 CUDA cores.
+void contract_smallk(int dt, int64_t P, int K, int J, int64_t Q, const void *S, int64_t sSk, int64_t sSj,
+                     const void *X, int64_t sXp, int64_t sXk, void *Y, int64_t sYp, int64_t sYj, zc alpha,
+                     cudaStream_t st);
+// y[r] += alpha * sum_c B[x0][x1][x2][x3] s[c] for a contiguous rank-4 B (dims d[4]) whose modes are
+// output modes (bit k of rmask set; y stride ys[k]) or contracted modes (s stride ss[k]); at most one of
+// modes 2 and 3 is an output mode.  Complex128 or complex64 (dt); atomics (order of summation varies).
+void contract_slab_gemv(int dt, const int64_t *d, int rmask, const void *B, const void *S, const int64_t *ss,
+                        void *Y, const int64_t *ys, zc alpha, cudaStream_t st);
+// tau[(i<j),(a<b)] = t2p + t1[i,a] t1[j,b] - t1[i,b] t1[j,a] over the packed doubles (complex128;
+// t1 [o][v]); the CCSD energy is sum over the packed doubles of <ij||ab> tau.
+void tau_packed(int o, int v, const void *t1, const void *t2p, void *tau, cudaStream_t st);
+// y = conj(x), n complex128 entries (y may be x)
+void vec_conj(int64_t n, const void *x, void *y, cudaStream_t st);
 void apply_denominator(int o, int v, const double *eps, void *t2, cudaStream_t st);
 void set_diag(int n, const double *d, void *out, cudaStream_t st);
 

@@ -153,9 +153,19 @@ void LadderTC::prepare(Engine &E, const Tens &Lvv, int o, int v, int naux, int s
   const int64_t vv = (int64_t)v * v;
   Lvv_ = Lvv.p;
   LA.alloc((size_t)vv * ld * es);
-  LB.release();  // the embedded B rows are prepared per group (only the group's a values)
   // A(m = (b,f), k = P) = L[P,b,f]
   tc_prep_a(Lvv.p, 1, vv, vv, naux, seg, kind, LA.p, ld, st);
+  // B(k = P, n = (a,e)) = L[P,a,e], embedded (two rows per complex column): prepared here for every
+  // a when it takes at most 3 GB (it is the same for every product with this L~_vv), else per group
+  // inside each product
+  const size_t lb_all = (size_t)2 * vv * ld * es;
+  lb_all_ = !lean && lb_all <= (size_t)3 << 30;
+  if (lb_all_) {
+    if (LB.bytes != lb_all) LB.alloc(lb_all);
+    tc_prep_b(Lvv.p, vv, 1, naux, vv, seg, kind, LB.p, ld, st);
+  } else {
+    LB.release();
+  }
   auto op = pairs(o), vp = pairs(v);
   opairs.alloc(std::max<size_t>(1, op.size()) * sizeof(int2));
   vpairs.alloc(std::max<size_t>(1, vp.size()) * sizeof(int2));
@@ -235,7 +245,7 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   QC = std::min(QC, Pv);
   const int64_t nch = (Pv + QC - 1) / QC, Kc = tc_kpad(QC), ldc = 2 * Kc * seg;
   if (W.bytes < (size_t)vv * ga * v * 8) W.alloc((size_t)vv * ga * v * 8);
-  if (LB.bytes < (size_t)2 * ga * v * ldL * es) LB.alloc((size_t)2 * ga * v * ldL * es);
+  if (!lb_all_ && LB.bytes < (size_t)2 * ga * v * ldL * es) LB.alloc((size_t)2 * ga * v * ldL * es);
   const size_t wp_bytes = dir > 0 ? (size_t)maxpairs * ldc * es : (size_t)2 * QC * (2 * kpg * seg) * es;
   if (Wp.bytes < wp_bytes) Wp.alloc(wp_bytes);
   const size_t xp_bytes = dir > 0 ? (size_t)nch * 2 * Po * NR * ldc * es : (size_t)Po * NR * (2 * kpg * seg) * es;
@@ -289,10 +299,12 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
       for (auto &e : fev)
         if (!e) CCLR_CUDA(cudaEventCreate(&e));
     }
-    // B(k = P, n = (a,e)) = L[P,a,e] for the group's a values, embedded
-    tc_prep_b((const char *)Lvv_ + (size_t)a0 * v * 8, vv, 1, naux_, cols, seg, kind, LBb, ldL, st);
+    // B(k = P, n = (a,e)) = L[P,a,e] for the group's a values, embedded (already prepared for
+    // every a when lb_all_)
+    const char *LBg = LBb + (lb_all_ ? (size_t)2 * a0 * v * ldL * es : 0);
+    if (!lb_all_) tc_prep_b((const char *)Lvv_ + (size_t)a0 * v * 8, vv, 1, naux_, cols, seg, kind, LBb, ldL, st);
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_], st));
-    tc_gemm_seg(LAb + (int64_t)a0 * v * ldL * es, ldL, LBb, ldL, rows, 2 * cols, ldL / seg, seg, kind, W.as<float>(),
+    tc_gemm_seg(LAb + (int64_t)a0 * v * ldL * es, ldL, LBg, ldL, rows, 2 * cols, ldL / seg, seg, kind, W.as<float>(),
                 2 * cols, zc(1.0), false, st);
     CCLR_CUDA(cudaEventRecord(fev[2 * nform_ + 1], st));
     ++nform_;

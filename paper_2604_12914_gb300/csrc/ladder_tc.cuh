@@ -54,6 +54,7 @@ class LadderTC {
   // frees the per-product buffers and the prepared operands (prepare() is needed again)
   void release() {
     W.release(); Wp.release(); Xp.release(); sig.release(); LB.release(); LA.release();
+    lb_all_ = false;
   }
   size_t stored_bytes() const { return Wall.bytes; }
   std::vector<std::pair<int, float>> tune_log;
@@ -62,6 +63,7 @@ class LadderTC {
   int o_ = 0, v_ = 0, naux_ = 0, seg_ = 0, kind_ = 0;
   int64_t Po_ = 0, Pv_ = 0;
   DevBuf LA, LB;            // formation operands: rows (b,f) (all), embedded rows (a,e) of one group; K = naux
+  bool lb_all_ = false;     // LB holds the embedded rows (a,e) of every a (prepared once per L~_vv)
   const void *Lvv_ = nullptr;  // the complex64 L~_vv the operands are prepared from
   DevBuf opairs, vpairs;    // pair tables (p, q), p < q, row-major pair order
   DevBuf W, Wp, Xp, sig;    // group formation block, packed group block, packed X, packed result

@@ -13,6 +13,7 @@
 #include <cstdio>
 #include <cstdlib>
 
+#include <chrono>
 #include "model.cuh"
 #include "tc_gemm.cuh"
 
@@ -108,6 +109,9 @@ void Model::ensure_src64() {
 }
 
 void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
+  // CCLR_OPTIME=1 also prints the wall time of every build (diagnostics)
+  static const bool optime = std::getenv("CCLR_OPTIME") && std::getenv("CCLR_OPTIME")[0] == '1';
+  const auto wall0 = std::chrono::steady_clock::now();
   out.dt = dt;
   const size_t es = dt_size(dt);
   const int P = naux;
@@ -245,7 +249,13 @@ void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
   for (int k = 0; k < 3; ++k)  // a ladder prepared from this buffer is stale
     if (ltc_src[k] == out.t[K_LVV].p) ltc_src[k] = nullptr;
   bump_state_epoch();  // and so is any captured program that read the set
+  E.clear_prep_cache();  // and every prepared constant operand
   out.valid = true;
+  if (optime) {
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    std::fprintf(stderr, "cclr build_set dt %d: %.3f ms\n", dt,
+                 std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count());
+  }
 }
 
 // H-bar of a one-body operator B (Hamiltonian without two-body part) with the T1 dressing
@@ -285,6 +295,7 @@ void Model::build_set_onebody(const void *Bd, const void *t1d, const void *t2d, 
   E.tc_mode = tc_saved;
   CCLR_CUDA(cudaStreamSynchronize(st));
   bump_state_epoch();
+  E.clear_prep_cache();
   out.valid = true;
 }
 
@@ -321,11 +332,13 @@ void Model::round_set(const CstSet &src, CstSet &dst) {
   for (int k = 0; k < 3; ++k)
     if (ltc_src[k] == dst.t[K_LVV].p) ltc_src[k] = nullptr;
   bump_state_epoch();
+  E.clear_prep_cache();
   CCLR_CUDA(cudaStreamSynchronize(st));
   dst.valid = true;
 }
 
 void Model::release_set(CstSet &s) {
+  E.clear_prep_cache();
   for (int k = 0; k < 3; ++k)
     if (s.t[K_LVV].p && ltc_src[k] == s.t[K_LVV].p) ltc_src[k] = nullptr;
   for (auto &b : s.buf) b.release();
@@ -507,7 +520,11 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
         if (op.kind == OP_LADDER || (op.kind == OP_CONTRACT && C.zero[op.cst])) continue;
         if (oe0 && r == 0) CCLR_CUDA(cudaEventRecord(oe0, st));
         switch (op.kind) {
-          case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.in), op.mi, V(r, op.out), op.mo); break;
+          case OP_CONTRACT:
+            E.cst_hint = Cst(op.cst).p;
+            E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.in), op.mi, V(r, op.out), op.mo);
+            E.cst_hint = nullptr;
+            break;
           case OP_PERM: E.permute(op.alpha, V(r, op.in), op.mi, V(r, op.out), op.mo, true); break;
           case OP_ZERO: E.zero(V(r, op.out)); break;
           case OP_ANTISYM:
@@ -551,7 +568,11 @@ void Model::apply_body(int dir, const CstSet &C, int nr, const void *const *x1, 
         const Op &op = *it;
         if (op.kind == OP_LADDER || (op.kind == OP_CONTRACT && C.zero[op.cst])) continue;
         switch (op.kind) {
-          case OP_CONTRACT: E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.out), op.mo, V(r, op.in), op.mi); break;
+          case OP_CONTRACT:
+            E.cst_hint = Cst(op.cst).p;
+            E.contract(op.alpha, Cst(op.cst), op.mc, V(r, op.out), op.mo, V(r, op.in), op.mi);
+            E.cst_hint = nullptr;
+            break;
           case OP_PERM: E.permute(op.alpha, V(r, op.out), op.mo, V(r, op.in), op.mi, true); break;
           case OP_ZERO: E.zero(V(r, op.out)); break;
           case OP_ANTISYM:
@@ -743,8 +764,8 @@ Program build_sigma_program(int o, int v, int naux) {
   const int X1 = var({O, Vv}), X2 = var({O, O, Vv, Vv}), S1 = var({O, Vv}), S2 = var({O, O, Vv, Vv});
   const int Zt = var({P, O, Vv}), Rab = var({O, O, Vv, Vv}), Rij = var({O, O, Vv, Vv}),
             Rijab = var({O, O, Vv, Vv}), Zoo = var({O, O, O, O}), U = var({P, Vv, O}),
-            cm = var({O, O}), dm = var({O, O, O, O}), sm = var({P, O, O}), Vm = var({O, Vv, O, Vv}),
-            Xvv = var({Vv, Vv}), Xoo = var({O, O}), w = var({P});
+            sm = var({P, O, O}), Vm = var({O, Vv, O, Vv}), Xvv = var({Vv, Vv}), Xoo = var({O, O}),
+            w = var({P});
   (void)S1;
   auto C = [&](double a, int cst, const char *mc, int in, const char *mi, int out, const char *mo) {
     p.ops.push_back(Op{OP_CONTRACT, zc(a), cst, mc, mi, mo, in, out});
@@ -770,18 +791,16 @@ Program build_sigma_program(int o, int v, int naux) {
   p.ops.push_back(Op{OP_LADDER, zc(1), -1, "", "ijef", "ijab", X2, S2});  // sum_ef <ab|ef>~ X
   Z(Zoo);  // vvvv element's T2 part: 1/2 t_mn^ab (1/2 <mn||ef> X_ij^ef)
   C(0.5, K_OOVV, "mnef", X2, "ijef", Zoo, "mnij");
+  // and P(ij) 1/2 t_mn^ab <mn||ej>~ x_i^e: the o^4 matrix it contracts with t joins Zoo, already
+  // antisymmetrised in (i,j), so one o^4 v^2 contraction serves both terms
+  C(-1, K_WOOOV, "mnje", X1, "ie", Zoo, "mnij");
+  C(1, K_WOOOV, "mnie", X1, "je", Zoo, "mnij");
   C(0.5, K_T2, "mnab", Zoo, "mnij", S2, "ijab");
   C(1, K_WOVVO, "mbej", X2, "imae", Rijab, "ijab");           // ring, P(ij)P(ab)
   // P(ij) sum_e Wvvvo_abej x_i^e, factorised through L~ (vvvo never stored)
   Z(U);
   C(1, K_LVV, "Pae", X1, "ie", U, "Pai");
   C(1, K_LVO, "Pbj", U, "Pai", Rijab, "ijab");               // <ab||ej>~ x_i^e
-  Z(cm);
-  C(1, K_FOV, "me", X1, "ie", cm, "mi");
-  C(-1, K_T2, "mjab", cm, "mi", Rij, "ijab");                // -Fov_me t_mj^ab x_i^e
-  Z(dm);
-  C(-1, K_WOOOV, "mnje", X1, "ie", dm, "mnji");
-  C(0.5, K_T2, "mnab", dm, "mnji", Rij, "ijab");             // 1/2 <mn||ej>~ t_mn^ab x_i^e
   Z(sm);
   C(1, K_LOV, "Pme", X1, "ie", sm, "Pmi");
   Z(Vm);                                                     // V_mbif = sum_e <mb||ef>~ x_i^e
@@ -798,6 +817,9 @@ Program build_sigma_program(int o, int v, int naux) {
   C(-0.5, K_OOVV, "mnef", X2, "mnbf", Xvv, "be");
   C(1, K_T2, "ijae", Xvv, "be", Rab, "ijab");
   Z(Xoo);
+  // -P(ij) Fov_me t_mj^ab x_i^e = -P(ij) t_im^ab (Fov_me x_j^e) (t antisymmetric): one more
+  // o x o matrix for the same contraction with t
+  C(1, K_FOV, "me", X1, "je", Xoo, "mj");
   C(1, K_WOOOV, "mnje", X1, "ne", Xoo, "mj");
   C(0.5, K_OOVV, "mnef", X2, "jnef", Xoo, "mj");
   C(-1, K_T2, "imab", Xoo, "mj", Rij, "ijab");

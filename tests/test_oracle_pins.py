@@ -348,3 +348,31 @@ def test_blocked_sigma_matches_term_list(t1_scale, a_chunk):
     assert float((b1 - q1).abs().max()) < 1e-13 * sc
     assert float((b2 - q2).abs().max()) < 1e-13 * sc
     assert float((E.sigma1_all() - q1).abs().max()) < 1e-13 * sc
+
+
+@pytest.mark.parametrize("o,v,naux,seed", [(2, 4, 6, 3), (3, 7, 12, 4)])
+def test_residual_is_gauss_legendre_integral_of_jacobian(o, v, naux, seed):
+    """Omega(T) = Omega(0) + int_0^1 A(sT) T ds, and two Gauss-Legendre nodes integrate it exactly.
+
+    Omega(sT) is a quartic polynomial in s (Sec. 2.2: H-bar truncates at four T), so its
+    s-derivative A(sT) T is cubic.  This ties the term-list Jacobian to the term-list residual at
+    a finite T (the finite-difference pins only test it locally); a one-node (midpoint) rule must
+    fail, so the check has teeth.
+    """
+    s = _system(o, v, naux, seed=seed, scale=0.5)
+    L = as_t(s.L)
+    g = eri_anti(L)
+    f = torch.diag(as_t(s.eps).to(C))
+    a1, a2 = random_amplitudes(o, v, seed=seed + 1, s1=0.3, s2=0.3)
+    t1, t2 = as_t(a1), as_t(a2)
+    r1, r2 = ccsd.residual(f, g, t1, t2)
+    z1, z2 = ccsd.residual(f, g, torch.zeros_like(t1), torch.zeros_like(t2))
+    h = 0.5 / np.sqrt(3.0)
+    q = [J.sigma_terms(J.Dressed(f, L, sn * t1, sn * t2), t1, t2) for sn in (0.5 - h, 0.5 + h)]
+    g1 = z1 + 0.5 * (q[0][0] + q[1][0])
+    g2 = z2 + 0.5 * (q[0][1] + q[1][1])
+    scale = float(r2.abs().max())
+    assert float((g1 - r1).abs().max()) < 1e-12 * scale
+    assert float((g2 - r2).abs().max()) < 1e-12 * scale
+    m1, m2 = J.sigma_terms(J.Dressed(f, L, 0.5 * t1, 0.5 * t2), t1, t2)
+    assert float((z2 + m2 - r2).abs().max()) > 1e-4 * scale
