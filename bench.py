@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--no-ccsd", action="store_true")
     ap.add_argument("--ccsd-config", default="C2")
     ap.add_argument("--ccsd-prec", default="3xtf32")
+    ap.add_argument("--ccsd-scale", type=float, default=0.01)
+    ap.add_argument("--ccsd-fp64-check", action="store_true")
     ap.add_argument("--solve-large", default="",
                     help="only run a large mixed-precision solve and print its JSON: "
                          "'C3' (3 components x {0, +-0.02, +-0.0428, +-0.0656} = 21 systems in one block) "
@@ -468,12 +470,14 @@ def solve_large(cfg, scale):
     return out
 
 
-def ground_state(cfg, scale, prec, tol):
+def ground_state(cfg, scale, prec, tol, fp64_check=False):
     """Ground-state CCSD on the device: Omega(T) = 0 from the first-order guess by quasi-Newton
     steps with DIIS, each residual from two intermediate builds and two sigma products (exact
-    two-point Gauss-Legendre rule); wall time, residuals formed, energy, and the FP64 residual
-    norm of the final amplitudes (an independent check that the mixed-precision solve met its
-    tolerance)."""
+    two-point Gauss-Legendre rule); wall time, residuals formed, energy, and (fp64_check) the FP64
+    residual norm of the final amplitudes, an independent check that the mixed-precision solve met
+    its tolerance (at o=32 v=240 that one FP64 residual takes over a minute on this GPU's FP64
+    rate).  The Cholesky scale keeps the synthetic system weakly correlated enough for the
+    first-order start: |Omega(T1st)| is about 500 at o=32 v=240 with s = 0.05."""
     import numpy as np
     from paper_2604_12914_gb300 import binding
     from paper_2604_12914_gb300.inputs import make_config
@@ -487,14 +491,15 @@ def ground_state(cfg, scale, prec, tol):
     el = time.perf_counter() - t0
     out.update({"seconds": el, "residuals": its, "seconds_per_residual": el / max(its, 1),
                 "residual_norm": rn, "converged": rn < tol, "energy": [e.real, e.imag]})
-    t1, t2 = ctx.cc_lr_get_t()
-    t0 = time.perf_counter()
-    r1, r2, e64 = ctx.cc_lr_ccsd_residual(t1, t2, prec="fp64")
-    out["fp64_residual_seconds"] = time.perf_counter() - t0
-    iu = np.triu_indices(s.o, 1)
-    ju = np.triu_indices(s.v, 1)
-    out["fp64_residual_norm"] = float(np.sqrt(np.sum(np.abs(r1) ** 2) +
-                                              np.sum(np.abs(r2[iu][:, ju[0], ju[1]]) ** 2)))
+    if fp64_check:
+        t1, t2 = ctx.cc_lr_get_t()
+        t0 = time.perf_counter()
+        r1, r2, e64 = ctx.cc_lr_ccsd_residual(t1, t2, prec="fp64")
+        out["fp64_residual_seconds"] = time.perf_counter() - t0
+        iu = np.triu_indices(s.o, 1)
+        ju = np.triu_indices(s.v, 1)
+        out["fp64_residual_norm"] = float(np.sqrt(np.sum(np.abs(r1) ** 2) +
+                                                  np.sum(np.abs(r2[iu][:, ju[0], ju[1]]) ** 2)))
     used, peak, _ = ctx.cc_lr_memory()
     out["device_memory_peak_gb"] = peak / 1e9
     ctx.close()
@@ -720,7 +725,7 @@ def run_cclr(args):
         c5 = packed_batch("C5", 1, ["tf32", "bf16x3"])
     gs = None
     if rank == 0 and not args.no_ccsd:
-        gs = ground_state(args.ccsd_config, 0.05, args.ccsd_prec, 1e-5)
+        gs = ground_state(args.ccsd_config, args.ccsd_scale, args.ccsd_prec, 1e-5, args.ccsd_fp64_check)
     if rank == 0:
         out = {
             "metric": METRIC, "value": value, "unit": "sigma-vectors/s", "n_gpus": world,

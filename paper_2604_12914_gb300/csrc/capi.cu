@@ -3,6 +3,7 @@
 #include <array>
 #include <chrono>
 #include <cmath>
+#include <limits>
 #include <complex>
 #include <cstring>
 #include <memory>
@@ -80,7 +81,11 @@ struct cclr_ctx {
     CCLR_CUDA(cudaStreamSynchronize(st));
     return zd(h.x, h.y);
   }
-  double norm(const void *a) { return std::sqrt(std::max(0.0, dot(a, a, 1).real())); }
+  // (a NaN or infinite vector gives a NaN or infinite norm: the solvers test for it)
+  double norm(const void *a) {
+    const double d = dot(a, a, 1).real();
+    return std::isfinite(d) ? std::sqrt(std::max(0.0, d)) : std::numeric_limits<double>::quiet_NaN();
+  }
   void axpy(zd a, const void *x, void *y) { vec_axpy(C128, ntot(), zc(a.real(), a.imag()), x, y, st); }
   void copy(const void *x, void *y) { CCLR_CUDA(cudaMemcpyAsync(y, x, (size_t)ntot() * 16, cudaMemcpyDeviceToDevice, st)); }
   void scal(zd a, void *y) { vec_scal(C128, ntot(), zc(a.real(), a.imag()), y, st); }
@@ -135,7 +140,19 @@ struct cclr_ctx {
     }
     op_batch_chunk(dir, nr, xs, ss, set);
   }
+  // the most device memory one product held beyond what stayed allocated after it (workspace,
+  // staging, ladder blocks released in a budgeted context): solvers keep this much free
+  size_t op_transient = 0;
   void op_batch_chunk(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set) {
+    struct PeakScope {  // the account's peak over this product alone, then restored
+      MemAcct &a;
+      size_t saved, &out;
+      PeakScope(MemAcct &a_, size_t &out_) : a(a_), saved(a_.peak), out(out_) { a.peak = a.used; }
+      ~PeakScope() {
+        out = std::max(out, a.peak > a.used ? a.peak - a.used : (size_t)0);
+        a.peak = std::max(saved, a.peak);
+      }
+    } peak_scope(acct, op_transient);
     sigma_calls += nr;
     const int dt = set->dt;
     const size_t es = dt_size(dt);
@@ -271,8 +288,14 @@ struct cclr_ctx {
   std::vector<AVec> kv;  // Krylov basis (kept between calls unless the context is budgeted)
   double solve_gmres(int dir, zd omega, const void *b, void *x, double tol, int m, int maxit,
                      int *its, bool warm) {
+    // Mixed modes: the Krylov basis of these correction solves is stored in complex64 (half the
+    // bytes; the correction is refined by an accurate residual, and rounding the orthonormal basis
+    // to FP32 costs far less accuracy than the products in the correction's own arithmetic). The
+    // Arnoldi dots, updates and the Hessenberg algebra stay in FP64.
+    const bool v64 = M->prec != CCLR_FP64;
+    const size_t vbytes = (size_t)ntot() * (v64 ? 8 : 16);
     m = std::max(2, std::min(m, 100));
-    if (acct.budget) m = std::min(m, block_restart(1, 0.2));
+    if (acct.budget) m = std::min(m, block_restart(1, 0.2, v64 ? 8 : 16));
     struct Release {
       cclr_ctx *c;
       ~Release() {
@@ -280,50 +303,70 @@ struct cclr_ctx {
       }
     } rel_guard{this};
     if ((int)kv.size() < m + 1) kv.resize(m + 1);
-    for (int k = 0; k <= m; ++k) alloc_vec(kv[k]);
-    AVec z, w;
+    for (int k = 0; k <= m; ++k)
+      if (kv[k].b.bytes != vbytes) kv[k].b.alloc(vbytes);
+    AVec z, w, vt;
     alloc_vec(z);
     alloc_vec(w);
+    if (v64) alloc_vec(vt);
+    const Tens k128 = make_tens(nullptr, C128, {ntot()});
+    // basis vector i as complex128 (converted into vt in the mixed modes)
+    auto basis = [&](int i) -> const void * {
+      if (!v64) return kv[i].b.p;
+      Tens src = make_tens(kv[i].b.p, C64, {ntot()}), dst = k128;
+      dst.p = vt.b.p;
+      M->E.permute(zc(1), src, "a", dst, "a", false);
+      return vt.b.p;
+    };
+    // kv[i] = scale * v (v complex128)
+    auto store = [&](const void *v, int i, double scale) {
+      if (!v64) {
+        copy(v, kv[i].b.p);
+        scal(zd(scale), kv[i].b.p);
+        return;
+      }
+      Tens src = k128, dst = make_tens(kv[i].b.p, C64, {ntot()});
+      src.p = (void *)v;
+      M->E.permute(zc(scale), src, "a", dst, "a", false);
+    };
     const double bn = std::max(norm(b), 1e-300);
     if (!warm) CCLR_CUDA(cudaMemsetAsync(x, 0, (size_t)ntot() * 16, st));
     double rel = 1.0;
     int used = 0;
     std::vector<zd> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1);
     while (used < maxit) {
-      // r = b - (Op - omega) x
-      copy(b, kv[0].b.p);
+      // r = b - (Op - omega) x, in w
+      copy(b, w.b.p);
       if (warm || used > 0) {
-        op(dir, x, w.b.p);
-        axpy(zd(-1), w.b.p, kv[0].b.p);
-        axpy(zd(omega), x, kv[0].b.p);
+        op(dir, x, z.b.p);
+        axpy(zd(-1), z.b.p, w.b.p);
+        axpy(zd(omega), x, w.b.p);
       }
       warm = true;
-      double beta = norm(kv[0].b.p);
+      double beta = norm(w.b.p);
       rel = beta / bn;
       if (verbose()) std::fprintf(stderr, "cclr gmres dir=%d omega=%g it=%d rel=%.3e prec=%d\n", dir, omega.real(), used, rel, M->prec);
       if (!(rel == rel)) throw Error(3, "solver produced NaN residual");
       if (rel < tol || beta == 0.0) break;
-      scal(zd(1.0 / beta), kv[0].b.p);
+      store(w.b.p, 0, 1.0 / beta);
       std::fill(g.begin(), g.end(), zd(0));
       g[0] = beta;
       int j = 0;
       for (; j < m && used < maxit; ++j) {
-        precond(omega, kv[j].b.p, z.b.p);
+        precond(omega, basis(j), z.b.p);
         op(dir, z.b.p, w.b.p);
         axpy(zd(-omega), z.b.p, w.b.p);
         ++used;
         if (its) ++*its;
         for (int i = 0; i <= j; ++i) {
-          const zd hij = dot(kv[i].b.p, w.b.p, 1);
+          const void *vi = basis(i);
+          const zd hij = dot(vi, w.b.p, 1);
           H[(size_t)i * m + j] = hij;
-          axpy(-hij, kv[i].b.p, w.b.p);
+          axpy(-hij, vi, w.b.p);
         }
         const double hn = norm(w.b.p);
         H[(size_t)(j + 1) * m + j] = hn;
-        if (hn > 0) {
-          copy(w.b.p, kv[j + 1].b.p);
-          scal(zd(1.0 / hn), kv[j + 1].b.p);
-        }
+        if (hn > 0) store(w.b.p, j + 1, 1.0 / hn);
         // apply previous rotations to column j, then a new one
         for (int i = 0; i < j; ++i) {
           const zd a = H[(size_t)i * m + j], c = H[(size_t)(i + 1) * m + j];
@@ -351,16 +394,16 @@ struct cclr_ctx {
         y[i] = std::abs(d) > 0 ? t / d : zd(0);
       }
       CCLR_CUDA(cudaMemsetAsync(w.b.p, 0, (size_t)ntot() * 16, st));
-      for (int i = 0; i < j; ++i) axpy(y[i], kv[i].b.p, w.b.p);
+      for (int i = 0; i < j; ++i) axpy(y[i], basis(i), w.b.p);
       precond(omega, w.b.p, z.b.p);
       axpy(zd(1), z.b.p, x);
       if (rel < tol) {
         // true residual for the return value
-        copy(b, kv[0].b.p);
-        op(dir, x, w.b.p);
-        axpy(zd(-1), w.b.p, kv[0].b.p);
-        axpy(zd(omega), x, kv[0].b.p);
-        rel = norm(kv[0].b.p) / bn;
+        copy(b, w.b.p);
+        op(dir, x, z.b.p);
+        axpy(zd(-1), z.b.p, w.b.p);
+        axpy(zd(omega), x, w.b.p);
+        rel = norm(w.b.p) / bn;
         if (rel < tol) break;
       }
     }
@@ -644,15 +687,25 @@ struct cclr_ctx {
 
   // restart length of the block solver: the Krylov bases of all systems must fit in half of
   // the free device memory (and of what the context's budget leaves)
-  int block_restart(int nr, double frac = 0.5) {
+  int block_restart(int nr, double frac = 0.5, int bytes_per_entry = 16) {
     size_t free_b = 0, total_b = 0;
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
       (void)cudaGetLastError();
       return krylov;
     }
-    if (acct.budget) free_b = std::min(free_b, acct.budget > acct.used ? acct.budget - acct.used : (size_t)0);
-    const double vec = (double)ntot() * 16;
-    const int fit = (int)(frac * (double)free_b / (vec * std::max(1, nr))) - 4;
+    if (acct.budget) {
+      size_t avail = acct.budget > acct.used ? acct.budget - acct.used : (size_t)0;
+      // once a product has run, its transient memory is known and is all that must stay free
+      if (op_transient) {
+        const size_t keep = op_transient + op_transient / 8;
+        avail = avail > keep ? avail - keep : 0;
+        frac = 0.9;
+      }
+      free_b = std::min(free_b, avail);
+    }
+    const double vec = (double)ntot() * bytes_per_entry;
+    // four complex128 work vectors besides the basis
+    const int fit = (int)((frac * (double)free_b - 4.0 * (double)ntot() * 16) / (vec * std::max(1, nr))) - 1;
     return std::max(2, std::min(krylov, fit));
   }
 
@@ -790,7 +843,10 @@ struct cclr_ctx {
     try {
       for (double s : {0.5 - h, 0.5 + h}) {
         M->E.permute(zc(s), TA, "a", TB, "a", false);
-        M->build_set(fullB.p1(), fullB.p2(n1), gs, p == CCLR_FP64 ? C128 : C64);
+        // complex64 intermediates at s T built on the tensor cores in 3xTF32 (FP32-level accuracy,
+        // a few times faster than the FP32 CUDA cores) when the products use them too
+        M->build_set(fullB.p1(), fullB.p2(n1), gs, p == CCLR_FP64 ? C128 : C64,
+                     p == CCLR_FP64 || p == CCLR_C64_FP32 ? 0 : 2);
         M->prec = p;
         op(+1, tp, sv.b.p, &gs);
         M->prec = saved;
@@ -863,13 +919,17 @@ struct cclr_ctx {
     alloc_vec(r);
     std::vector<zd> B((size_t)depth * depth);
     int nh = 0, head = 0;
-    double rn = 1e300;
+    double rn = 1e300, rn0 = 1e300;
     for (int it = 0; it < maxit; ++it) {
       ccsd_residual(p, tv.b.p, r.b.p);
       rn = norm(r.b.p);
       if (its) ++*its;
       if (verbose()) std::fprintf(stderr, "cclr ccsd it=%d |Omega|=%.3e prec=%d\n", it, rn, p);
-      if (!(rn == rn)) throw Error(3, "ground-state iteration produced a NaN residual");
+      if (!(rn == rn)) throw Error(3, "ground-state iteration produced a non-finite residual");
+      if (it == 0) rn0 = rn;
+      if (rn > 1e3 * rn0)
+        throw Error(3, "ground-state iteration diverged (residual " + std::to_string(rn) + " from " +
+                           std::to_string(rn0) + "): the amplitudes are left unchanged");
       if (rn < tol) break;
       const int k = head;
       head = (head + 1) % depth;
@@ -1272,13 +1332,24 @@ static void solve_right(cclr_ctx *c, int dir, const std::vector<zd> &sh, const s
                         const std::vector<void *> &xs, double tol, int diis_depth, cclr_stats &loc,
                         bool warm = false) {
   if (c->method == 2) {
-    std::vector<int> its;
-    std::vector<double> rels;
-    c->solve_block(dir, sh, bs, xs, tol, c->maxit, its, rels, warm);
-    for (size_t k = 0; k < its.size(); ++k) {
-      loc.iterations += its[k];
-      loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
-      if (!(rels[k] < tol)) loc.converged = 0;
+    // every system of a block keeps its own Krylov basis and six work vectors: the systems go in
+    // blocks small enough that each gets a restart length of min(subspace, 20) in the memory left
+    const int n = (int)bs.size();
+    int g = n;
+    while (g > 1 && c->block_restart(g, c->M->lean ? 0.2 : 0.5) < std::min(c->krylov, 20) + 6) g = (g + 1) / 2;
+    for (int k0 = 0; k0 < n; k0 += g) {
+      const int k1 = std::min(n, k0 + g);
+      std::vector<zd> s2(sh.begin() + k0, sh.begin() + k1);
+      std::vector<const void *> b2(bs.begin() + k0, bs.begin() + k1);
+      std::vector<void *> x2(xs.begin() + k0, xs.begin() + k1);
+      std::vector<int> its;
+      std::vector<double> rels;
+      c->solve_block(dir, s2, b2, x2, tol, c->maxit, its, rels, warm);
+      for (size_t k = 0; k < its.size(); ++k) {
+        loc.iterations += its[k];
+        loc.max_rel_residual = std::max(loc.max_rel_residual, rels[k]);
+        if (!(rels[k] < tol)) loc.converged = 0;
+      }
     }
     return;
   }

@@ -809,9 +809,10 @@ __global__ void diag_kernel(int o, int v, const double2 *Foo, const double2 *Fvv
 // once and Y read and written once, all coalesced along q.
 template <typename T>
 __global__ void __launch_bounds__(128) smallk_kernel(int64_t P, int K, int J, int64_t Q,
-                                                     const typename cpx<T>::t *S, int64_t sSk, int64_t sSj,
-                                                     const typename cpx<T>::t *X, int64_t sXp, int64_t sXk,
-                                                     typename cpx<T>::t *Y, int64_t sYp, int64_t sYj, T ar, T ai) {
+                                                     const typename cpx<T>::t *__restrict__ S, int64_t sSk,
+                                                     int64_t sSj, const typename cpx<T>::t *__restrict__ X,
+                                                     int64_t sXp, int64_t sXk, typename cpx<T>::t *__restrict__ Y,
+                                                     int64_t sYp, int64_t sYj, T ar, T ai) {
   using C2 = typename cpx<T>::t;
   extern __shared__ __align__(16) unsigned char smk_raw[];
   C2 *Ss = (C2 *)smk_raw;     // [K][J]
@@ -826,9 +827,23 @@ __global__ void __launch_bounds__(128) smallk_kernel(int64_t P, int K, int J, in
     const int64_t p = t / nqt, q = (t % nqt) * 128 + threadIdx.x;
     if (q >= Q) continue;
     const C2 *xp = X + p * sXp + q;
-    for (int k = 0; k < K; ++k) Xs[k * 128 + threadIdx.x] = xp[(int64_t)k * sXk];
+    // the column in batches of eight independent loads (latency overlapped), then to shared memory
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      C2 xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < K) xv[u] = xp[(int64_t)(k0 + u) * sXk];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < K) Xs[(k0 + u) * 128 + threadIdx.x] = xv[u];
+    }
     C2 *yp = Y + p * sYp + q;
     for (int j0 = 0; j0 < J; j0 += 8) {
+      // the eight outputs' old values are loaded first, so their latency overlaps the sums
+      C2 yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < J) yv[u] = yp[(int64_t)(j0 + u) * sYj];
       T re[8], im[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) { re[u] = 0; im[u] = 0; }
@@ -847,7 +862,7 @@ __global__ void __launch_bounds__(128) smallk_kernel(int64_t P, int K, int J, in
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         if (j0 + u < J) {
-          C2 y = yp[(int64_t)(j0 + u) * sYj];
+          C2 y = yv[u];
           y.x += ar * re[u] - ai * im[u];
           y.y += ar * im[u] + ai * re[u];
           yp[(int64_t)(j0 + u) * sYj] = y;

@@ -108,17 +108,17 @@ void Model::ensure_src64() {
   conv(h, h64, (int64_t)n * n);
 }
 
-void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt) {
+void Model::build_set(const void *t1d, const void *t2d, CstSet &out, int dt, int tc) {
   // CCLR_OPTIME=1 also prints the wall time of every build (diagnostics)
   static const bool optime = std::getenv("CCLR_OPTIME") && std::getenv("CCLR_OPTIME")[0] == '1';
   const auto wall0 = std::chrono::steady_clock::now();
   out.dt = dt;
   const size_t es = dt_size(dt);
   const int P = naux;
-  // complex64 builds run on the FP32 CUDA cores (FP32-accurate: the stored intermediates
-  // enter every sigma, so their error is systematic)
+  // complex64 builds run on the FP32 CUDA cores by default (FP32-accurate: the stored
+  // intermediates enter every sigma, so their error is systematic), or in 3xTF32 (tc = 2)
   const int tc_saved = E.tc_mode;
-  E.tc_mode = 0;
+  E.tc_mode = dt == C64 ? tc : 0;
   auto alloc = [&](int id, std::initializer_list<int64_t> dims) {
     int64_t ne = 1;
     for (auto d : dims) ne *= d;

@@ -115,7 +115,9 @@ class Model {
                      const double *t1_h, const double *t2_h, int device_ptrs);
   // Build dressed blocks + intermediates for amplitudes (t1d, t2d; complex128 device) in
   // precision dt (complex64 on the tensor cores with the 3xTF32 split).
-  void build_set(const void *t1d, const void *t2d, CstSet &out, int dt);
+  // tc: tensor-core mode of a complex64 build's contractions (0: FP32 CUDA cores, the default;
+  // 2: 3xTF32)
+  void build_set(const void *t1d, const void *t2d, CstSet &out, int dt, int tc = 0);
   // The set of the one-body operator B alone (no two-body part; complex128) at amplitudes
   // (t1d, t2d): its sigma program is the Jacobian of xi^B(T) = Omega[B](T).
   void build_set_onebody(const void *Bd, const void *t1d, const void *t2d, CstSet &out);

@@ -415,8 +415,9 @@ def test_damped_alpha_two_electrons_equals_sum_over_states():
 def test_gemm_autotuner_caches_shapes_and_keeps_results():
     """The tile autotuner: the first tensor-core sigma tunes every GEMM shape it meets (rows in
     cc_lr_gemm_tuning with the candidates timed, the best no slower than the rules' choice), and
-    the tuned launches give the same sigma as the rules' configuration (autotune off)."""
-    s = make_config("C1")
+    the tuned launches give the same sigma as the rules' configuration (autotune off).  The table is
+    per process, so the sizes here (o=9, v=44) are ones no other test tunes."""
+    s = make_system(9, 44, 180, seed=3)
     x1, x2 = random_amplitudes(s.o, s.v, seed=3)
     from paper_2604_12914_gb300 import binding
     ref = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec="3xtf32")
