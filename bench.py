@@ -391,19 +391,21 @@ def time_to_alpha_large(cfg, scale, comps=(2,), omegas=(0.0,), tol=1e-6):
             "device_memory_peak_gb": mem[1] / 1e9}
 
 
-def packed_batch(cfg, nrhs, precs, reps=2):
+def packed_batch(cfg, nrhs, precs, reps=2, budget=0):
     """sigma-vectors/s of an nrhs batch in the packed unique-amplitude layout at workload cfg
-    (lean memory: the FP64 state is released), with the context's device memory."""
+    (the FP64 state is released), with the context's device memory; budget > 0 runs the context
+    under that HBM budget (every allocation charged and checked)."""
     import torch
     from paper_2604_12914_gb300 import binding
     from paper_2604_12914_gb300.inputs import make_config
     s = make_config(cfg)
     t0 = time.perf_counter()
     stream = torch.cuda.current_stream()
-    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=precs[0], stream=stream.cuda_stream)
+    ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=precs[0], stream=stream.cuda_stream,
+                          hbm_budget=int(budget))
     ctx.cc_lr_set_refinement("3xtf32")          # no FP64 product: its set is released
     out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, {nrhs} RHS in one batched product (packed layout)",
-           "init_seconds": time.perf_counter() - t0, "nrhs": nrhs}
+           "init_seconds": time.perf_counter() - t0, "nrhs": nrhs, "budget_gb": budget / 1e9 if budget else None}
     del s
     g = torch.Generator(device="cuda")
     g.manual_seed(11)
@@ -722,7 +724,7 @@ def run_cclr(args):
     if rank == 0 and not args.no_c3:
         c3 = packed_batch("C3", 21, ["tf32", "3xtf32"])
     if rank == 0 and not args.no_c5:
-        c5 = packed_batch("C5", 1, ["tf32", "bf16x3"])
+        c5 = packed_batch("C5", 1, ["tf32", "bf16x3"], budget=180e9)
     gs = None
     if rank == 0 and not args.no_ccsd:
         gs = ground_state(args.ccsd_config, args.ccsd_scale, args.ccsd_prec, 1e-5, args.ccsd_fp64_check)

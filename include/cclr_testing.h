@@ -66,6 +66,13 @@ int cc_lr_bench_hbm(int o, int v, int reps, double *out, int n);
  * Returns 0 on success, else a cclr_status code. */
 int cc_lr_selftest_gemm_noalloc(int M, int N, int K, int mode, unsigned seed, double *err);
 
+/* The diagonal preconditioner out = r / (D - (omega + i omega_im)) on n seeded complex128 entries
+ * (D uniform in [0.1, 20], r normal), whose kernel forms the FP64 reciprocal by Newton-Raphson
+ * iteration from the FP32 reciprocal: writes max |out - r/(D - z)| / |r/(D - z)| over the entries,
+ * the reference quotient computed on the host in FP64 (IEEE division).  Returns 0 on success,
+ * else a cclr_status code. */
+int cc_lr_selftest_precond(int n, double omega, double omega_im, unsigned seed, double *max_rel_err);
+
 /* Failure-detection self-test: launches one block that waits on an mbarrier phase that
  * nothing completes, with a limit of timeout_us microseconds (globaltimer).  The wait gives
  * up, raises the device error flag and returns; *flag receives the flag (1 expected) and the

@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "cc_lr_bench_gemm": [I, I, I, I, I, P],
         "cc_lr_bench_hbm": [I, I, I, P, I],
         "cc_lr_selftest_timeout": [I, ctypes.POINTER(ctypes.c_int)],
+        "cc_lr_selftest_precond": [I, D, D, ctypes.c_uint, ctypes.POINTER(ctypes.c_double)],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -408,6 +409,13 @@ def cc_lr_selftest_timeout(timeout_us=1000):
     flag = ctypes.c_int(0)
     st = load().cc_lr_selftest_timeout(int(timeout_us), ctypes.byref(flag))
     return st, flag.value
+
+
+def cc_lr_selftest_precond(n=1 << 20, omega=0.0, omega_im=0.0, seed=1):
+    """Max relative error of the device preconditioner against host FP64 division."""
+    err = ctypes.c_double(0.0)
+    _check(load().cc_lr_selftest_precond(int(n), float(omega), float(omega_im), int(seed), ctypes.byref(err)))
+    return err.value
 
 
 def cc_lr_launch_count() -> int:

@@ -1819,6 +1819,35 @@ const char *cc_lr_last_error(void) { return g_last_error.c_str(); }
 
 unsigned long long cc_lr_launch_count(void) { return cclr::launch_count(); }
 
+int cc_lr_selftest_precond(int n, double omega, double omega_im, unsigned seed, double *max_rel_err) {
+  if (n < 1 || n > (1 << 26) || !max_rel_err) return fail(CCLR_EINVAL, "bad selftest_precond arguments");
+  return guarded([&] {
+    std::mt19937_64 g(seed);
+    std::uniform_real_distribution<double> ud(0.1, 20.0);
+    std::normal_distribution<double> nd(0.0, 1.0);
+    std::vector<double> D(n), r(2 * (size_t)n), out(2 * (size_t)n);
+    for (auto &d : D) d = ud(g);
+    for (auto &x : r) x = nd(g);
+    cudaStream_t st;
+    CCLR_CUDA(cudaStreamCreate(&st));
+    DevBuf Dd((size_t)n * 8), rd((size_t)n * 16), od((size_t)n * 16);
+    CCLR_CUDA(cudaMemcpyAsync(Dd.p, D.data(), Dd.bytes, cudaMemcpyHostToDevice, st));
+    CCLR_CUDA(cudaMemcpyAsync(rd.p, r.data(), rd.bytes, cudaMemcpyHostToDevice, st));
+    vec_precond(C128, n, Dd.as<double>(), omega, omega_im, rd.p, od.p, st);
+    CCLR_CUDA(cudaMemcpyAsync(out.data(), od.p, od.bytes, cudaMemcpyDeviceToHost, st));
+    CCLR_CUDA(cudaStreamSynchronize(st));
+    CCLR_CUDA(cudaStreamDestroy(st));
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const std::complex<double> ref = std::complex<double>(r[2 * i], r[2 * i + 1]) /
+                                       std::complex<double>(D[i] - omega, -omega_im);
+      const std::complex<double> got(out[2 * i], out[2 * i + 1]);
+      if (std::abs(ref) > 0) mx = std::max(mx, std::abs(got - ref) / std::abs(ref));
+    }
+    *max_rel_err = mx;
+  });
+}
+
 int cc_lr_selftest_timeout(int timeout_us, int *flag) {
   if (timeout_us < 1 || timeout_us > 10000000 || !flag) return fail(CCLR_EINVAL, "bad selftest_timeout arguments");
   int st = guarded([&] {

@@ -617,6 +617,19 @@ void antisym_apply(int dt, int o, int v, int dir, void *S, void *Rab, void *Rij,
 template <typename T>
 __global__ void axpy_kernel(int64_t n, double ar, double ai, const typename cpx<T>::t *x,
                             typename cpx<T>::t *y) {
+  // a real scale takes half the FP64 operations (this GPU's FP64 rate, not HBM, bounds the
+  // complex128 vector kernels)
+  if (ai == 0.0) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+      auto xv = x[i];
+      auto yv = y[i];
+      yv.x += (T)(ar * xv.x);
+      yv.y += (T)(ar * xv.y);
+      y[i] = yv;
+    }
+    return;
+  }
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     auto xv = x[i];
@@ -733,6 +746,17 @@ void vec_dot(int dt, int64_t n, const void *x, const void *y, int herm, double2 
     CCLR_CUDA(cudaGetLastError());
 }
 
+// 1/x in FP64 by Newton-Raphson iteration for the reciprocal, y <- y (2 - x y), from the FP32
+// reciprocal: each step squares the relative error (2^-24 -> 2^-48 -> below FP64 rounding), so two
+// steps give the FP64 reciprocal to about an ulp with four FP64 FMAs instead of an FP64 division
+// (this GPU's FP64 rate bounds the preconditioner). For normal x within FP32 range.
+__device__ __forceinline__ double recip_newton(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = fma(y, fma(-x, y, 1.0), y);
+  y = fma(y, fma(-x, y, 1.0), y);
+  return y;
+}
+
 // Delta = r / (D - omega), D real; in place allowed.
 template <typename T>
 __global__ void precond_kernel(int64_t n, const double *D, double omega, double omega_im,
@@ -744,10 +768,11 @@ __global__ void precond_kernel(int64_t n, const double *D, double omega, double 
     if (omega_im == 0.0) {
       double d = D[i] - omega;
       if (fabs(d) < 1e-8) d = d < 0 ? -1e-8 : 1e-8;
-      o.x = (T)(v.x / d);
-      o.y = (T)(v.y / d);
+      const double q = recip_newton(d);
+      o.x = (T)(v.x * q);
+      o.y = (T)(v.y * q);
     } else {  // v / (d - i w_im) = v (d + i w_im) / (d^2 + w_im^2)
-      const double d = D[i] - omega, q = 1.0 / (d * d + omega_im * omega_im);
+      const double d = D[i] - omega, q = recip_newton(d * d + omega_im * omega_im);
       o.x = (T)((v.x * d - v.y * omega_im) * q);
       o.y = (T)((v.y * d + v.x * omega_im) * q);
     }
@@ -1043,32 +1068,37 @@ void build_diag(int o, int v, const void *Foo, const void *Fvv, double *D1, doub
 // F (+)= alpha * unpack(P), one thread per full entry (writes coalesced; the packed row of one
 // (i,j) pair is read with a stride that depends on the (a,b) order, from L2).
 template <typename TP, typename TF>
-__global__ void unpack_doubles_kernel(int o, int v, const typename cpx<TP>::t *P, typename cpx<TF>::t *F,
-                                      double ar, double ai, int acc) {
-  const int64_t vv = (int64_t)v * v, n = (int64_t)o * o * vv, Pv = (int64_t)v * (v - 1) / 2;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t ab = e % vv, ij = e / vv;
-    const int a = (int)(ab / v), b = (int)(ab % v), i = (int)(ij / o), j = (int)(ij % o);
-    typename cpx<TP>::t z;
-    z.x = 0;
-    z.y = 0;
-    double sg = 0.0;
-    if (i != j && a != b) {
-      const int p = min(i, j), q = max(i, j), r = min(a, b), s = max(a, b);
-      sg = ((i < j) == (a < b)) ? 1.0 : -1.0;
-      z = P[pair_id(p, q, o) * Pv + pair_id(r, s, v)];
-    }
-    const double zr = sg * (double)z.x, zi = sg * (double)z.y;
-    double wr = ar * zr - ai * zi, wi = ar * zi + ai * zr;
-    if (acc) {
-      wr += (double)F[e].x;
-      wi += (double)F[e].y;
-    }
-    typename cpx<TF>::t w;
-    w.x = (TF)wr;
-    w.y = (TF)wi;
-    F[e] = w;
+__global__ void __launch_bounds__(256) unpack_doubles_kernel(int o, int v, const typename cpx<TP>::t *__restrict__ P,
+                                                             typename cpx<TF>::t *__restrict__ F, double ar, double ai,
+                                                             int acc, int unit) {
+  // block (32, 8): b = blockIdx.x * 32 + x, a = blockIdx.y * 8 + y, (i, j) = blockIdx.z: no division
+  const int b = blockIdx.x * 32 + threadIdx.x, a = blockIdx.y * 8 + threadIdx.y;
+  if (a >= v || b >= v) return;
+  const int i = blockIdx.z / o, j = blockIdx.z % o;
+  const int64_t Pv = (int64_t)v * (v - 1) / 2;
+  const int64_t e = ((int64_t)blockIdx.z * v + a) * v + b;
+  TF zr = 0, zi = 0;
+  if (i != j && a != b) {
+    const int p = min(i, j), q = max(i, j), r = min(a, b), s2 = max(a, b);
+    const typename cpx<TP>::t z = P[pair_id(p, q, o) * Pv + pair_id(r, s2, v)];
+    const bool pos = (i < j) == (a < b);
+    zr = pos ? (TF)z.x : -(TF)z.x;
+    zi = pos ? (TF)z.y : -(TF)z.y;
   }
+  // alpha = 1 (unit) takes no multiply: this GPU's FP64 rate would bound the complex128 case
+  TF wr = zr, wi = zi;
+  if (!unit) {
+    wr = (TF)(ar * (double)zr - ai * (double)zi);
+    wi = (TF)(ar * (double)zi + ai * (double)zr);
+  }
+  if (acc) {
+    wr += F[e].x;
+    wi += F[e].y;
+  }
+  typename cpx<TF>::t w;
+  w.x = wr;
+  w.y = wi;
+  F[e] = w;
 }
 
 // P = F[i<j, a<b], one thread per packed entry (writes coalesced, reads along b).
@@ -1088,18 +1118,18 @@ __global__ void pack_doubles_kernel(int o, int v, const typename cpx<TF>::t *F, 
 }
 
 void unpack_doubles(int dt_p, int dt_f, int o, int v, const void *P, void *F, zc alpha, bool acc, cudaStream_t st) {
-  const int64_t n = (int64_t)o * o * v * v;
-  if (n == 0) return;
-  const unsigned g = grid_for(n);
-  const int a = acc ? 1 : 0;
+  if ((int64_t)o * o * v * v == 0) return;
+  CCLR_REQUIRE((int64_t)o * o < 65536, "unpack_doubles: too many occupied pairs for the grid");
+  const dim3 g((unsigned)((v + 31) / 32), (unsigned)((v + 7) / 8), (unsigned)(o * o)), b(32, 8);
+  const int a = acc ? 1 : 0, u = (alpha.re == 1.0 && alpha.im == 0.0) ? 1 : 0;
   if (dt_p == C128 && dt_f == C128)
-    unpack_doubles_kernel<double, double><<<g, 256, 0, st>>>(o, v, (const double2 *)P, (double2 *)F, alpha.re, alpha.im, a);
+    unpack_doubles_kernel<double, double><<<g, b, 0, st>>>(o, v, (const double2 *)P, (double2 *)F, alpha.re, alpha.im, a, u);
   else if (dt_p == C128 && dt_f == C64)
-    unpack_doubles_kernel<double, float><<<g, 256, 0, st>>>(o, v, (const double2 *)P, (float2 *)F, alpha.re, alpha.im, a);
+    unpack_doubles_kernel<double, float><<<g, b, 0, st>>>(o, v, (const double2 *)P, (float2 *)F, alpha.re, alpha.im, a, u);
   else if (dt_p == C64 && dt_f == C128)
-    unpack_doubles_kernel<float, double><<<g, 256, 0, st>>>(o, v, (const float2 *)P, (double2 *)F, alpha.re, alpha.im, a);
+    unpack_doubles_kernel<float, double><<<g, b, 0, st>>>(o, v, (const float2 *)P, (double2 *)F, alpha.re, alpha.im, a, u);
   else
-    unpack_doubles_kernel<float, float><<<g, 256, 0, st>>>(o, v, (const float2 *)P, (float2 *)F, alpha.re, alpha.im, a);
+    unpack_doubles_kernel<float, float><<<g, b, 0, st>>>(o, v, (const float2 *)P, (float2 *)F, alpha.re, alpha.im, a, u);
   count_launch();
   CCLR_CUDA(cudaGetLastError());
 }

@@ -74,23 +74,84 @@ __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *
   }
 }
 
-// out[i,j,a,b] += alpha * S[(ab) * lds + (ij)] with the four antisymmetric images.
-__global__ void unpack_sig(const float2 *S, int64_t lds, int o, int v, const int2 *op, const int2 *vp,
-                           int64_t Po, int64_t Pv, float ar, float ai, float2 *out) {
-  const int64_t total = Po * Pv;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t n = e / Pv, k = e % Pv;  // n = (i<j), k = (a<b)
-    const int2 ij = op[n], ab = vp[k];
-    const float2 s = S[k * lds + n];
-    const float2 val = make_float2(ar * s.x - ai * s.y, ar * s.y + ai * s.x);
-    const int64_t i = ij.x, j = ij.y, a = ab.x, b = ab.y;
-    float2 *p;
-    p = out + ((i * o + j) * v + a) * v + b; p->x += val.x; p->y += val.y;
-    p = out + ((j * o + i) * v + a) * v + b; p->x -= val.x; p->y -= val.y;
-    p = out + ((i * o + j) * v + b) * v + a; p->x -= val.x; p->y -= val.y;
-    p = out + ((j * o + i) * v + b) * v + a; p->x += val.x; p->y += val.y;
+// out[i,j,a,b] += alpha * S[(ab) * lds + (ij)] with the four antisymmetric images (S rows (a<b),
+// columns (i<j)).
+// By orbit tiles: one block takes a 32 x 32 tile of (a, b) with a-block <= b-block and
+// SIG_TN consecutive (i<j) pairs; it reads S[(ab)][(ij) .. (ij) + SIG_TN) (one 32-byte run per pair
+// (ab)) into shared memory, then writes the four images out[i,j,a,b], out[j,i,a,b] (along b) and
+// out[i,j,b,a], out[j,i,b,a] (along a, through the transposed shared tile), each coalesced.  Every
+// unordered (a, b) belongs to one tile and every (i<j) to one chunk, so no two blocks touch one entry.
+constexpr int SIG_TN = 4;
+__global__ void __launch_bounds__(256) unpack_sig_tiled(const float2 *__restrict__ S, int64_t lds, int o, int v,
+                                                        const int2 *__restrict__ op, int64_t Po, int nbv, float ar,
+                                                        float ai, float2 *__restrict__ out) {
+  __shared__ float2 T[SIG_TN][32][33];
+  // tile (A, B), A <= B, from blockIdx.x in row order of the upper triangle of nbv x nbv blocks
+  int A = 0, t = blockIdx.x;
+  while (t >= nbv - A) { t -= nbv - A; ++A; }
+  const int B = A + t;
+  const int a0 = A * 32, b0 = B * 32, tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t n0 = (int64_t)blockIdx.y * SIG_TN;
+  const int nn = Po - n0 < SIG_TN ? (int)(Po - n0) : SIG_TN;
+  for (int al = ty; al < 32; al += 8) {
+    const int a = a0 + al, b = b0 + tx;
+    const bool in = a < b && b < v;
+    const int64_t k = in ? ((int64_t)a * v - (int64_t)a * (a + 1) / 2 + b - a - 1) : 0;
+    for (int q = 0; q < SIG_TN; ++q) {
+      float2 s = make_float2(0.f, 0.f);
+      if (in && q < nn) {
+        const float2 z = S[k * lds + n0 + q];
+        s = make_float2(ar * z.x - ai * z.y, ar * z.y + ai * z.x);
+      }
+      T[q][al][tx] = s;
+    }
   }
+  __syncthreads();
+  for (int q = 0; q < nn; ++q) {
+    const int2 ij = op[n0 + q];
+    const int64_t rij = ((int64_t)ij.x * o + ij.y) * v, rji = ((int64_t)ij.y * o + ij.x) * v;
+    for (int rl = ty; rl < 32; rl += 8) {
+      {  // (a = a0 + rl, b = b0 + tx): images (ij, ab) and (ji, ab)
+        const int a = a0 + rl, b = b0 + tx;
+        if (a < b && b < v) {
+          const float2 val = T[q][rl][tx];
+          float2 *p = out + (rij + a) * v + b;
+          float2 w = *p;
+          w.x += val.x; w.y += val.y;
+          *p = w;
+          p = out + (rji + a) * v + b;
+          w = *p;
+          w.x -= val.x; w.y -= val.y;
+          *p = w;
+        }
+      }
+      {  // (b = b0 + rl, a = a0 + tx): images (ij, ba) and (ji, ba)
+        const int b = b0 + rl, a = a0 + tx;
+        if (a < b && b < v) {
+          const float2 val = T[q][tx][rl];
+          float2 *p = out + (rij + b) * v + a;
+          float2 w = *p;
+          w.x -= val.x; w.y -= val.y;
+          *p = w;
+          p = out + (rji + b) * v + a;
+          w = *p;
+          w.x += val.x; w.y += val.y;
+          *p = w;
+        }
+      }
+    }
+  }
+}
+
+void launch_unpack_sig(const float2 *S, int64_t lds, int o, int v, const int2 *op, int64_t Po, float ar, float ai,
+                       float2 *out, cudaStream_t st) {
+  if (Po == 0 || v < 2) return;
+  const int nbv = (v + 31) / 32;
+  const int64_t ny = (Po + SIG_TN - 1) / SIG_TN;
+  CCLR_REQUIRE(ny < 65536, "unpack_sig: too many occupied pairs for the grid");
+  unpack_sig_tiled<<<dim3((unsigned)(nbv * (nbv + 1) / 2), (unsigned)ny), dim3(32, 8), 0, st>>>(S, lds, o, v, op, Po,
+                                                                                              nbv, ar, ai, out);
+  count_launch();
 }
 
 // out[i,j,e,f] += alpha * Z[(ij)][(ef)] for i<j, e<f only (Z rows of Pv).
@@ -137,9 +198,7 @@ void ladder_unpack_sig_bench(int o, int v, const void *S, void *out, cudaStream_
     po = o;
     pv = v;
   }
-  unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>((const float2 *)S, Po, o, v, opairs.as<int2>(), vpairs.as<int2>(), Po, Pv,
-                                               1.f, 0.f, (float2 *)out);
-  count_launch();
+  launch_unpack_sig((const float2 *)S, Po, o, v, opairs.as<int2>(), Po, 1.f, 0.f, (float2 *)out, st);
   CCLR_CUDA(cudaGetLastError());
 }
 
@@ -350,13 +409,13 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   }
   for (int64_t r = 0; r < NR; ++r) {
     if (dir > 0) {
-      unpack_sig<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>() + Po * r, Po * NR, o, v, op, vp, Po, Pv,
-                                                   (float)alpha.re, (float)alpha.im, (float2 *)out[r]);
+      launch_unpack_sig(sig.as<float2>() + Po * r, Po * NR, o, v, op, Po, (float)alpha.re, (float)alpha.im,
+                        (float2 *)out[r], st);
     } else {
       unpack_z<<<grid1d(Po * Pv), 256, 0, st>>>(sig.as<float2>() + Po * Pv * r, o, v, op, vp, Po, Pv,
                                                  (float)alpha.re, (float)alpha.im, (float2 *)out[r]);
+      count_launch();
     }
-    count_launch();
   }
   CCLR_CUDA(cudaGetLastError());
 }

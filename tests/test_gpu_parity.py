@@ -464,3 +464,11 @@ def test_packed_sigma_entry_point_matches_full_layout(prec, tol):
             ref = pack(g1[r], g2[r])
             assert np.abs(got[r] - ref).max() < tol * np.abs(ref).max()
     ctx.close()
+
+
+@pytest.mark.parametrize("omega,omega_im", [(0.0, 0.0), (0.0428, 0.0), (0.7, 0.02)])
+def test_preconditioner_reciprocal_within_fp64_rounding(omega, omega_im):
+    """The preconditioner's Newton-Raphson FP64 reciprocal against host IEEE division."""
+    from paper_2604_12914_gb300 import binding
+    err = binding.cc_lr_selftest_precond(1 << 20, omega, omega_im, seed=5)
+    assert err < 1e-15, err
