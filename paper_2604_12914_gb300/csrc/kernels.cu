@@ -897,6 +897,65 @@ __global__ void __launch_bounds__(128) smallk_kernel(int64_t P, int K, int J, in
   }
 }
 
+// The complex64 case with k <= 32: each thread keeps its column X[p][.][q] in registers (all K loads
+// issued at once), prefetches eight outputs at a time, and reads S from shared memory.
+template <int KT>
+__global__ void __launch_bounds__(128) smallk_reg_kernel(int64_t P, int K, int J, int64_t Q,
+                                                         const float2 *__restrict__ S, int64_t sSk, int64_t sSj,
+                                                         const float2 *__restrict__ X, int64_t sXp, int64_t sXk,
+                                                         float2 *__restrict__ Y, int64_t sYp, int64_t sYj, float ar,
+                                                         float ai) {
+  extern __shared__ __align__(16) unsigned char smr_raw[];
+  float2 *Ss = (float2 *)smr_raw;  // [K][J]
+  for (int e = threadIdx.x; e < K * J; e += blockDim.x) {
+    const int k = e / J, j = e % J;
+    Ss[e] = S[(int64_t)k * sSk + (int64_t)j * sSj];
+  }
+  __syncthreads();
+  const int64_t nqt = (Q + 127) / 128;
+  for (int64_t t = blockIdx.x; t < P * nqt; t += gridDim.x) {
+    const int64_t p = t / nqt, q = (t % nqt) * 128 + threadIdx.x;
+    if (q >= Q) continue;
+    const float2 *xp = X + p * sXp + q;
+    float2 x[KT];
+#pragma unroll
+    for (int k = 0; k < KT; ++k) x[k] = k < K ? xp[(int64_t)k * sXk] : make_float2(0.f, 0.f);
+    float2 *yp = Y + p * sYp + q;
+    for (int j0 = 0; j0 < J; j0 += 8) {
+      float2 yv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j0 + u < J) yv[u] = yp[(int64_t)(j0 + u) * sYj];
+      float re[8], im[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) { re[u] = 0.f; im[u] = 0.f; }
+#pragma unroll
+      for (int k = 0; k < KT; ++k) {
+        if (k < K) {
+          const float2 *sr = Ss + k * J + j0;
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (j0 + u < J) {
+              const float2 sv = sr[u];
+              re[u] += sv.x * x[k].x - sv.y * x[k].y;
+              im[u] += sv.x * x[k].y + sv.y * x[k].x;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j0 + u < J) {
+          float2 y = yv[u];
+          y.x += ar * re[u] - ai * im[u];
+          y.y += ar * im[u] + ai * re[u];
+          yp[(int64_t)(j0 + u) * sYj] = y;
+        }
+      }
+    }
+  }
+}
+
 void contract_smallk(int dt, int64_t P, int K, int J, int64_t Q, const void *S, int64_t sSk, int64_t sSj,
                      const void *X, int64_t sXp, int64_t sXk, void *Y, int64_t sYp, int64_t sYj, zc alpha,
                      cudaStream_t st) {
@@ -916,6 +975,14 @@ void contract_smallk(int dt, int64_t P, int K, int J, int64_t Q, const void *S, 
   }
   const int64_t tiles = P * ((Q + 127) / 128);
   const unsigned grid = (unsigned)std::min<int64_t>(tiles, (int64_t)152 * 16);
+  if (dt == C64 && K <= 32) {
+    smallk_reg_kernel<32><<<grid, 128, (size_t)K * J * 8, st>>>(P, K, J, Q, (const float2 *)S, sSk, sSj,
+                                                                (const float2 *)X, sXp, sXk, (float2 *)Y, sYp, sYj,
+                                                                (float)alpha.re, (float)alpha.im);
+    count_launch();
+    CCLR_CUDA(cudaGetLastError());
+    return;
+  }
   if (dt == C128)
     smallk_kernel<double><<<grid, 128, smem, st>>>(P, K, J, Q, (const double2 *)S, sSk, sSj, (const double2 *)X, sXp,
                                                    sXk, (double2 *)Y, sYp, sYj, alpha.re, alpha.im);
