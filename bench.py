@@ -493,6 +493,17 @@ def ground_state(cfg, scale, prec, tol, fp64_check=False):
     el = time.perf_counter() - t0
     out.update({"seconds": el, "residuals": its, "seconds_per_residual": el / max(its, 1),
                 "residual_norm": rn, "converged": rn < tol, "energy": [e.real, e.imag]})
+    # then the ground-state Lambda at the converged T (lambda A = -dE/dT): TF32 corrections with
+    # 3xTF32 refinement residuals, relative residual 1e-6
+    ctx.cc_lr_set_precision("tf32")
+    ctx.cc_lr_set_refinement("3xtf32")
+    t0 = time.perf_counter()
+    try:
+        ctx.cc_lr_lambda(tol=1e-6)
+        out["lambda_seconds"] = time.perf_counter() - t0
+        out["lambda_precision_mode"] = "tf32 corrections, 3xtf32 refinement, relative residual 1e-6"
+    except binding.CclrError as err:
+        out["lambda_error"] = str(err)
     if fp64_check:
         t1, t2 = ctx.cc_lr_get_t()
         t0 = time.perf_counter()

@@ -154,3 +154,21 @@ def test_solve_reports_no_convergence():
         ctx.cc_lr_ccsd(tol=1e-14, max_iterations=1)
     assert ei.value.status == binding.CCLR_ENOCONV
     ctx.close()
+
+
+def test_solve_two_electrons_equals_fci():
+    """o=2: the library's converged CCSD energy is the exact (FCI) correlation energy of the state
+    the CC wave function represents, and its amplitudes reproduce that state."""
+    from oracle import secondq
+    o, v = 2, 6
+    s = make_system(o, v, 10, seed=6, scale=0.4)
+    f, g, L, _, _ = oracle_setup(s, np.zeros((o, v)), np.zeros((o, o, v, v)))
+    ctx = gpu_context(s)
+    e, rn, its = ctx.cc_lr_ccsd(tol=1e-12, max_iterations=200, prec="fp64")
+    gt1, gt2 = ctx.cc_lr_get_t()
+    bf = secondq.BruteForce(f.numpy(), g.numpy(), o)
+    w, U = bf.fci()
+    st, ov = secondq.cc_state_overlap(U, gt1, gt2, bf)
+    assert ov > 1 - 1e-10
+    assert abs(e - (w[st] - bf.e_ref)) < 1e-11 * max(1.0, abs(e))
+    ctx.close()

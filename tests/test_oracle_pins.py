@@ -376,3 +376,17 @@ def test_residual_is_gauss_legendre_integral_of_jacobian(o, v, naux, seed):
     assert float((g2 - r2).abs().max()) < 1e-12 * scale
     m1, m2 = J.sigma_terms(J.Dressed(f, L, 0.5 * t1, 0.5 * t2), t1, t2)
     assert float((z2 + m2 - r2).abs().max()) > 1e-4 * scale
+
+
+def test_ccsd_energy_two_electrons_equals_fci():
+    """Two electrons: CCSD is exact, so the converged correlation energy is the FCI eigenvalue of
+    the state the CC wave function represents, minus the reference energy (Sec. 2.2 energy)."""
+    o, v = 2, 5
+    s = _system(o, v, 8, seed=6, scale=0.4)
+    P = oracle_problem(s, converge=True)
+    bf = secondq.BruteForce(P.f.numpy(), P.g.numpy(), o)
+    w, U = bf.fci()
+    st, ov = secondq.cc_state_overlap(U, P.t1.numpy(), P.t2.numpy(), bf)
+    assert ov > 1 - 1e-10
+    e = complex(ccsd.energy(P.f, P.g, P.t1, P.t2))
+    assert abs(e - (w[st] - bf.e_ref)) < 1e-11 * max(1.0, abs(e))
