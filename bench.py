@@ -423,8 +423,9 @@ def packed_batch(cfg, nrhs, precs, reps=2, budget=0):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
         tm = ctx.cc_lr_last_timings()
-        out[p] = {"ms_per_batch": ms, "sigma_vectors_per_s": nrhs / (ms / 1e3), "ladder_ms": float(tm[0]),
-                  "formation_ms": float(tm[3]), "ladder_group_size": ctx.cc_lr_ladder_tuning(p)[0]}
+        out[p] = {"ms_per_batch": ms, "sigma_vectors_per_s": nrhs / (ms / 1e3),
+                  "products_per_batch": int(tm[4]), "last_product_ladder_ms": float(tm[0]),
+                  "last_product_formation_ms": float(tm[3]), "ladder_group_size": ctx.cc_lr_ladder_tuning(p)[0]}
     used, peak, _ = ctx.cc_lr_memory()
     out["device_memory_gb"] = {"held": used / 1e9, "peak": peak / 1e9,
                                "caller_vectors": 2 * x.numel() * 16 / 1e9}

@@ -278,9 +278,11 @@ cclr_status cc_lr_gemm_tuning(cclr_ctx *ctx, int cap, int *n, double *rec);
 cclr_status cc_lr_memory(cclr_ctx *ctx, size_t *in_use, size_t *peak, size_t *budget);
 
 /* Device-side timing (CUDA events on the context's stream) of the last sigma or
- * sigma^T product, in milliseconds; writes the first min(n, 4) of: [0] particle-particle
+ * sigma^T product, in milliseconds; writes the first min(n, 5) of: [0] particle-particle
  * ladder (formation of <ab|ef>~ from L~_vv and its contraction with X), [1] every other
- * kernel, [2] total, [3] the ladder's formation GEMMs alone (tensor-core modes; 0 otherwise). */
+ * kernel, [2] total, [3] the ladder's formation GEMMs alone (tensor-core modes; 0 otherwise),
+ * [4] the number of batched products the last multi-vector call was split into to fit the
+ * device memory (1: all its vectors in one product). */
 cclr_status cc_lr_last_timings(cclr_ctx *ctx, double *ms, int n);
 
 void cc_lr_free(cclr_ctx *ctx);

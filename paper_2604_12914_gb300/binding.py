@@ -366,9 +366,10 @@ class Context:
         return a.value, b.value, c.value
 
     def cc_lr_last_timings(self):
-        """[ladder, everything else, total, ladder formation GEMMs] of the last product (ms)."""
-        out = np.zeros(4, dtype=np.float64)
-        _check(load().cc_lr_last_timings(self._h, _ptr(out), 4))
+        """[ladder, everything else, total, ladder formation GEMMs] of the last product (ms), and
+        [4] the number of products the last multi-vector call was split into."""
+        out = np.zeros(5, dtype=np.float64)
+        _check(load().cc_lr_last_timings(self._h, _ptr(out), 5))
         return out
 
 

@@ -131,9 +131,11 @@ struct cclr_ctx {
     const int fit = (int)(free_b / 3.0 / per);
     return std::max(1, std::min(nr, fit));
   }
+  int last_products = 1;  // batched products the last op_batch was split into
   void op_batch(int dir, int nr, const void *const *xs, void *const *ss, const CstSet *set = nullptr) {
     if (set == nullptr) set = &M->cst_for(M->prec);
     const int cap = batch_cap(dir, set->dt, nr);
+    last_products = (nr + cap - 1) / cap;
     if (cap < nr) {  // several batched products, each sharing its formed blocks
       for (int r0 = 0; r0 < nr; r0 += cap) op_batch_chunk(dir, std::min(cap, nr - r0), xs + r0, ss + r0, set);
       return;
@@ -1790,6 +1792,7 @@ cclr_status cc_lr_memory(cclr_ctx *c, size_t *in_use, size_t *peak, size_t *budg
 cclr_status cc_lr_last_timings(cclr_ctx *c, double *ms, int n) {
   if (!c || !ms || n < 0) return (cclr_status)fail(CCLR_EINVAL, "bad timings arguments");
   for (int k = 0; k < n && k < 4; ++k) ms[k] = c->M->ms_last[k];
+  if (n > 4) ms[4] = c->last_products;
   return CCLR_OK;
 }
 
