@@ -404,7 +404,8 @@ def packed_batch(cfg, nrhs, precs, reps=2, budget=0):
     ctx = binding.Context(s.o, s.v, s.naux, s.eps, s.L, s.mu, prec=precs[0], stream=stream.cuda_stream,
                           hbm_budget=int(budget))
     ctx.cc_lr_set_refinement("3xtf32")          # no FP64 product: its set is released
-    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, {nrhs} RHS in one batched product (packed layout)",
+    out = {"workload": f"{cfg} o={s.o} v={s.v} naux={s.naux}, {nrhs} RHS per call in the packed layout "
+                       "(split into as few batched products as the device memory allows: products_per_batch)",
            "init_seconds": time.perf_counter() - t0, "nrhs": nrhs, "budget_gb": budget / 1e9 if budget else None}
     del s
     g = torch.Generator(device="cuda")

@@ -74,55 +74,6 @@ __global__ void pack_w(const float2 *W, int64_t ldw, int v, int a0, const int2 *
   }
 }
 
-// Mode 0 of pack_w by 32 x 32 tiles of (e, f), e-block <= f-block, one (a,b) pair of the group per
-// block row: the two gathers W[(b,f)][(a,e)] (rows f, along e) and W[(b,e)][(a,f)] (rows e, along f)
-// become coalesced tile loads, and the packed (e<f) entries of a tile row are written along f.  Tiles
-// with no (e<f) pair in q0 .. q0 + nq - 1 return before loading; the pad columns nq .. Kp-1 of each
-// row are written (zero) by its first tile.
-template <int KIND>
-__global__ void __launch_bounds__(256) pack_w_tiled(const float2 *__restrict__ W, int64_t ldw, int v, int a0,
-                                                    const int2 *__restrict__ vp, int64_t p0, int64_t q0, int64_t nq,
-                                                    int64_t Kp, int seg, int nbv, typename TcElem<KIND>::T *dst,
-                                                    int64_t ldd) {
-  __shared__ float2 T1[32][33], T2[32][33];
-  int E = 0, t = blockIdx.x;
-  while (t >= nbv - E) { t -= nbv - E; ++E; }
-  const int F = E + t;
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int64_t r = blockIdx.y;
-  typename TcElem<KIND>::T *row = dst + r * ldd;
-  if (blockIdx.x == 0)
-    for (int64_t q = nq + ty * 32 + tx; q < Kp; q += 256) tc_put_a<KIND>(row, q, Kp, seg, make_float2(0.f, 0.f));
-  const int e0 = E * 32, f0 = F * 32;
-  auto qof = [&](int64_t e, int64_t f) { return e * v - e * (e + 1) / 2 + f - e - 1; };
-  {  // the tile's (e<f) pairs span [qmin, qmax]
-    const int64_t elast = min(e0 + 31, v - 2), flast = min(f0 + 31, v - 1);
-    const int64_t ffirst = max(f0, e0 + 1);
-    if (elast < e0 || ffirst > flast) return;
-    const int64_t qmin = qof(e0, ffirst), qmax = qof(elast, flast);
-    if (qmax < q0 || qmin >= q0 + nq) return;
-  }
-  const int2 ab = vp[p0 + r];
-  const int64_t rb = (int64_t)(ab.y - a0) * v, ca = (int64_t)(ab.x - a0) * v;
-  for (int l = ty; l < 32; l += 8) {
-    const int f = f0 + l, e = e0 + tx;
-    T1[l][tx] = (f < v && e < v) ? W[(rb + f) * ldw + ca + e] : make_float2(0.f, 0.f);
-    const int e2 = e0 + l, f2 = f0 + tx;
-    T2[l][tx] = (e2 < v && f2 < v) ? W[(rb + e2) * ldw + ca + f2] : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int el = ty; el < 32; el += 8) {
-    const int e = e0 + el, f = f0 + tx;
-    if (e < f && f < v) {
-      const int64_t q = qof(e, f) - q0;
-      if (q >= 0 && q < nq) {
-        const float2 w1 = T1[tx][el], w2 = T2[el][tx];
-        tc_put_a<KIND>(row, q, Kp, seg, make_float2(w1.x - w2.x, w1.y - w2.y));
-      }
-    }
-  }
-}
-
 // out[i,j,a,b] += alpha * S[(ab) * lds + (ij)] with the four antisymmetric images (S rows (a<b),
 // columns (i<j)).
 // By orbit tiles: one block takes a 32 x 32 tile of (a, b) with a-block <= b-block and
@@ -387,18 +338,6 @@ void LadderTC::apply(Engine &E, int dir, zc alpha, int nrhs, const void *const *
   // pack_w launch into dst (rows of ldd elements of the mode's operand type)
   auto packw = [&](int a0, int64_t p0, int64_t np, int64_t q0, int64_t nq, int64_t cols, int64_t Kp, int mode,
                    void *dst, int64_t ldd) {
-    if (mode == 0 && np < 65536) {  // the forward operand by orbit tiles of (e, f)
-      const int nbv = (v + 31) / 32;
-      const dim3 g((unsigned)(nbv * (nbv + 1) / 2), (unsigned)np), b(32, 8);
-      if (kind == TC_BF16)
-        pack_w_tiled<TC_BF16><<<g, b, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, q0, nq, Kp, seg, nbv,
-                                              (__nv_bfloat16 *)dst, ldd);
-      else
-        pack_w_tiled<TC_TF32><<<g, b, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, q0, nq, Kp, seg, nbv,
-                                              (float *)dst, ldd);
-      count_launch();
-      return;
-    }
     const int64_t total = mode == 0 ? np * Kp : nq * Kp;
     if (kind == TC_BF16)
       pack_w<TC_BF16><<<grid1d(total), 256, 0, st>>>(W.as<float2>(), cols, v, a0, vp, p0, np, q0, nq, Kp, seg, mode,
