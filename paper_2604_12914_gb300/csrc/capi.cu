@@ -1088,7 +1088,19 @@ struct cclr_ctx {
     AVec sv;
     alloc_vec(sv);
     CCLR_CUDA(cudaMemsetAsync(out, 0, (size_t)ntot() * 16, st));
+    // a budgeted context holds one set of intermediates at a time: the working set is freed while
+    // the stencil's sets exist and rebuilt on its next use
+    if (M->lean) {
+      M->release_set(M->c64);
+      M->release_set(M->c128);
+    }
     for (int s = 0; s < 4; ++s) {
+      // and the products' own buffers are freed before each build, whose temporaries need the room
+      if (M->lean) {
+        M->release_product_buffers();
+        for (auto &v : xfs) v.clear();
+        for (auto &v : sfs) v.clear();
+      }
       AVec &ts = shifted(x, ks[s] * h);
       const int saved = M->prec;
       const int use = M->prec == CCLR_FP64 ? CCLR_FP64 : hi_prec;

@@ -352,6 +352,21 @@ void Model::release_fp64() {
   lcc.release();
 }
 
+void Model::release_product_buffers() {
+  tmp64.clear();
+  tmp128.clear();
+  x2bar[0].clear();
+  x2bar[1].clear();
+  E.release_ws();
+  E.clear_prep_cache();
+  for (int k = 0; k < 3; ++k) {
+    ltc[k].release();
+    ltc_src[k] = nullptr;
+  }
+  lcc.release();
+  clear_graphs();
+}
+
 void Model::release_fp64_inputs() {
   ensure_src64();
   oovv_packed();

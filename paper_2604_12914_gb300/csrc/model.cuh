@@ -131,6 +131,10 @@ class Model {
   // frees everything the FP64 products hold (the complex128 set, temporaries and the CUDA-core
   // ladder's blocks); an FP64 product afterwards rebuilds them
   void release_fp64();
+  // frees what a product allocates for itself and keeps for the next one (program temporaries,
+  // x2-bar, workspace, the ladders' blocks and prepared operands); the next product allocates
+  // them again
+  void release_product_buffers();
   // lean memory (a context with an HBM budget): also frees the undressed complex128 Cholesky
   // blocks once their complex64 copies exist; FP64 products are refused afterwards
   bool fp64_gone = false;
